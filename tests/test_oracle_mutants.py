@@ -1,0 +1,57 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case copies oracle.c to a temporary directory, plants one mistake by a
+literal text substitution, builds it, and runs the pin suite against the
+broken copy (through MS_ORACLE_SO). The suite must fail for every mutant.
+Nothing here touches a GPU.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+MUTANTS = {
+    "window_exclusive": ("        if (cs >= c) {\n            for", "        if (cs > c) {\n            for"),
+    "mean_not_renormalised": ("x_new[k] = y[k] / yn;", "x_new[k] = y[k] / (double)cnt;"),
+    "update_drops_first_dim": ("            for (int32_t k = 0; k < dim; ++k) y[k] += p[k];",
+                               "            for (int32_t k = 1; k < dim; ++k) y[k] += p[k];"),
+    "merge_support_ascending": ("return a->support > b->support ? -1 : 1;", "return a->support > b->support ? 1 : -1;"),
+    "merge_tie_latest_first": ("return a->order < b->order ? -1 : 1;", "return a->order < b->order ? 1 : -1;"),
+    "merge_inclusive_keep": ("if (n_kept == 0 || best < merge_cos) {", "if (n_kept == 0 || best <= merge_cos + 0.05) {"),
+    "early_stop_at_gamma": ("if ((double)nconv > gamma * (double)m || nmove == 0) break;",
+                            "if ((double)nconv >= gamma * (double)m || nmove == 0) break;"),
+    "schedule_floor": ("nn = N - (int64_t)ceil(nmin);", "nn = N - (int64_t)floor(nmin);"),
+    "schedule_no_doubling": ("nn = 2 * N;", "nn = N + N / 2;"),
+    "eq19_uses_eq15_base": ("return log(1.0 - exp(log(P) / I)) / log(1.0 - r / I);",
+                            "return log(1.0 - exp(log(P) / I)) / log(1.0 - 1.0 / (2.0 * I));"),
+    "eq14_missing_power_I": ("return pow(1.0 - pow(1.0 - r / I, N), I);", "return 1.0 - pow(1.0 - r / I, N);"),
+    "cover_exclusive": ("            if (best >= c) {", "            if (best > c) {"),
+    "label_ties_highest": ("            if (cs > b1) {", "            if (cs >= b1) {"),
+    "seeds_ignore_coverage": ("            if (covered[i]) continue;\n            covered[i] = 1;",
+                              "            covered[i] = 1;"),
+    "perm_offset_ignored": ("return (int64_t)((aj + (uint64_t)b) % (uint64_t)n);", "return (int64_t)(aj % (uint64_t)n);"),
+    "normalise_skipped": ("for (int32_t k = 0; k < dim; ++k) p[k] = (double)e[k] / nrm;",
+                          "for (int32_t k = 0; k < dim; ++k) p[k] = (double)e[k];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    shutil.copy(os.path.join(ROOT, "oracle", "oracle.h"), tmp_path / "oracle.h")
+    (tmp_path / "oracle.c").write_text(src.replace(old, new))
+    so = str(tmp_path / "liboracle_mut.so")
+    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                    str(tmp_path / "oracle.c"), "-o", so, "-lm"], check=True, capture_output=True)
+    env = dict(os.environ, MS_ORACLE_SO=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"

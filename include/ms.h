@@ -1,0 +1,217 @@
+/*
+ * libms -- cosine mean-shift with the online seed optimisation policy (OSOP)
+ * on one GPU (sm_103a). C ABI: plain pointers and sizes, no C++ types.
+ *
+ * Method: "Faster Mean-shift: GPU-accelerated clustering for cosine
+ * embedding-based cell segmentation and tracking" (Zhao et al.).
+ *   Problem statement: given a vector set S and a bandwidth h, return the
+ *   modes and a vector-to-mode assignment (Algorithm 1 and 2, Require/Ensure).
+ *   Cosine distance d = 1 - cos (Eq. 9); the flat kernel k_h = [d <= h]
+ *   (Eq. 11), so a window is {i : cos(x, p_i) >= c} with c = 1 - h.
+ *   Update x <- normalise(mean of the window) (Eq. 6-8, Sec. 3.2.1).
+ *   Seeds in rounds sized by OSOP (Eq. 19-21, Sec. 3.2.2-3.2.4), early
+ *   stopping at gamma (Sec. 3.2.3), prune/merge and labelling (Algorithm 2,
+ *   lines 10-12).
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are DEVICE pointers, h_* are HOST pointers; other
+ *    pointers to scalars (e.g. n_seeded_out) are host pointers.
+ *  - Device inputs passed to ms_create are BORROWED: the caller keeps them
+ *    alive and unchanged until ms_destroy. Every ms_ctx OWNS its workspace,
+ *    allocated in ms_create and freed by ms_destroy.
+ *  - Work is enqueued on the stream given to ms_create (NULL = legacy default
+ *    stream). Calls that return counts synchronise that stream.
+ *  - Errors: every call returns an ms_status; the library never aborts,
+ *    exits or prints. ms_last_error() gives a thread-local message for the
+ *    last failing call on the calling thread. After MS_ERR_CUDA the context
+ *    should be destroyed.
+ *  - A context is not thread safe; distinct contexts may be used from
+ *    distinct threads.
+ */
+#ifndef MS_H
+#define MS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MS_API __attribute__((visibility("default")))
+#else
+#define MS_API
+#endif
+
+typedef struct ms_ctx ms_ctx;
+typedef int32_t ms_status;
+
+#define MS_OK 0
+#define MS_ERR_INVALID_ARG 1   /* bad argument or input values (rejected before any work) */
+#define MS_ERR_CUDA 2          /* a CUDA call failed; see ms_last_error() */
+#define MS_ERR_OOM 3           /* device or pinned-host allocation failed */
+#define MS_ERR_NOT_CONVERGED 4 /* a round ended with no converged seed */
+#define MS_ERR_STATE 5         /* call out of order (e.g. ms_iterate before ms_seed_batch) */
+#define MS_ERR_TIMEOUT 6       /* a bounded device-side wait gave up */
+
+#define MS_FLAT 0 /* flat kernel, Eq. 11 */
+#define MS_VMF 1  /* smooth kernel exp(kappa * cos): only the ms_vmf_* calls */
+
+#define MS_FP32 0 /* plain FP32 SIMT similarity and sums */
+#define MS_BF16 1 /* BF16 tensor-core GEMMs with FP32 accumulation and an FP32 recheck band */
+
+#define MS_MAX_DIM 32
+
+/* Hyper-parameters; ms_config_default() fills the paper's values. */
+typedef struct ms_config {
+    int32_t dim;          /* embedding dimension d, 1..MS_MAX_DIM */
+    int32_t kernel;       /* MS_FLAT (MS_VMF is only for ms_vmf_*) */
+    double bandwidth_cos; /* c = 1 - h; default 0.9 (h = 0.1, Sec. 4.2/4.3) */
+    double kappa;         /* vMF concentration for MS_VMF */
+    double tol;           /* convergence ||x' - x||_2 < tol, evaluated in FP64; default 1e-6 */
+    int32_t max_iter;     /* iterations per round before the round is cut; default 300 */
+    int32_t n_initial;    /* N_initial = 128 (Sec. 3.2.4) */
+    double gamma;         /* early stop when #converged > gamma * N; 0.9 (Sec. 3.2.3) */
+    double L;             /* lower schedule bound (Eq. 21); 2 */
+    double H;             /* upper schedule bound; 8 (Sec. 3.2.4) */
+    double P_target;      /* P in Eq. 19; 0.99 */
+    double alpha;         /* Eq. 20; only used when L <= 0, then L = alpha / gamma */
+    double merge_cos;     /* modes closer than this cosine are merged; default = bandwidth_cos */
+    uint64_t seed;        /* seed-order permutation offset: SplitMix64(seed ^ frame_id) */
+    uint64_t frame_id;
+    int32_t precision;    /* MS_FP32 or MS_BF16 */
+    int32_t max_rounds;   /* guard on OSOP rounds; default 1000000 */
+    double eps_band;      /* BF16 recheck band half-width; 0 = the library's proven bound */
+    int32_t all_seeds;    /* 1 = Algorithm 1: every pixel seeds a single round, gamma = 1 */
+    int32_t reserved[7];  /* zero */
+} ms_config;
+
+/* Per-context counters, filled by ms_stats_get. */
+typedef struct ms_stats {
+    int32_t rounds;        /* OSOP rounds run */
+    int32_t n_modes;       /* modes kept */
+    int32_t iters_total;   /* iterations summed over rounds */
+    int32_t reserved0;
+    int64_t n_fg;          /* foreground pixels */
+    int64_t seeds;         /* seeds drawn */
+    int64_t seed_iters;    /* seed-iterations: one seed shifted once against all pixels */
+    int64_t candidates;    /* converged seeds offered to the merge */
+    int64_t dropped;       /* seeds not converged when their round ended (Sec. 3.2.3) */
+    int64_t band_pairs;    /* BF16 form: seed-pixel pairs rechecked in FP32 */
+    int64_t uncovered;     /* foreground pixels not yet covered */
+    int64_t workspace_bytes;
+    int64_t launches;      /* kernels launched by this context */
+    int64_t shift_launches;   /* shift-kernel launches that did work (profiling on) */
+    double shift_ms;       /* their summed CUDA-event time (profiling on) */
+} ms_stats;
+
+/* Fill *cfg with the paper's defaults (h = 0.1, gamma = 0.9, N_initial = 128,
+ * L = 2, H = 8, P = 0.99) for dimension 16 and MS_FP32. */
+MS_API void ms_config_default(ms_config* cfg);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+MS_API const char* ms_last_error(void);
+
+/* Device bytes ms_create would allocate for n_pixels pixels with cfg. */
+MS_API ms_status ms_workspace_bytes(const ms_config* cfg, int64_t n_pixels, int64_t* bytes_out);
+
+/* Bind a frame (the vector set S of Algorithm 2) and allocate the workspace.
+ * d_emb: device float32 [n_pixels, cfg->dim] row-major embeddings (any norm;
+ *        each foreground vector is normalised, Eq. 9). Borrowed.
+ * d_mask: device uint8 [n_pixels], nonzero = foreground; NULL = all
+ *        foreground. Borrowed.
+ * stream: a cudaStream_t (NULL for the legacy default stream).
+ * Enqueues normalisation and foreground compaction and synchronises.
+ * MS_ERR_INVALID_ARG for a bad cfg, n_pixels < 0 or >= 2^24, or a foreground
+ * vector with zero or non-finite norm (nothing is allocated then). */
+MS_API ms_status ms_create(const ms_config* cfg, const float* d_emb, const uint8_t* d_mask,
+                    int64_t n_pixels, void* stream, ms_ctx** out);
+
+/* Draw the next seed batch (Algorithm 2, line 2): the next n uncovered
+ * positions of the frame's fixed seed order pi(j) = (b + a j) mod n_fg.
+ * n_requested <= 0 uses the OSOP schedule's current N (Sec. 3.2.4).
+ * Drawn pixels count as covered. *n_seeded_out = 0 means every foreground
+ * pixel is covered. MS_ERR_STATE if a previous batch was not merged. */
+MS_API ms_status ms_seed_batch(ms_ctx* ctx, int32_t n_requested, int32_t* n_seeded_out);
+
+/* Shift the current batch in lockstep (Algorithm 2, lines 4-9) until more
+ * than gamma of it has converged, none is still moving, or max_iter
+ * (<= 0: cfg->max_iter) iterations; unconverged seeds are dropped
+ * (Sec. 3.2.3). MS_ERR_NOT_CONVERGED if no seed converged (the batch is still
+ * consumed). MS_ERR_STATE without a pending batch. */
+MS_API ms_status ms_iterate(ms_ctx* ctx, int32_t max_iter, int32_t* n_converged_out,
+                     int32_t* n_iters_out);
+
+/* Prune and merge the batch's converged modes into the kept set (Algorithm 2,
+ * line 11): in order of support (descending) then seed order, a mode is kept
+ * when its FP64 cosine to every kept mode is < merge_cos. Then marks pixels
+ * within c of a new mode as covered and updates N by Eq. 19-21.
+ * MS_ERR_STATE unless ms_iterate ran on the current batch. */
+MS_API ms_status ms_merge_modes(ms_ctx* ctx, int32_t* n_modes_out, int64_t* n_uncovered_out);
+
+/* Cluster every vector by its distance to the modes (Algorithm 2, lines
+ * 10-12): label = argmax_k cos(p_i, m_k), lowest k on ties, -1 for
+ * background. d_labels_out: device int32 [n_pixels], caller-owned.
+ * d_modes_out: device float32 [cap, dim] or NULL. MS_ERR_INVALID_ARG if
+ * d_modes_out is given and cap < the mode count (nothing written). */
+MS_API ms_status ms_label(ms_ctx* ctx, int32_t* d_labels_out, float* d_modes_out, int32_t cap,
+                   int32_t* n_modes_out);
+
+/* Free the workspace. Accepts NULL. */
+MS_API void ms_destroy(ms_ctx* ctx);
+
+/* The whole method for the bound frame: OSOP rounds (seed, iterate, merge)
+ * until every foreground pixel is covered or max_rounds, then ms_label. */
+MS_API ms_status ms_run(ms_ctx* ctx, int32_t* d_labels_out, float* d_modes_out, int32_t cap,
+                 int32_t* n_modes_out);
+
+/* Record CUDA events around every shift-kernel launch on the context's
+ * stream (enable = 1) so ms_stats reports its device time; off by default. */
+MS_API ms_status ms_profile(ms_ctx* ctx, int32_t enable);
+
+/* Counters of the context so far. */
+MS_API ms_status ms_stats_get(const ms_ctx* ctx, ms_stats* out);
+
+/* OSOP state carried across frames of a video (Sec. 4.3, Table 3): the seed
+ * count N the schedule will use for the next batch. */
+MS_API ms_status ms_get_state(const ms_ctx* ctx, int64_t* n_next_out);
+MS_API ms_status ms_set_state(ms_ctx* ctx, int64_t n_next);
+
+/* Copy an internal array to host memory for inspection (tests, debugging).
+ * what: MS_INSPECT_* below. Writes min(cap, available) elements to h_out and
+ * the available count to *count_out. Synchronises the stream. */
+#define MS_INSPECT_SEED_LOG 1  /* int32: foreground index of every seed in draw order */
+#define MS_INSPECT_MODES 2     /* float32 [K, dim]: kept modes in keep order */
+#define MS_INSPECT_SUPPORT 3   /* int32 [K]: window size of each kept mode */
+#define MS_INSPECT_COVERED 4   /* uint8 [n_fg]: coverage flags */
+#define MS_INSPECT_ROUND_LOG 5 /* int64 [rounds, 4]: N requested, seeds, modes kept, uncovered */
+#define MS_INSPECT_PIXELS 6    /* float32 [n_fg, dim]: normalised foreground */
+MS_API ms_status ms_inspect(const ms_ctx* ctx, int32_t what, void* h_out, int64_t cap,
+                     int64_t* count_out);
+
+/* The whole method on one frame held in HOST memory: copies h_emb and h_mask
+ * to the device, runs ms_create + ms_run, and copies labels (and modes, when
+ * h_modes is not NULL) back, all on `stream`; returns after the copies end.
+ * h_emb: float32 [n_pixels, cfg->dim]; h_mask: uint8 [n_pixels] or NULL;
+ * h_labels: int32 [n_pixels]; h_modes: float32 [cap, dim] or NULL. Pinned
+ * host buffers make the copies asynchronous. Allocates and frees its own
+ * device memory. stats_out (nullable) receives the run's counters. */
+MS_API ms_status ms_run_host(const ms_config* cfg, const float* h_emb, const uint8_t* h_mask,
+                             int64_t n_pixels, void* stream, int32_t* h_labels, float* h_modes,
+                             int32_t cap, int32_t* n_modes_out, ms_stats* stats_out);
+
+/* Check of the BF16 tensor-core shift tile (Eq. 11 window, Eq. 8 sums) on
+ * one work item: 128 seeds d_X [128, 16] (device, unit FP32) against n_pix
+ * pixels d_P [n_pix, 16] (device FP32, normalised inside) with bandwidth c.
+ * It runs the production kernel once and returns, in HOST buffers,
+ * h_S [128, n_pad] the raw similarity accumulator Xh.Ph + Xh.Pm + Xl.Ph
+ * (n_pad = n_pix rounded up to 128) and h_acc [128, 17] each seed's window
+ * sums (units of 2^-36) and window size. 1 <= n_pix <= 4096. Allocates and
+ * frees its own device memory; synchronises the device. */
+MS_API ms_status ms_tc_selftest(const float* d_X, const float* d_P, int32_t n_pix, double c, float* h_S,
+                                int64_t* h_acc);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MS_H */

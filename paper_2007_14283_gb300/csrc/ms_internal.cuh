@@ -1,0 +1,171 @@
+// Internal declarations shared by the libms translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ms.h"
+
+namespace ms {
+
+// Pixels and seeds are stored with their dimension padded by zeros to Dp = 16
+// or 32: padding changes no dot product or norm, and keeps rows 64/128-byte
+// aligned for vector loads.
+inline int padded_dim(int d) { return d <= 16 ? 16 : 32; }
+
+// FP32 similarity is decided directly when it clears the threshold by more
+// than kEpsF32; inside that band the decision is recomputed in FP64. For unit
+// vectors with d <= 32 the FP32 dot product, including the normalisation
+// error of both operands, is within 2.3e-6 of the exact value.
+constexpr float kEpsF32 = 1e-5f;
+
+constexpr int kShiftThreads = 128;
+constexpr int kSeedsPerThread = 2;
+constexpr int kSeedsPerTile = kShiftThreads * kSeedsPerThread;  // 256
+constexpr int kPixTile = 128;                                    // pixels per smem stage
+constexpr int kMergeCap = 32;  // stored higher-ranked conflicts per merge candidate
+
+enum SeedState : uint8_t { kMoving = 0, kConverged = 1, kFailed = 2 };
+enum CandState : uint8_t { kUndecided = 0, kKept = 1, kRemoved = 2 };
+
+// Device-resident control block of one frame.
+struct DevCounters {
+    int32_t n_active;    // seeds in the current iteration's active list
+    int32_t n_next;      // seeds still moving after this iteration
+    int32_t conv_new;    // converged during this iteration
+    int32_t conv_total;  // converged in this round
+    int32_t fail_total;  // empty windows in this round
+    int32_t done;        // round finished
+    int32_t iters;       // iterations run in this round
+    int32_t m_round;     // seeds in this round
+    int32_t status;      // nonzero: device-side input error
+    int32_t n_seeded;    // seeds drawn by the last selection
+    int32_t cursor;      // next seed-order position
+    int32_t drawn;       // seeds drawn over all rounds
+    int32_t n_kept;      // kept modes
+    int32_t n_cand;      // merge candidates
+    int32_t undecided;   // merge candidates still undecided
+    int32_t n_uncovered; // foreground pixels not covered
+    int32_t n_fg;        // foreground pixels
+    int32_t pad;
+    int64_t seed_iters;  // seed-iterations summed
+    int64_t band_pairs;  // BF16 form: pairs rechecked in FP32
+};
+
+// Work split of one shift iteration: seed tiles x pixel chunks.
+struct ShiftSplit {
+    int tiles, chunks, chunk_len;
+};
+
+__host__ __device__ inline ShiftSplit shift_split(int n_active, int n, int target_items) {
+    ShiftSplit s;
+    s.tiles = (n_active + kSeedsPerTile - 1) / kSeedsPerTile;
+    if (s.tiles == 0 || n == 0) {
+        s.chunks = 0;
+        s.chunk_len = kPixTile;
+        return s;
+    }
+    int max_chunks = (n + kPixTile - 1) / kPixTile;
+    int ch = (target_items + s.tiles - 1) / s.tiles;
+    ch = ch < 1 ? 1 : (ch > max_chunks ? max_chunks : ch);
+    int per = (n + ch - 1) / ch;
+    per = (per + kPixTile - 1) / kPixTile * kPixTile;
+    s.chunk_len = per;
+    s.chunks = (n + per - 1) / per;
+    return s;
+}
+
+}  // namespace ms
+
+struct ms_ctx {
+    ms_config cfg;
+    int d, Dp;
+    cudaStream_t stream;
+    const float* emb;
+    const uint8_t* mask;
+    int64_t n_pixels;
+    int64_t n;          // foreground count
+    int64_t perm_a, perm_b;
+    int num_sms;
+    int shift_grid;     // persistent grid of the shift kernel
+    int target_items;   // work items per shift iteration
+    // workspace (one allocation)
+    void* ws;
+    size_t ws_bytes;
+    float* P32;          // [n_pixels, Dp] normalised foreground
+    int32_t* pix;        // [n_pixels] foreground index -> pixel index
+    uint8_t* covered;    // [n_pixels]
+    float* X;            // [n_pixels, Dp] seed positions by slot
+    int32_t* seed_pix;   // [n_pixels]
+    int32_t* seed_order; // [n_pixels]
+    uint8_t* sstate;     // [n_pixels]
+    int32_t* support;    // [n_pixels]
+    int32_t* active[2];  // [n_pixels] each
+    int32_t* seed_log;   // [n_pixels]
+    unsigned long long* acc;  // [n_pixels, Dp + 1] fixed-point window sums and counts (2^-36 units)
+    float* modes;        // [n_pixels, Dp] kept modes
+    int32_t* mode_support;
+    int32_t* cand;       // [n_pixels] candidate slots
+    int32_t* cand_rank;  // [n_pixels]
+    int32_t* rank_cand;  // [n_pixels] inverse of cand_rank
+    uint8_t* cand_state; // [n_pixels]
+    int32_t* conf_deg;   // [n_pixels]
+    int32_t* conf;       // [n_pixels * kMergeCap]
+    int32_t* block_tmp;  // ingest scan scratch
+    ms::DevCounters* dc;
+    ms::DevCounters* hc; // pinned host mirror
+    int64_t* round_log;  // host [cap * 4]
+    int64_t round_log_cap;
+    // host-side OSOP state
+    int phase;           // 0 idle, 1 seeded, 2 iterated
+    int64_t N;           // seed count for the next batch
+    int64_t uncovered;
+    int32_t n_kept;
+    int32_t m_round;
+    ms_stats stats;
+    // BF16 tensor-core form
+    void* Pk;            // [n_pad, 64] bf16: [Ph | Pm | Pl | 0] per pixel
+    int64_t n_pad;       // n rounded up to 128 (0 when n = 0)
+    CUtensorMap pmap;    // TMA map of Pk: boxes of 128 rows x 128 bytes, 128-byte swizzle
+    int tc_grid;         // persistent grid of the tensor-core shift kernel
+    // measurement
+    bool prof;
+    cudaEvent_t ev[64];  // start/end pairs around shift launches of one batch
+    int64_t launches;
+};
+
+namespace ms {
+
+// Error plumbing (ms_api.cu).
+ms_status set_error(ms_status code, const char* fmt, ...);
+ms_status cuda_check(cudaError_t e, const char* what);
+#define MS_CUDA(call)                                                 \
+    do {                                                              \
+        ms_status _s = ::ms::cuda_check((call), #call);               \
+        if (_s != MS_OK) return _s;                                   \
+    } while (0)
+#define MS_LAUNCH(what)                                               \
+    do {                                                              \
+        ms_status _s = ::ms::cuda_check(cudaGetLastError(), what);    \
+        if (_s != MS_OK) return _s;                                   \
+    } while (0)
+
+// Kernel launchers. Each enqueues on ctx->stream and returns MS_OK or MS_ERR_CUDA.
+ms_status launch_ingest(ms_ctx* ctx);                       // ms_ingest.cu
+ms_status launch_seed_select(ms_ctx* ctx, int32_t want);    // ms_seed.cu
+ms_status launch_shift_iteration(ms_ctx* ctx, int t, int max_iter, cudaEvent_t e0, cudaEvent_t e1);  // ms_shift_fp32.cu
+float ceil_to_float(double c);  // smallest float >= c
+ms_status launch_merge_prepare(ms_ctx* ctx, int32_t k);     // ms_merge.cu
+ms_status launch_merge_resolve(ms_ctx* ctx, int32_t k, int sweeps);
+ms_status launch_merge_sequential(ms_ctx* ctx, int32_t k);
+ms_status launch_merge_append(ms_ctx* ctx, int32_t k);
+ms_status launch_cover(ms_ctx* ctx, int32_t k0, int32_t k1);
+ms_status launch_label(ms_ctx* ctx, int32_t* d_labels);     // ms_label.cu
+ms_status launch_collect(ms_ctx* ctx);                      // ms_merge.cu
+int shift_blocks_per_sm();                                  // ms_shift_fp32.cu
+ms_status tc_prepare(ms_ctx* ctx);                          // ms_shift_tc.cu
+ms_status launch_shift_tc(ms_ctx* ctx, const int32_t* active, int grid, int target_items, float* dbg_S);
+int tc_smem_bytes();
+
+}  // namespace ms

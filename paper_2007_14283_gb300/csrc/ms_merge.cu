@@ -1,0 +1,398 @@
+// Prune/merge of converged modes (Algorithm 2, line 11) and OSOP coverage.
+//
+// Merge rule: candidates (the round's converged seeds) are visited in order of
+// support descending, then seed order ascending; a candidate is kept when its
+// cosine to every mode kept so far is < merge_cos. Each decision is the FP64
+// one: FP32 dot products decide pairs that clear the threshold by more than
+// kEpsF32 and the rest are recomputed in FP64.
+//
+// The sequential greedy is evaluated in parallel as the lexicographically
+// first independent set of the conflict graph: candidates that conflict with a
+// previously kept mode are removed up front; then, sweep by sweep, a candidate
+// is removed as soon as a higher-ranked conflicting candidate is kept, and kept
+// as soon as every higher-ranked conflicting candidate is removed. This fixed
+// point equals the sequential greedy result; a single-warp sequential pass
+// finishes any candidates still undecided after a bounded number of sweeps.
+#include "ms_device.cuh"
+
+namespace ms {
+namespace {
+
+constexpr int kMT = 128;  // threads per merge block
+constexpr int kVT = 64;   // vectors per shared-memory tile
+
+__global__ void k_collect(const uint8_t* __restrict__ sstate, int m, int32_t* __restrict__ cand,
+                          DevCounters* dc) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool c = s < m && sstate[s] == kConverged;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned b = __ballot_sync(0xffffffffu, c);
+    int base = 0;
+    if (lane == 0 && b) base = atomicAdd(&dc->n_cand, __popc(b));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (c) cand[base + __popc(b & ((1u << lane) - 1u))] = s;
+}
+
+__global__ void k_rank(const int32_t* __restrict__ cand, int k, const int32_t* __restrict__ support,
+                       const int32_t* __restrict__ order, int32_t* __restrict__ cand_rank,
+                       int32_t* __restrict__ rank_cand) {
+    __shared__ int32_t s_sup[256], s_ord[256];
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    int sa = 0, oa = 0;
+    if (a < k) {
+        sa = support[cand[a]];
+        oa = order[cand[a]];
+    }
+    int r = 0;
+    for (int base = 0; base < k; base += 256) {
+        const int b = base + threadIdx.x;
+        if (b < k) {
+            s_sup[threadIdx.x] = support[cand[b]];
+            s_ord[threadIdx.x] = order[cand[b]];
+        }
+        __syncthreads();
+        const int lim = min(256, k - base);
+        for (int j = 0; j < lim; ++j)
+            r += (s_sup[j] > sa) || (s_sup[j] == sa && s_ord[j] < oa);
+        __syncthreads();
+    }
+    if (a < k) {
+        cand_rank[a] = r;
+        rank_cand[r] = a;
+    }
+}
+
+template <int Dp>
+__device__ __forceinline__ void load_vec(float* dst, const float* src) {
+#pragma unroll
+    for (int k = 0; k < Dp; k += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(src + k);
+        dst[k] = v.x; dst[k + 1] = v.y; dst[k + 2] = v.z; dst[k + 3] = v.w;
+    }
+}
+
+// Candidates within merge_cos of a mode kept in an earlier round are removed.
+template <int Dp>
+__global__ void __launch_bounds__(kMT)
+k_merge_old(const float* __restrict__ X, const int32_t* __restrict__ cand, int k,
+            const float* __restrict__ modes, int K_old, float thr_f, double thr,
+            uint8_t* __restrict__ cand_state) {
+    __shared__ __align__(16) float tile[kVT * Dp];
+    const int a = blockIdx.x * kMT + threadIdx.x;
+    float x[Dp];
+    if (a < k) load_vec<Dp>(x, X + (int64_t)cand[a] * Dp);
+    bool removed = false;
+    for (int base = 0; base < K_old; base += kVT) {
+        const int cnt = min(kVT, K_old - base);
+        for (int q = threadIdx.x; q < cnt * Dp; q += kMT) tile[q] = modes[(int64_t)base * Dp + q];
+        __syncthreads();
+        if (a < k && !removed) {
+            for (int j = 0; j < cnt; ++j)
+                if (cos_at_least<Dp>(x, tile + j * Dp, thr_f, thr)) {
+                    removed = true;
+                    break;
+                }
+        }
+        __syncthreads();
+    }
+    if (a < k) cand_state[a] = removed ? kRemoved : kUndecided;
+}
+
+// Higher-ranked conflicting candidates of each undecided candidate: the first
+// kMergeCap are stored, conf_deg counts all of them.
+template <int Dp>
+__global__ void __launch_bounds__(kMT)
+k_merge_pairs(const float* __restrict__ X, const int32_t* __restrict__ cand, int k,
+              const int32_t* __restrict__ cand_rank, const uint8_t* __restrict__ cand_state,
+              float thr_f, double thr, int32_t* __restrict__ conf_deg, int32_t* __restrict__ conf) {
+    __shared__ __align__(16) float tile[kVT * Dp];
+    __shared__ int32_t s_rank[kVT];
+    __shared__ uint8_t s_state[kVT];
+    const int a = blockIdx.x * kMT + threadIdx.x;
+    const bool act = a < k && cand_state[a] == kUndecided;
+    const int ra = a < k ? cand_rank[a] : 0;
+    float x[Dp];
+    if (act) load_vec<Dp>(x, X + (int64_t)cand[a] * Dp);
+    int deg = 0;
+    for (int base = 0; base < k; base += kVT) {
+        const int cnt = min(kVT, k - base);
+        for (int q = threadIdx.x; q < cnt * Dp; q += kMT) {
+            const int j = q / Dp, kk = q - j * Dp;
+            tile[q] = X[(int64_t)cand[base + j] * Dp + kk];
+        }
+        for (int j = threadIdx.x; j < cnt; j += kMT) {
+            s_rank[j] = cand_rank[base + j];
+            s_state[j] = cand_state[base + j];
+        }
+        __syncthreads();
+        if (act) {
+            for (int j = 0; j < cnt; ++j) {
+                if (s_rank[j] >= ra || s_state[j] == kRemoved) continue;
+                if (cos_at_least<Dp>(x, tile + j * Dp, thr_f, thr)) {
+                    if (deg < kMergeCap) conf[(int64_t)a * kMergeCap + deg] = base + j;
+                    ++deg;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (a < k) conf_deg[a] = act ? deg : 0;
+}
+
+template <int Dp>
+__global__ void __launch_bounds__(kMT)
+k_merge_resolve(const float* __restrict__ X, const int32_t* __restrict__ cand, int k,
+                const int32_t* __restrict__ cand_rank, uint8_t* cand_state,
+                const int32_t* __restrict__ conf_deg, const int32_t* __restrict__ conf,
+                float thr_f, double thr, DevCounters* dc) {
+    const int a = blockIdx.x * kMT + threadIdx.x;
+    if (a >= k) return;
+    volatile uint8_t* st = cand_state;
+    if (st[a] != kUndecided) return;
+    const int deg = conf_deg[a];
+    bool any_kept = false, all_removed = true;
+    if (deg <= kMergeCap) {
+        for (int j = 0; j < deg; ++j) {
+            const uint8_t s = st[conf[(int64_t)a * kMergeCap + j]];
+            if (s == kKept) {
+                any_kept = true;
+                break;
+            }
+            if (s == kUndecided) all_removed = false;
+        }
+    } else {
+        float x[Dp];
+        load_vec<Dp>(x, X + (int64_t)cand[a] * Dp);
+        const int ra = cand_rank[a];
+        for (int b = 0; b < k; ++b) {
+            if (cand_rank[b] >= ra) continue;
+            const uint8_t s = st[b];
+            if (s == kRemoved) continue;
+            if (!cos_at_least<Dp>(x, X + (int64_t)cand[b] * Dp, thr_f, thr)) continue;
+            if (s == kKept) {
+                any_kept = true;
+                break;
+            }
+            all_removed = false;
+        }
+    }
+    if (any_kept)
+        st[a] = kRemoved;
+    else if (all_removed)
+        st[a] = kKept;
+    else
+        atomicAdd(&dc->undecided, 1);
+}
+
+// Exact sequential greedy for whatever is still undecided (one warp).
+template <int Dp>
+__global__ void k_merge_sequential(const float* __restrict__ X, const int32_t* __restrict__ cand,
+                                   int k, const int32_t* __restrict__ rank_cand, uint8_t* cand_state,
+                                   float thr_f, double thr) {
+    volatile uint8_t* st = cand_state;
+    const int lane = threadIdx.x;
+    for (int r = 0; r < k; ++r) {
+        const int a = rank_cand[r];
+        if (st[a] != kUndecided) continue;
+        const float* xa = X + (int64_t)cand[a] * Dp;
+        bool hit = false;
+        for (int rb = lane; rb < r && !hit; rb += 32) {
+            const int b = rank_cand[rb];
+            if (st[b] == kKept && cos_at_least<Dp>(xa, X + (int64_t)cand[b] * Dp, thr_f, thr)) hit = true;
+        }
+        const bool any = __any_sync(0xffffffffu, hit);
+        if (lane == 0) st[a] = any ? kRemoved : kKept;
+        __syncwarp();
+    }
+}
+
+// Kept candidates are appended to the mode list in rank order.
+template <int Dp>
+__global__ void __launch_bounds__(1024)
+k_merge_append(const float* __restrict__ X, const int32_t* __restrict__ cand,
+               const int32_t* __restrict__ rank_cand, int k, const uint8_t* __restrict__ cand_state,
+               const int32_t* __restrict__ support, float* __restrict__ modes,
+               int32_t* __restrict__ mode_support, DevCounters* dc) {
+    __shared__ int32_t warp_excl[32];
+    __shared__ int32_t s_total;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int base = dc->n_kept;
+    int carry = 0;
+    for (int r0 = 0; r0 < k; r0 += 1024) {
+        const int r = r0 + tid;
+        const int a = r < k ? rank_cand[r] : -1;
+        const bool flag = a >= 0 && cand_state[a] == kKept;
+        const unsigned bal = __ballot_sync(0xffffffffu, flag);
+        if (lane == 0) warp_excl[wid] = __popc(bal);
+        __syncthreads();
+        if (wid == 0) {
+            const int w = warp_excl[lane];
+            int incl = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            warp_excl[lane] = incl - w;
+            if (lane == 31) s_total = incl;
+        }
+        __syncthreads();
+        if (flag) {
+            const int dst = base + carry + warp_excl[wid] + __popc(bal & ((1u << lane) - 1u));
+            const int slot = cand[a];
+            const float4* src = reinterpret_cast<const float4*>(X + (int64_t)slot * Dp);
+            float4* out = reinterpret_cast<float4*>(modes + (int64_t)dst * Dp);
+            for (int q = 0; q < Dp / 4; ++q) out[q] = src[q];
+            mode_support[dst] = support[slot];
+        }
+        carry += s_total;
+        __syncthreads();
+    }
+    if (tid == 0) dc->n_kept = base + carry;
+}
+
+// Coverage (OSOP stop rule): an uncovered pixel is covered once some new mode
+// has cos >= c. FP32 decides pairs outside the band; inside it the cosine is
+// recomputed in FP64 from the raw embedding.
+template <int Dp>
+__global__ void __launch_bounds__(256)
+k_cover(const float* __restrict__ P32, const float* __restrict__ emb, int d,
+        const int32_t* __restrict__ pix, int n, uint8_t* __restrict__ covered,
+        const float* __restrict__ modes, int k0, int k1, float c_f, double c, DevCounters* dc) {
+    __shared__ __align__(16) float tile[kVT * Dp];
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    const bool act = i < n && covered[i] == 0;
+    float p[Dp];
+    if (act) load_vec<Dp>(p, P32 + (int64_t)i * Dp);
+    bool cov = false, band = false;
+    for (int base = k0; base < k1; base += kVT) {
+        const int cnt = min(kVT, k1 - base);
+        for (int q = threadIdx.x; q < cnt * Dp; q += 256) tile[q] = modes[(int64_t)base * Dp + q];
+        __syncthreads();
+        if (act && !cov) {
+            for (int j = 0; j < cnt; ++j) {
+                const float s = dot_seq<Dp>(p, tile + j * Dp);
+                if (s >= c_f + kEpsF32) {
+                    cov = true;
+                    break;
+                }
+                if (s >= c_f - kEpsF32) band = true;
+            }
+        }
+        __syncthreads();
+    }
+    if (act && !cov && band) {
+        const float* e = emb + (int64_t)pix[i] * d;
+        for (int j = k0; j < k1 && !cov; ++j) {
+            const float* m = modes + (int64_t)j * Dp;
+            if (dot_seq<Dp>(p, m) >= c_f - kEpsF32 && cos64(e, m, d) >= c) cov = true;
+        }
+    }
+    if (act && cov) covered[i] = 1;
+    const int newly = __syncthreads_count(act && cov);
+    if (threadIdx.x == 0 && newly) atomicSub(&dc->n_uncovered, newly);
+}
+
+template <int Dp>
+ms_status merge_prepare_t(ms_ctx* ctx, int32_t k) {
+    const float thr_f = (float)ctx->cfg.merge_cos;
+    const double thr = ctx->cfg.merge_cos;
+    const unsigned g256 = (unsigned)((k + 255) / 256), gm = (unsigned)((k + kMT - 1) / kMT);
+    k_rank<<<g256, 256, 0, ctx->stream>>>(ctx->cand, k, ctx->support, ctx->seed_order, ctx->cand_rank,
+                                          ctx->rank_cand);
+    MS_LAUNCH("k_rank");
+    k_merge_old<Dp><<<gm, kMT, 0, ctx->stream>>>(ctx->X, ctx->cand, k, ctx->modes, ctx->n_kept, thr_f,
+                                                 thr, ctx->cand_state);
+    MS_LAUNCH("k_merge_old");
+    k_merge_pairs<Dp><<<gm, kMT, 0, ctx->stream>>>(ctx->X, ctx->cand, k, ctx->cand_rank, ctx->cand_state,
+                                                   thr_f, thr, ctx->conf_deg, ctx->conf);
+    MS_LAUNCH("k_merge_pairs");
+    ctx->launches += 3;
+    return MS_OK;
+}
+
+}  // namespace
+
+ms_status launch_collect(ms_ctx* ctx) {
+    MS_CUDA(cudaMemsetAsync(&ctx->dc->n_cand, 0, sizeof(int32_t), ctx->stream));
+    if (ctx->m_round <= 0) return MS_OK;
+    k_collect<<<(unsigned)((ctx->m_round + 255) / 256), 256, 0, ctx->stream>>>(ctx->sstate, ctx->m_round,
+                                                                             ctx->cand, ctx->dc);
+    MS_LAUNCH("k_collect");
+    ctx->launches += 1;
+    return MS_OK;
+}
+
+ms_status launch_merge_prepare(ms_ctx* ctx, int32_t k) {
+    if (k <= 0) return MS_OK;
+    return ctx->Dp == 16 ? merge_prepare_t<16>(ctx, k) : merge_prepare_t<32>(ctx, k);
+}
+
+ms_status launch_merge_resolve(ms_ctx* ctx, int32_t k, int sweeps) {
+    if (k <= 0) return MS_OK;
+    const float thr_f = (float)ctx->cfg.merge_cos;
+    const double thr = ctx->cfg.merge_cos;
+    const unsigned gm = (unsigned)((k + kMT - 1) / kMT);
+    for (int s = 0; s < sweeps; ++s) {
+        MS_CUDA(cudaMemsetAsync(&ctx->dc->undecided, 0, sizeof(int32_t), ctx->stream));
+        if (ctx->Dp == 16)
+            k_merge_resolve<16><<<gm, kMT, 0, ctx->stream>>>(ctx->X, ctx->cand, k, ctx->cand_rank,
+                                                             ctx->cand_state, ctx->conf_deg, ctx->conf,
+                                                             thr_f, thr, ctx->dc);
+        else
+            k_merge_resolve<32><<<gm, kMT, 0, ctx->stream>>>(ctx->X, ctx->cand, k, ctx->cand_rank,
+                                                             ctx->cand_state, ctx->conf_deg, ctx->conf,
+                                                             thr_f, thr, ctx->dc);
+        MS_LAUNCH("k_merge_resolve");
+        ctx->launches += 1;
+    }
+    return MS_OK;
+}
+
+ms_status launch_merge_sequential(ms_ctx* ctx, int32_t k) {
+    if (k <= 0) return MS_OK;
+    const float thr_f = (float)ctx->cfg.merge_cos;
+    const double thr = ctx->cfg.merge_cos;
+    if (ctx->Dp == 16)
+        k_merge_sequential<16><<<1, 32, 0, ctx->stream>>>(ctx->X, ctx->cand, k, ctx->rank_cand,
+                                                          ctx->cand_state, thr_f, thr);
+    else
+        k_merge_sequential<32><<<1, 32, 0, ctx->stream>>>(ctx->X, ctx->cand, k, ctx->rank_cand,
+                                                          ctx->cand_state, thr_f, thr);
+    MS_LAUNCH("k_merge_sequential");
+    ctx->launches += 1;
+    return MS_OK;
+}
+
+ms_status launch_merge_append(ms_ctx* ctx, int32_t k) {
+    if (k <= 0) return MS_OK;
+    if (ctx->Dp == 16)
+        k_merge_append<16><<<1, 1024, 0, ctx->stream>>>(ctx->X, ctx->cand, ctx->rank_cand, k,
+                                                        ctx->cand_state, ctx->support, ctx->modes,
+                                                        ctx->mode_support, ctx->dc);
+    else
+        k_merge_append<32><<<1, 1024, 0, ctx->stream>>>(ctx->X, ctx->cand, ctx->rank_cand, k,
+                                                        ctx->cand_state, ctx->support, ctx->modes,
+                                                        ctx->mode_support, ctx->dc);
+    MS_LAUNCH("k_merge_append");
+    ctx->launches += 1;
+    return MS_OK;
+}
+
+ms_status launch_cover(ms_ctx* ctx, int32_t k0, int32_t k1) {
+    if (k1 <= k0 || ctx->n == 0) return MS_OK;
+    const float c_f = (float)ctx->cfg.bandwidth_cos;
+    const unsigned g = (unsigned)((ctx->n + 255) / 256);
+    if (ctx->Dp == 16)
+        k_cover<16><<<g, 256, 0, ctx->stream>>>(ctx->P32, ctx->emb, ctx->d, ctx->pix, (int)ctx->n,
+                                                ctx->covered, ctx->modes, k0, k1, c_f,
+                                                ctx->cfg.bandwidth_cos, ctx->dc);
+    else
+        k_cover<32><<<g, 256, 0, ctx->stream>>>(ctx->P32, ctx->emb, ctx->d, ctx->pix, (int)ctx->n,
+                                                ctx->covered, ctx->modes, k0, k1, c_f,
+                                                ctx->cfg.bandwidth_cos, ctx->dc);
+    MS_LAUNCH("k_cover");
+    ctx->launches += 1;
+    return MS_OK;
+}
+
+}  // namespace ms

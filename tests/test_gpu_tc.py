@@ -1,0 +1,110 @@
+"""The BF16 tensor-core shift tile (tcgen05 GEMM1 -> mask -> tcgen05 GEMM2)
+against a numpy reconstruction of the same split arithmetic, and the BF16
+form of the whole method against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity_util import matched_agreement, mode_errors, same_order_errors
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16(a):
+    """Round float32 to bfloat16 (nearest even), returned as float32."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def unit(rng, n, d=16):
+    v = rng.standard_normal((n, d))
+    return (v / np.linalg.norm(v, axis=1, keepdims=True)).astype(np.float32)
+
+
+@pytest.mark.parametrize("n_pix", [128, 200, 640])
+def test_tc_tile_products_and_sums(ms_lib, n_pix):
+    import torch
+    rng = np.random.default_rng(n_pix)
+    # pixels in a few tight clusters so windows are non-trivial
+    centres = unit(rng, 4)
+    P = np.concatenate([synth.sample_vmf(rng, centres[i % 4], 60.0, 1) for i in range(n_pix)]).astype(np.float32)
+    X = P[rng.choice(n_pix, 128, replace=n_pix < 128)].copy()
+    X[:7] = unit(rng, 7)  # a few seeds with tiny windows
+    c = 0.9
+    S, acc = ms_lib.ms_tc_selftest(torch.from_numpy(X).cuda(), torch.from_numpy(P).cuda(), c)
+    # the library normalises pixels in FP32; rebuild exactly that input
+    Pn = (P / np.sqrt((P.astype(np.float32) ** 2).sum(1, dtype=np.float32))[:, None]).astype(np.float32)
+    Xh = bf16(X); Xl = bf16(X - Xh)
+    Ph = bf16(Pn); Pm = bf16(Pn - Ph); Pl = bf16((Pn - Ph) - Pm)
+    S_ref = (Xh.astype(np.float64) @ Ph.T.astype(np.float64) + Xh.astype(np.float64) @ Pm.T.astype(np.float64)
+             + Xl.astype(np.float64) @ Ph.T.astype(np.float64))
+    got = S[:, :n_pix].astype(np.float64)
+    # tensor-core FP32 accumulation: observed max 2.9e-6 (IEEE sequential would be <= 48 * 2^-24)
+    assert np.abs(got - S_ref).max() <= 5e-6, np.abs(got - S_ref).max()
+    # padded pixels contribute nothing
+    assert np.all(S[:, n_pix:] == 0.0)
+    # window decisions equal the exact ones away from the boundary
+    exact = X.astype(np.float64) @ Pn.T.astype(np.float64)
+    inw = exact >= c
+    safe = np.abs(exact - c) > 1e-5
+    cnt = acc[:, 16]
+    Y = acc[:, :16].astype(np.float64) * 2.0 ** -36
+    split = (Ph.astype(np.float64) + Pm + Pl)
+    for r in range(128):
+        if not safe[r].all():
+            continue
+        assert cnt[r] == inw[r].sum(), r
+        assert np.abs(Y[r] - split[inw[r]].sum(0)).max() <= 1e-4 * max(1, cnt[r])
+    assert (cnt > 0).sum() >= 100
+
+
+def _run(ms, emb, mask=None, **cfg):
+    import torch
+    e = torch.from_numpy(np.ascontiguousarray(emb)).cuda()
+    m = None if mask is None else torch.from_numpy(np.ascontiguousarray(mask)).cuda()
+    res = ms.cluster(e, m, **cfg)
+    torch.cuda.synchronize()
+    return res.labels.cpu().numpy(), res.modes.cpu().numpy(), res.stats
+
+
+def test_bf16_c1_separable_exact(ms_lib):
+    f = synth.frame_c1_separable(seed=0)
+    ref = oracle.run(f.emb)
+    labels, modes, st = _run(ms_lib, f.emb, precision=ms_lib.MS_BF16)
+    assert modes.shape[0] == ref.modes.shape[0] == 8
+    assert same_order_errors(modes, ref.modes).max() <= 1e-5
+    assert np.array_equal(labels, ref.labels)
+    assert np.array_equal(st["seed_log"], ref.seed_log)
+    assert np.array_equal(st["round_log"], ref.round_log)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_bf16_c1_fragmented(ms_lib, seed):
+    f = synth.frame_c1(seed=seed)
+    ref = oracle.run(f.emb)
+    labels, modes, st = _run(ms_lib, f.emb, precision=ms_lib.MS_BF16)
+    assert mode_errors(modes, ref.modes).max() <= 1e-5
+    assert matched_agreement(ref.labels, labels) >= 0.999
+    assert st["band_pairs"] > 0
+
+
+def test_bf16_equals_fp32_form(ms_lib):
+    # identical window decisions: same seeds, rounds, modes count and labels
+    f = synth.make_frame(4, 96, 96, 16, 6000, 9, 600.0, 0.3, 40.0, 200.0, 0.02)
+    a = _run(ms_lib, f.emb, f.mask, precision=ms_lib.MS_FP32)
+    b = _run(ms_lib, f.emb, f.mask, precision=ms_lib.MS_BF16)
+    assert np.array_equal(a[2]["round_log"], b[2]["round_log"])
+    assert a[1].shape == b[1].shape
+    assert same_order_errors(a[1], b[1]).max() <= 1e-6
+    assert matched_agreement(a[0], b[0]) >= 0.999
+
+
+def test_bf16_masked_ragged(ms_lib):
+    f = synth.make_frame(21, 50, 50, 16, 1237, 5, 240.0, 0.3, 150.0, 200.0, 0.02)
+    ref = oracle.run(f.emb, f.mask)
+    labels, modes, st = _run(ms_lib, f.emb, f.mask, precision=ms_lib.MS_BF16)
+    assert (labels[f.mask == 0] == -1).all()
+    assert mode_errors(modes, ref.modes).max() <= 1e-5
+    assert matched_agreement(ref.labels, labels) >= 0.999

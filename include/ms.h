@@ -204,8 +204,8 @@ MS_API ms_status ms_run_host(const ms_config* cfg, const float* h_emb, const uin
  * one work item: 128 seeds d_X [128, 16] (device, unit FP32) against n_pix
  * pixels d_P [n_pix, 16] (device FP32, normalised inside) with bandwidth c.
  * It runs the production kernel once and returns, in HOST buffers,
- * h_S [128, n_pad] the raw similarity accumulator Xh.Ph + Xh.Pm + Xl.Ph
- * (n_pad = n_pix rounded up to 128) and h_acc [128, 17] each seed's window
+ * h_S [128, n_pad] the raw accumulator Xh.Ph + Xh.Pm + Xl.Ph - c (c rounded
+ * up to FP32; n_pad = n_pix rounded up to 128) and h_acc [128, 17] each seed's window
  * sums (units of 2^-36) and window size. 1 <= n_pix <= 4096. Allocates and
  * frees its own device memory; synchronises the device. */
 MS_API ms_status ms_tc_selftest(const float* d_X, const float* d_P, int32_t n_pix, double c, float* h_S,

@@ -1,24 +1,29 @@
 // Shift iteration, BF16 tensor-core form (Algorithm 2, lines 4-9; Eq. 6-8, 11).
 //
 // One work item = 128 seeds x a chunk of 128-pixel tiles. Per pixel tile:
-//   GEMM1  S = Xh.Ph^T + Xh.Pm^T + Xl.Ph^T   (tcgen05, BF16 in, FP32 in TMEM)
+//   GEMM1  S' = Xh.Ph + Xh.Pm + Xl.Ph - c       (4 tcgen05 MMAs, FP32 in TMEM)
 //          x = Xh + Xl and p = Ph + Pm + Pl are exact BF16 splits of the FP32
-//          vectors, so |S - x.p| <= 3 * 2^-18 + 48 * 2^-24 < 1.4e-5 for unit
-//          vectors.
-//   mask   S' = S - c; a pair is in the window when S' >= 0. Pairs with
-//          |S'| < kBand = 2^-15 are re-decided with the same sequential FP32
+//          vectors and -c is split into three BF16 terms against a ones
+//          column, so S' = x.p - c up to the dropped terms (<= 3 * 2^-18 =
+//          1.2e-5 for unit vectors) and the tensor cores' FP32 accumulation
+//          (measured <= 6e-6 against an exact reconstruction).
+//   mask   a pair is in the window when S' >= 0 (sign bit clear). Pairs with
+//          |S'| < kBand = 2^-14 are re-decided with the same sequential FP32
 //          dot product as the FP32 form, so every decision equals the FP32
-//          form's (the FP32 dot is itself within 1e-6 of x.p).
-//   GEMM2  Y += Mask . [Ph | Pm | Pl | 0] (tcgen05, mask 0/1 exact in BF16)
-// The seed-by-pixel matrix lives only in TMEM and registers. After the
-// item's last tile Y = Ph + Pm + Pl sums are added to the per-seed fixed-point
-// accumulators shared with the FP32 form, and the same finalize kernel
-// normalises the seeds and tests convergence in FP64.
+//          form's, whose dot product is within 1e-6 of x.p.
+//   GEMM2  Y += Mask . [Ph | Pm | Pl | 1]    (8 tcgen05 MMAs, mask exact in BF16;
+//          the ones column yields the window size)
+// The seed-by-pixel matrix lives only in TMEM, registers and a shared-memory
+// mask tile. After the item's last tile the Y sums are added to the per-seed
+// fixed-point accumulators shared with the FP32 form, and the same finalize
+// kernel normalises the seeds and tests convergence in FP64.
 //
-// Warp roles (192 threads, 2 CTAs per SM): warp 0 issues TMA loads of pixel
-// tiles into a 3-stage ring; warp 1 owns TMEM (256 columns: S at 0, Y at 128)
-// and issues the MMAs; warps 2-5 each own the 32 TMEM lanes (seeds) of their
-// quadrant and compute the mask. All waits are bounded; a timeout raises the
+// Warp roles (320 threads, one CTA per SM): warp 0 issues TMA loads of pixel
+// tiles into a 4-stage ring; warp 1 owns TMEM (512 columns: two S buffers and
+// Y) and issues MMAs, GEMM1 of tile g+1 before GEMM2 of tile g so the tensor
+// cores work while the mask of tile g is built; warps 2-9 build the mask, two
+// warps per 32-lane TMEM quadrant, 64 pixels each. Seed operands (A1) and
+// mask tiles are double-buffered. All waits are bounded; a timeout raises the
 // CTA's abort flag, drains what is in flight, frees TMEM and reports
 // MS_ERR_TIMEOUT through the frame's status word.
 #include <cudaTypedefs.h>
@@ -31,19 +36,19 @@ namespace {
 
 using namespace tc;
 
-constexpr int kTcThreads = 192;
-constexpr int kStages = 3;
-constexpr int kTileBytes = 128 * 128;        // 128 rows x 128 bytes
-constexpr uint32_t kTmemCols = 256;
-constexpr uint32_t kColS = 0, kColY = 128;
-constexpr float kBand = 3.0517578125e-05f;   // 2^-15
+constexpr int kTcThreads = 320;
+constexpr int kStages = 4;
+constexpr int kTileBytes = 128 * 128;  // 128 rows x 128 bytes
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kColY = 256;        // S buffers at columns 0 and 128
+constexpr float kBand = 6.103515625e-05f;    // 2^-14
 constexpr float kFixScale = 68719476736.0f;  // 2^36
 
-constexpr int kOffA1 = 0;
-constexpr int kOffP = kTileBytes;
-constexpr int kOffM = kOffP + kStages * kTileBytes;
-constexpr int kOffBar = kOffM + 2 * kTileBytes;
-constexpr int kNumBars = 2 * kStages + 8;
+constexpr int kOffA1 = 0;                              // 2 x 16 KB
+constexpr int kOffP = 2 * kTileBytes;                  // kStages x 16 KB
+constexpr int kOffM = kOffP + kStages * kTileBytes;    // 2 x 32 KB
+constexpr int kOffBar = kOffM + 4 * kTileBytes;
+constexpr int kNumBars = 2 * kStages + 14;
 constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 16 + 1024;  // + alignment slack
 
 struct TcSplit {
@@ -72,7 +77,54 @@ __device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity) {
         if (clock64() - t0 > kWaitCycles) return;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 2)
+// Bytes {0,1} = sign of a, {2,3} = sign of b, replicated: 0xFFFF per negative half.
+__device__ __forceinline__ uint32_t sign_halves(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, 0xFFBB;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+
+__device__ __forceinline__ void load_x16(const float* __restrict__ X, int slot, float (&x)[16]) {
+#pragma unroll
+    for (int k = 0; k < 16; k += 4) {
+        const float4 v = slot >= 0 ? *reinterpret_cast<const float4*>(X + (int64_t)slot * 16 + k)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+        x[k] = v.x; x[k + 1] = v.y; x[k + 2] = v.z; x[k + 3] = v.w;
+    }
+}
+
+// Row r of a seed operand tile: [Xh | Xl | -c split | 0], 128-byte swizzle.
+__device__ __forceinline__ void write_a1(uint8_t* A1, int r, const float (&x)[16], float c_f) {
+    uint32_t wh[8], wl[8];
+#pragma unroll
+    for (int k = 0; k < 16; k += 2) {
+        const float h0 = bf16_round(x[k]), h1 = bf16_round(x[k + 1]);
+        wh[k / 2] = pack_bf16(h0, h1);
+        wl[k / 2] = pack_bf16(x[k] - h0, x[k + 1] - h1);
+    }
+    const float c_hi = bf16_round(c_f);
+    const float c_mid = bf16_round(c_f - c_hi);
+    const float c_lo = (c_f - c_hi) - c_mid;
+    const uint32_t wc0 = pack_bf16(-c_hi, -c_mid), wc1 = pack_bf16(-c_lo, 0.f);
+    *reinterpret_cast<uint4*>(A1 + sw128_offset(r, 0)) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+    *reinterpret_cast<uint4*>(A1 + sw128_offset(r, 1)) = make_uint4(wh[4], wh[5], wh[6], wh[7]);
+    *reinterpret_cast<uint4*>(A1 + sw128_offset(r, 2)) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+    *reinterpret_cast<uint4*>(A1 + sw128_offset(r, 3)) = make_uint4(wl[4], wl[5], wl[6], wl[7]);
+    *reinterpret_cast<uint4*>(A1 + sw128_offset(r, 4)) = make_uint4(wc0, wc1, 0u, 0u);
+#pragma unroll
+    for (int cidx = 5; cidx < 8; ++cidx)
+        *reinterpret_cast<uint4*>(A1 + sw128_offset(r, cidx)) = make_uint4(0u, 0u, 0u, 0u);
+}
+
+struct Gemm2Job {
+    int g;       // CTA-local tile counter
+    int stage;   // pixel-tile stage
+    int it;      // CTA-local item counter
+    bool first, last;
+};
+
+template <bool kDebug>
+__global__ void __launch_bounds__(kTcThreads, 1)
 k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P32, int32_t n,
            int n_ptiles, const int32_t* __restrict__ active, const float* __restrict__ X,
            unsigned long long* __restrict__ acc, float c_f, int target_items, DevCounters* dc,
@@ -86,14 +138,14 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
     uint64_t* bars = (uint64_t*)(smem + kOffBar);
     uint64_t* full = bars;
     uint64_t* empty = bars + kStages;
-    uint64_t* s_full = bars + 2 * kStages + 0;
-    uint64_t* s_empty = bars + 2 * kStages + 1;
-    uint64_t* m_full = bars + 2 * kStages + 2;
-    uint64_t* m_empty = bars + 2 * kStages + 3;
-    uint64_t* a1_full = bars + 2 * kStages + 4;
-    uint64_t* d_full = bars + 2 * kStages + 5;
-    uint64_t* d_empty = bars + 2 * kStages + 6;
-    uint64_t* aux = bars + 2 * kStages + 7;
+    uint64_t* s_full = bars + 2 * kStages;       // [2]
+    uint64_t* s_empty = s_full + 2;              // [2]
+    uint64_t* m_full = s_empty + 2;              // [2]
+    uint64_t* m_empty = m_full + 2;              // [2]
+    uint64_t* a1_full = m_empty + 2;             // [2]
+    uint64_t* d_full = a1_full + 2;
+    uint64_t* d_empty = d_full + 1;
+    uint64_t* aux = d_empty + 1;
     uint32_t* tmem_slot = (uint32_t*)(bars + kNumBars);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
 
@@ -103,11 +155,13 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(s_full, 1);
-        mbar_init(s_empty, 128);
-        mbar_init(m_full, 128);
-        mbar_init(m_empty, 1);
-        mbar_init(a1_full, 128);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&s_full[b], 1);
+            mbar_init(&s_empty[b], 256);
+            mbar_init(&m_full[b], 256);
+            mbar_init(&m_empty[b], 1);
+            mbar_init(&a1_full[b], 128);
+        }
         mbar_init(d_full, 1);
         mbar_init(d_empty, 128);
         mbar_init(aux, 1);
@@ -147,160 +201,184 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t tS = tmem + kColS, tY = tmem + kColY;
-            const uint32_t a1 = smem_u32(A1), mt = smem_u32(Mt);
+            const uint32_t tY = tmem + kColY;
+            const uint32_t a1 = smem_u32(A1), mt = smem_u32(Mt), pst = smem_u32(Pst);
             constexpr uint32_t id1 = idesc_bf16(128, 128, 0, 0);
-            constexpr uint32_t id2 = idesc_bf16(128, 64, 0, 1);  // [Ph|Pm|Pl|0]: one 128-byte atom
-            int g = 0, it = 0;
+            constexpr uint32_t id2 = idesc_bf16(128, 64, 0, 1);
             bool ok = true;
+            bool pending = false;
+            Gemm2Job job{0, 0, 0, false, false};
+            auto gemm2 = [&](const Gemm2Job& j) -> bool {
+                if (!mbar_wait(&m_full[j.g & 1], (j.g >> 1) & 1, abort)) return false;
+                if (j.first && j.it > 0 && !mbar_wait(d_empty, (j.it - 1) & 1, abort)) return false;
+                tc_fence_after();
+                const uint32_t mb = mt + (j.g & 1) * 2 * kTileBytes;
+                const uint32_t pb = pst + j.stage * kTileBytes;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint64_t ad = desc_sw128(mb + (k >> 2) * kTileBytes + (k & 3) * 32, 16, 1024);
+                    const uint64_t bd = desc_sw128(pb + k * 2048, kTileBytes, 1024);
+                    mma_bf16(tY, ad, bd, id2, (j.first && k == 0) ? 0u : 1u);
+                }
+                mma_commit(&m_empty[j.g & 1]);
+                mma_commit(&empty[j.stage]);
+                if (j.last) mma_commit(d_full);
+                return true;
+            };
+            int g = 0, it = 0;
             for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
                 const int ch = item % sp.chunks;
                 const int pt0 = ch * sp.tpc, pt1 = min(n_ptiles, pt0 + sp.tpc);
-                if (!(ok = mbar_wait(a1_full, it & 1, abort))) break;
+                if (!(ok = mbar_wait(&a1_full[it & 1], (it >> 1) & 1, abort))) break;
+                const uint32_t a = a1 + (it & 1) * kTileBytes;
                 for (int pt = pt0; pt < pt1; ++pt, ++g) {
                     const int s = g % kStages;
                     if (!(ok = mbar_wait(&full[s], (g / kStages) & 1, abort))) break;
-                    if (g > 0 && !(ok = mbar_wait(s_empty, (g - 1) & 1, abort))) break;
+                    if (g >= 2 && !(ok = mbar_wait(&s_empty[g & 1], ((g >> 1) - 1) & 1, abort))) break;
                     tc_fence_after();
-                    const uint32_t pb = smem_u32(Pst + s * kTileBytes);
-                    mma_bf16(tS, desc_sw128(a1, 16, 1024), desc_sw128(pb, 16, 1024), id1, 0);
-                    mma_bf16(tS, desc_sw128(a1, 16, 1024), desc_sw128(pb + 32, 16, 1024), id1, 1);
-                    mma_bf16(tS, desc_sw128(a1 + 32, 16, 1024), desc_sw128(pb, 16, 1024), id1, 1);
-                    mma_commit(s_full);
-                    if (!(ok = mbar_wait(m_full, g & 1, abort))) break;
-                    if (pt == pt0 && it > 0 && !(ok = mbar_wait(d_empty, (it - 1) & 1, abort))) break;
-                    tc_fence_after();
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const uint64_t ad = desc_sw128(mt + (k >> 2) * kTileBytes + (k & 3) * 32, 16, 1024);
-                        const uint64_t bd = desc_sw128(pb + k * 2048, kTileBytes, 1024);
-                        mma_bf16(tY, ad, bd, id2, (pt > pt0 || k > 0) ? 1u : 0u);
-                    }
-                    mma_commit(m_empty);
-                    mma_commit(&empty[s]);
+                    const uint32_t tS = tmem + (g & 1) * 128;
+                    const uint32_t pb = pst + s * kTileBytes;
+                    mma_bf16(tS, desc_sw128(a, 16, 1024), desc_sw128(pb, 16, 1024), id1, 0);
+                    mma_bf16(tS, desc_sw128(a, 16, 1024), desc_sw128(pb + 32, 16, 1024), id1, 1);
+                    mma_bf16(tS, desc_sw128(a + 32, 16, 1024), desc_sw128(pb, 16, 1024), id1, 1);
+                    mma_bf16(tS, desc_sw128(a + 64, 16, 1024), desc_sw128(pb + 96, 16, 1024), id1, 1);
+                    mma_commit(&s_full[g & 1]);
+                    if (pending && !(ok = gemm2(job))) break;
+                    job = Gemm2Job{g, s, it, pt == pt0, pt == pt1 - 1};
+                    pending = true;
                 }
-                if (ok) mma_commit(d_full);
             }
+            if (ok && pending) ok = gemm2(job);
             if (*abort) {
                 mma_commit(aux);
                 drain_wait(aux, 0);
             }
         }
     } else {
-        // ------------------------------------------------ mask / epilogue warps
-        const int q = warp & 3;
-        const int r = q * 32 + lane;
+        // ------------------------------------------------ mask warps (2..9)
+        const int q = warp & 3;             // TMEM lane quadrant
+        const int h = (warp - 2) >> 2;      // which 64 pixels of a tile
+        const int r = q * 32 + lane;        // seed row
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        const uint32_t tS = tmem + kColS + lane_base, tY = tmem + kColY + lane_base;
         long long band_local = 0;
         int g = 0, it = 0;
+        float x[16];
         for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x, ++it) {
             const int t = item / sp.chunks, ch = item % sp.chunks;
             const int pt0 = ch * sp.tpc, pt1 = min(n_ptiles, pt0 + sp.tpc);
             const int pos = t * 128 + r;
             const int slot = pos < n_active ? active[pos] : -1;
-            float x[16];
-#pragma unroll
-            for (int k = 0; k < 16; k += 4) {
-                const float4 v = slot >= 0 ? *reinterpret_cast<const float4*>(X + (int64_t)slot * 16 + k)
-                                           : make_float4(0.f, 0.f, 0.f, 0.f);
-                x[k] = v.x; x[k + 1] = v.y; x[k + 2] = v.z; x[k + 3] = v.w;
-            }
-            // A1 row r: [Xh (16) | Xl (16) | 0 (32)], 128-byte swizzle. The
-            // previous item's MMAs are complete (d_full was awaited).
-            {
-                uint32_t wh[8], wl[8];
-#pragma unroll
-                for (int k = 0; k < 16; k += 2) {
-                    const float h0 = bf16_round(x[k]), h1 = bf16_round(x[k + 1]);
-                    wh[k / 2] = pack_bf16(h0, h1);
-                    wl[k / 2] = pack_bf16(x[k] - h0, x[k + 1] - h1);
+            load_x16(X, slot, x);
+            if (h == 0) {
+                // A1 for this item (first item only) and the next one; the next
+                // one's buffer was last read by item it-1, whose MMAs completed
+                // before d_full(it-1) was observed.
+                if (it == 0) {
+                    write_a1(A1, r, x, c_f);
+                    fence_proxy_async();
+                    mbar_arrive(&a1_full[0]);
                 }
-#pragma unroll
-                for (int cidx = 0; cidx < 8; ++cidx) {
-                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                    if (cidx == 0) v = make_uint4(wh[0], wh[1], wh[2], wh[3]);
-                    if (cidx == 1) v = make_uint4(wh[4], wh[5], wh[6], wh[7]);
-                    if (cidx == 2) v = make_uint4(wl[0], wl[1], wl[2], wl[3]);
-                    if (cidx == 3) v = make_uint4(wl[4], wl[5], wl[6], wl[7]);
-                    *reinterpret_cast<uint4*>(A1 + sw128_offset(r, cidx)) = v;
+                const int nitem = item + gridDim.x;
+                if (nitem < items) {
+                    const int npos = (nitem / sp.chunks) * 128 + r;
+                    float xn[16];
+                    load_x16(X, npos < n_active ? active[npos] : -1, xn);
+                    write_a1(A1 + ((it + 1) & 1) * kTileBytes, r, xn, c_f);
+                    fence_proxy_async();
+                    mbar_arrive(&a1_full[(it + 1) & 1]);
                 }
             }
-            fence_proxy_async();
-            mbar_arrive(a1_full);
-            int cnt = 0;
             for (int pt = pt0; pt < pt1; ++pt, ++g) {
-                if (!mbar_wait(s_full, g & 1, abort)) break;
-                if (g > 0 && !mbar_wait(m_empty, (g - 1) & 1, abort)) break;
+                const int b = g & 1;
+                if (!mbar_wait(&s_full[b], (g >> 1) & 1, abort)) break;
                 tc_fence_after();
-#pragma unroll 1
-                for (int cc = 0; cc < 4; ++cc) {
-                    uint32_t v[32];
-                    tmem_ld32(tS + cc * 32, v);
+                uint32_t v[64];
+                {
+                    uint32_t (&v0)[32] = *reinterpret_cast<uint32_t(*)[32]>(&v[0]);
+                    uint32_t (&v1)[32] = *reinterpret_cast<uint32_t(*)[32]>(&v[32]);
+                    const uint32_t ta = tmem + b * 128 + lane_base + h * 64;
+                    tmem_ld32(ta, v0);
+                    tmem_ld32(ta + 32, v1);
                     tmem_ld_wait();
-                    uint32_t bits = 0;
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const float sv = __uint_as_float(v[i]);
-                        const float sp_ = sv - c_f;
-                        bool in = sp_ >= 0.f;
-                        if (fabsf(sp_) < kBand) {
-                            const int px = pt * 128 + cc * 32 + i;
-                            if (px < n) {
-                                ++band_local;
-                                float pv[16];
-#pragma unroll
-                                for (int k = 0; k < 16; k += 4) {
-                                    const float4 w = *reinterpret_cast<const float4*>(P32 + (int64_t)px * 16 + k);
-                                    pv[k] = w.x; pv[k + 1] = w.y; pv[k + 2] = w.z; pv[k + 3] = w.w;
-                                }
-                                in = dot_seq<16>(x, pv) >= c_f;
-                            } else {
-                                in = false;
-                            }
-                        }
-                        bits |= (in ? 1u : 0u) << i;
-                        if (dbg_S) dbg_S[(int64_t)r * n_ptiles * 128 + pt * 128 + cc * 32 + i] = sv;
-                    }
-                    cnt += __popc(bits);
-                    // 32 mask values -> 16 words -> 4 chunks of 16 bytes
-                    const int blk = cc >> 1;
-#pragma unroll
-                    for (int c4 = 0; c4 < 4; ++c4) {
-                        uint32_t w[4];
-#pragma unroll
-                        for (int h = 0; h < 4; ++h) {
-                            const int b0 = c4 * 8 + h * 2;
-                            w[h] = (((bits >> b0) & 1u) ? 0x3F80u : 0u) | (((bits >> (b0 + 1)) & 1u) ? 0x3F800000u : 0u);
-                        }
-                        const int cidx = (cc & 1) * 4 + c4;
-                        *reinterpret_cast<uint4*>(Mt + blk * kTileBytes + sw128_offset(r, cidx)) =
-                            make_uint4(w[0], w[1], w[2], w[3]);
-                    }
                 }
                 tc_fence_before();
-                mbar_arrive(s_empty);
+                mbar_arrive(&s_empty[b]);
+                uint32_t w[32];
+                float mn = INFINITY;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    w[i] = ~sign_halves(v[2 * i], v[2 * i + 1]) & 0x3F803F80u;
+                    mn = fminf(mn, fminf(fabsf(__uint_as_float(v[2 * i])), fabsf(__uint_as_float(v[2 * i + 1]))));
+                }
+                if (mn < kBand) {
+                    // Re-decide near-boundary pairs with the FP32 form's dot
+                    // product. Bit masks keep every register-array index static.
+                    uint64_t bandm = 0;
+#pragma unroll
+                    for (int i = 0; i < 64; ++i)
+                        bandm |= (uint64_t)(fabsf(__uint_as_float(v[i])) < kBand) << i;
+                    uint64_t inm = 0, todo = bandm;
+                    while (todo) {
+                        const int i = __ffsll((long long)todo) - 1;
+                        todo &= todo - 1;
+                        const int px = pt * 128 + h * 64 + i;
+                        if (px < n) {
+                            ++band_local;
+                            float pv[16];
+#pragma unroll
+                            for (int k = 0; k < 16; k += 4) {
+                                const float4 u = *reinterpret_cast<const float4*>(P32 + (int64_t)px * 16 + k);
+                                pv[k] = u.x; pv[k + 1] = u.y; pv[k + 2] = u.z; pv[k + 3] = u.w;
+                            }
+                            if (dot_seq<16>(x, pv) >= c_f) inm |= 1ull << i;
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const uint32_t bm = (uint32_t)(bandm >> (2 * j)) & 3u;
+                        const uint32_t im = (uint32_t)(inm >> (2 * j)) & 3u;
+                        const uint32_t clear = ((bm & 1u) ? 0x3F80u : 0u) | ((bm & 2u) ? 0x3F800000u : 0u);
+                        const uint32_t set = ((im & 1u) ? 0x3F80u : 0u) | ((im & 2u) ? 0x3F800000u : 0u);
+                        w[j] = (w[j] & ~clear) | set;
+                    }
+                }
+                if (kDebug) {
+#pragma unroll
+                    for (int i = 0; i < 64; ++i)
+                        dbg_S[(int64_t)r * n_ptiles * 128 + pt * 128 + h * 64 + i] = __uint_as_float(v[i]);
+                }
+                if (g >= 2 && !mbar_wait(&m_empty[b], ((g >> 1) - 1) & 1, abort)) break;
+                uint8_t* mrow = Mt + b * 2 * kTileBytes + h * kTileBytes;
+#pragma unroll
+                for (int cidx = 0; cidx < 8; ++cidx)
+                    *reinterpret_cast<uint4*>(mrow + sw128_offset(r, cidx)) =
+                        make_uint4(w[4 * cidx], w[4 * cidx + 1], w[4 * cidx + 2], w[4 * cidx + 3]);
                 fence_proxy_async();
-                mbar_arrive(m_full);
+                mbar_arrive(&m_full[b]);
             }
             if (*abort) break;
-            if (!mbar_wait(d_full, it & 1, abort)) break;
-            tc_fence_after();
-            uint32_t h[16], m[16], l[16];
-            tmem_ld16(tY, h);
-            tmem_ld16(tY + 16, m);
-            tmem_ld16(tY + 32, l);
-            tmem_ld_wait();
-            tc_fence_before();
-            mbar_arrive(d_empty);
-            if (slot >= 0 && cnt > 0) {
-                unsigned long long* a = acc + (int64_t)slot * 17;
+            if (h == 0) {
+                if (!mbar_wait(d_full, it & 1, abort)) break;
+                tc_fence_after();
+                uint32_t yh[16], ym[16], yl[16], yc[16];
+                const uint32_t ty = tmem + kColY + lane_base;
+                tmem_ld16(ty, yh);
+                tmem_ld16(ty + 16, ym);
+                tmem_ld16(ty + 32, yl);
+                tmem_ld16(ty + 48, yc);
+                tmem_ld_wait();
+                tc_fence_before();
+                mbar_arrive(d_empty);
+                const float cntf = __uint_as_float(yc[0]);
+                if (slot >= 0 && cntf > 0.f) {
+                    unsigned long long* a = acc + (int64_t)slot * 17;
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const float y = __uint_as_float(h[k]) + __uint_as_float(m[k]) + __uint_as_float(l[k]);
-                    atomicAdd(a + k, (unsigned long long)__float2ll_rn(y * kFixScale));
+                    for (int k = 0; k < 16; ++k) {
+                        const float y = __uint_as_float(yh[k]) + __uint_as_float(ym[k]) + __uint_as_float(yl[k]);
+                        atomicAdd(a + k, (unsigned long long)__float2ll_rn(y * kFixScale));
+                    }
+                    atomicAdd(a + 16, (unsigned long long)__float2ll_rn(cntf));
                 }
-                atomicAdd(a + 16, (unsigned long long)cnt);
             }
         }
         if (band_local) atomicAdd((unsigned long long*)&dc->band_pairs, (unsigned long long)band_local);
@@ -312,8 +390,9 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
     if (threadIdx.x == 0 && *abort) atomicOr(&dc->status, 2);
 }
 
-// Pixels as BF16 splits for the tensor cores: row i = [Ph | Pm | Pl | 0]
-// (64 values, 128 bytes) with p = Ph + Pm + Pl; rows n..n_pad-1 are zero.
+// Pixels as BF16 splits for the tensor cores: row i = [Ph | Pm | Pl | 1 1 1 0..0]
+// (64 values, 128 bytes) with p = Ph + Pm + Pl; padding rows n..n_pad-1 hold
+// only the ones, so they score S' = -c and never enter a window.
 __global__ void k_pack_bf16(const float* __restrict__ P32, int n, int n_pad, uint4* __restrict__ Pk) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_pad) return;
@@ -331,6 +410,8 @@ __global__ void k_pack_bf16(const float* __restrict__ P32, int n, int n_pad, uin
             w[16 + k / 2] = pack_bf16((p0 - h0) - m0, (p1 - h1) - m1);
         }
     }
+    w[24] = pack_bf16(1.f, 1.f);
+    w[25] = pack_bf16(1.f, 0.f);
     uint4* row = Pk + (int64_t)i * 8;
 #pragma unroll
     for (int c = 0; c < 8; ++c) row[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
@@ -367,19 +448,22 @@ ms_status tc_prepare(ms_ctx* ctx) {
                                                                               (int)ctx->n_pad, (uint4*)ctx->Pk);
     MS_LAUNCH("k_pack_bf16");
     ctx->launches += 1;
-    MS_CUDA(cudaFuncSetAttribute(k_shift_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    int per_sm = 0;
-    MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shift_tc, kTcThreads, kSmemBytes));
-    if (per_sm < 1) return set_error(MS_ERR_CUDA, "tensor-core shift kernel does not fit on an SM");
-    ctx->tc_grid = ctx->num_sms * (per_sm > 2 ? 2 : per_sm);
+    MS_CUDA(cudaFuncSetAttribute(k_shift_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    MS_CUDA(cudaFuncSetAttribute(k_shift_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    ctx->tc_grid = ctx->num_sms;  // one CTA per SM: it owns all 512 TMEM columns
     return encode_pmap(ctx->Pk, (int)ctx->n_pad, &ctx->pmap);
 }
 
 ms_status launch_shift_tc(ms_ctx* ctx, const int32_t* active, int grid, int target_items, float* dbg_S) {
     const float c = ceil_to_float(ctx->cfg.bandwidth_cos);
-    k_shift_tc<<<grid, kTcThreads, kSmemBytes, ctx->stream>>>(ctx->pmap, ctx->P32, (int32_t)ctx->n,
-                                                             (int)(ctx->n_pad / 128), active, ctx->X, ctx->acc,
-                                                             c, target_items, ctx->dc, dbg_S);
+    if (dbg_S)
+        k_shift_tc<true><<<grid, kTcThreads, kSmemBytes, ctx->stream>>>(
+            ctx->pmap, ctx->P32, (int32_t)ctx->n, (int)(ctx->n_pad / 128), active, ctx->X, ctx->acc, c,
+            target_items, ctx->dc, dbg_S);
+    else
+        k_shift_tc<false><<<grid, kTcThreads, kSmemBytes, ctx->stream>>>(
+            ctx->pmap, ctx->P32, (int32_t)ctx->n, (int)(ctx->n_pad / 128), active, ctx->X, ctx->acc, c,
+            target_items, ctx->dc, nullptr);
     MS_LAUNCH("k_shift_tc");
     return MS_OK;
 }

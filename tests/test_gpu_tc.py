@@ -40,11 +40,12 @@ def test_tc_tile_products_and_sums(ms_lib, n_pix):
     Ph = bf16(Pn); Pm = bf16(Pn - Ph); Pl = bf16((Pn - Ph) - Pm)
     S_ref = (Xh.astype(np.float64) @ Ph.T.astype(np.float64) + Xh.astype(np.float64) @ Pm.T.astype(np.float64)
              + Xl.astype(np.float64) @ Ph.T.astype(np.float64))
-    got = S[:, :n_pix].astype(np.float64)
-    # tensor-core FP32 accumulation: observed max 2.9e-6 (IEEE sequential would be <= 48 * 2^-24)
-    assert np.abs(got - S_ref).max() <= 5e-6, np.abs(got - S_ref).max()
-    # padded pixels contribute nothing
-    assert np.all(S[:, n_pix:] == 0.0)
+    c_f = float(np.nextafter(np.float32(c), np.float32(2))) if float(np.float32(c)) < c else float(np.float32(c))
+    got = S[:, :n_pix].astype(np.float64) + c_f
+    # tensor-core FP32 accumulation error, measured: <= 6e-6 (the mask's recheck band is 2^-14)
+    assert np.abs(got - S_ref).max() <= 1e-5, np.abs(got - S_ref).max()
+    # padded pixels score exactly -c and never enter a window
+    assert np.all(np.abs(S[:, n_pix:] + c_f) <= 1e-6)
     # window decisions equal the exact ones away from the boundary
     exact = X.astype(np.float64) @ Pn.T.astype(np.float64)
     inw = exact >= c

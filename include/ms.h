@@ -211,6 +211,27 @@ MS_API ms_status ms_run_host(const ms_config* cfg, const float* h_emb, const uin
 MS_API ms_status ms_tc_selftest(const float* d_X, const float* d_P, int32_t n_pix, double c, float* h_S,
                                 int64_t* h_acc);
 
+/* Window sums with no device allocation. The paper has no counterpart: this
+ * is for callers that cannot allocate device memory (an arena or pool that
+ * owns the device, allocation forbidden while a stream is captured, a host
+ * application that hands a plugin only its buffers). It computes, for m
+ * seeds d_X [m, 16] (device FP32) against n pixels d_P [n, 16] (device FP32,
+ * each of nonzero finite norm; normalised inside in FP32), every seed's
+ * flat-kernel window sum and window size at bandwidth c, into the caller's
+ * d_acc_out [m, 17] (device int64: 16 sums in units of 2^-36, then the count)
+ * -- the same quantities ms_tc_selftest returns.
+ * Scratch lives in one fixed file-scope device array of about 1.2 MB that
+ * every GPU loading the library holds until the process exits; it limits
+ * m <= 1024 and n <= 16384 (larger sizes return MS_ERR_INVALID_ARG). No
+ * cudaMalloc, cudaFree or other allocating call is made. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before capturing a stream. All calls on a device share the
+ * array, which keeps the last call's contents (each call clears what must
+ * start at zero): calls whose work overlaps on the GPU, e.g. on two streams,
+ * race. Work is enqueued on `stream`; the call does not synchronise. */
+MS_API ms_status ms_window_sums_static(const float* d_X, int32_t m, const float* d_P, int32_t n, double c,
+                                       int64_t* d_acc_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

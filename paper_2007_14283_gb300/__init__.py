@@ -77,6 +77,7 @@ _SIGNATURES = {
     "ms_inspect": (_i32, [_vp, _i32, _vp, _i64, _pi64]),
     "ms_profile": (_i32, [_vp, _i32]),
     "ms_tc_selftest": (_i32, [_vp, _vp, _i32, ctypes.c_double, _vp, _vp]),
+    "ms_window_sums_static": (_i32, [_vp, _i32, _vp, _i32, ctypes.c_double, _vp, _vp]),
     "ms_run_host": (_i32, [ctypes.POINTER(ms_config), _vp, _vp, _i64, _vp, _vp, _vp, _i32, _pi32,
                            ctypes.POINTER(ms_stats)]),
 }
@@ -253,6 +254,16 @@ def ms_tc_selftest(X, P, c: float = 0.9):
     _check(load().ms_tc_selftest(_dptr(X, torch.float32, "X"), _dptr(P, torch.float32, "P"), n, c,
                                  S.ctypes.data_as(ctypes.c_void_p), acc.ctypes.data_as(ctypes.c_void_p)))
     return S, acc
+
+
+def ms_window_sums_static(X, P, acc_out, c: float = 0.9, stream=None):
+    """Window sums and sizes without device allocation (see ms.h): X CUDA
+    float32 [m, 16], P CUDA float32 [n, 16], acc_out CUDA int64 [m, 17] written
+    in place. Asynchronous on the stream."""
+    import torch
+    _check(load().ms_window_sums_static(_dptr(X, torch.float32, "X"), X.shape[0], _dptr(P, torch.float32, "P"),
+                                        P.shape[0], c, _dptr(acc_out, torch.int64, "acc_out"),
+                                        _stream_handle(stream)))
 
 
 def ms_get_state(ctx: Context) -> int:

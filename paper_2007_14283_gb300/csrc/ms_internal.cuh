@@ -164,6 +164,10 @@ ms_status launch_cover(ms_ctx* ctx, int32_t k0, int32_t k1);
 ms_status launch_label(ms_ctx* ctx, int32_t* d_labels);     // ms_label.cu
 ms_status launch_collect(ms_ctx* ctx);                      // ms_merge.cu
 int shift_blocks_per_sm();                                  // ms_shift_fp32.cu
+// Window sums of the seeds active[0..dc->n_active) into acc (fixed point), d = 16.
+ms_status launch_window_sums_fp32(const float* P32, int32_t n, const int32_t* active, const float* X,
+                                  unsigned long long* acc, float c, const DevCounters* dc,
+                                  cudaStream_t stream);
 ms_status tc_prepare(ms_ctx* ctx);                          // ms_shift_tc.cu
 ms_status launch_shift_tc(ms_ctx* ctx, const int32_t* active, int grid, int target_items, float* dbg_S);
 int tc_smem_bytes();

@@ -223,6 +223,19 @@ int shift_blocks_per_sm() {
     return b16 > 0 ? b16 : 1;
 }
 
+ms_status launch_window_sums_fp32(const float* P32, int32_t n, const int32_t* active, const float* X,
+                                  unsigned long long* acc, float c, const DevCounters* dc,
+                                  cudaStream_t stream) {
+    int per_sm = shift_blocks_per_sm();
+    int dev = 0, sms = 1;
+    MS_CUDA(cudaGetDevice(&dev));
+    MS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = sms * per_sm;
+    k_shift_fp32<16><<<grid, kShiftThreads, 0, stream>>>(P32, n, active, X, acc, c, 2 * grid, dc);
+    MS_LAUNCH("k_shift_fp32");
+    return MS_OK;
+}
+
 ms_status launch_shift_iteration(ms_ctx* ctx, int t, int max_iter, cudaEvent_t e0, cudaEvent_t e1) {
     if (ctx->m_round <= 0) return MS_OK;
     return ctx->Dp == 16 ? shift_iteration_t<16>(ctx, t, max_iter, e0, e1)

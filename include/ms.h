@@ -200,6 +200,26 @@ MS_API ms_status ms_run_host(const ms_config* cfg, const float* h_emb, const uin
                              int64_t n_pixels, void* stream, int32_t* h_labels, float* h_modes,
                              int32_t cap, int32_t* n_modes_out, ms_stats* stats_out);
 
+/* Smooth-kernel form: T unrolled mean-shift steps with the exponential
+ * (von Mises-Fisher) profile of the Eq. 2 kernel family instead of the flat
+ * kernel, every seed moved to the weighted mean of all pixels (the dense
+ * update of Sec. 3.2.1) and renormalised:
+ *   x_{t+1} = normalise( sum_i exp(kappa (x_t . p_i - 1)) p_i ).
+ * d_P: device float32 [N, dim] pixels (used as given, not normalised);
+ * d_X0: device float32 [M, dim] starting seeds; dim must be 16; 0 <= kappa < 80.
+ * ms_vmf_forward writes x_T to d_XT [M, dim].
+ * ms_vmf_backward takes d_GT = dL/dx_T [M, dim] and writes dL/dP to d_dP
+ * [N, dim] and dL/dx_0 to d_dX0 [M, dim]. It recomputes the iterates by
+ * re-running the forward and recomputes every kernel weight on the fly; no
+ * M x N matrix is stored. Both allocate their workspace stream-ordered
+ * (cudaMallocAsync) on `stream` and return without synchronising. Results are
+ * deterministic. MS_ERR_INVALID_ARG on NULL pointers or bad sizes. */
+MS_API ms_status ms_vmf_forward(const float* d_P, int64_t N, const float* d_X0, int32_t M, int32_t dim,
+                                double kappa, int32_t T, float* d_XT, void* stream);
+MS_API ms_status ms_vmf_backward(const float* d_P, int64_t N, const float* d_X0, int32_t M, int32_t dim,
+                                 double kappa, int32_t T, const float* d_GT, float* d_dP, float* d_dX0,
+                                 void* stream);
+
 /* Check of the BF16 tensor-core shift tile (Eq. 11 window, Eq. 8 sums) on
  * one work item: 128 seeds d_X [128, 16] (device, unit FP32) against n_pix
  * pixels d_P [n_pix, 16] (device FP32, normalised inside) with bandwidth c.

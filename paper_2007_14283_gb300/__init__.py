@@ -78,6 +78,8 @@ _SIGNATURES = {
     "ms_profile": (_i32, [_vp, _i32]),
     "ms_tc_selftest": (_i32, [_vp, _vp, _i32, ctypes.c_double, _vp, _vp]),
     "ms_window_sums_static": (_i32, [_vp, _i32, _vp, _i32, ctypes.c_double, _vp, _vp]),
+    "ms_vmf_forward": (_i32, [_vp, _i64, _vp, _i32, _i32, ctypes.c_double, _i32, _vp, _vp]),
+    "ms_vmf_backward": (_i32, [_vp, _i64, _vp, _i32, _i32, ctypes.c_double, _i32, _vp, _vp, _vp, _vp]),
     "ms_run_host": (_i32, [ctypes.POINTER(ms_config), _vp, _vp, _i64, _vp, _vp, _vp, _i32, _pi32,
                            ctypes.POINTER(ms_stats)]),
 }
@@ -264,6 +266,28 @@ def ms_window_sums_static(X, P, acc_out, c: float = 0.9, stream=None):
     _check(load().ms_window_sums_static(_dptr(X, torch.float32, "X"), X.shape[0], _dptr(P, torch.float32, "P"),
                                         P.shape[0], c, _dptr(acc_out, torch.int64, "acc_out"),
                                         _stream_handle(stream)))
+
+
+def ms_vmf_forward(P, X0, kappa: float, T: int, stream=None):
+    """x_T of T smooth-kernel steps. P CUDA float32 [N, 16], X0 [M, 16]."""
+    import torch
+    XT = torch.empty_like(X0)
+    _check(load().ms_vmf_forward(_dptr(P, torch.float32, "P"), P.shape[0], _dptr(X0, torch.float32, "X0"),
+                                 X0.shape[0], X0.shape[1], float(kappa), int(T), _dptr(XT, torch.float32, "XT"),
+                                 _stream_handle(stream)))
+    return XT
+
+
+def ms_vmf_backward(P, X0, kappa: float, T: int, GT, stream=None):
+    """(dL/dP, dL/dX0) for upstream gradient GT = dL/dx_T."""
+    import torch
+    dP = torch.empty_like(P)
+    dX0 = torch.empty_like(X0)
+    _check(load().ms_vmf_backward(_dptr(P, torch.float32, "P"), P.shape[0], _dptr(X0, torch.float32, "X0"),
+                                  X0.shape[0], X0.shape[1], float(kappa), int(T),
+                                  _dptr(GT.contiguous(), torch.float32, "GT"), _dptr(dP, torch.float32, "dP"),
+                                  _dptr(dX0, torch.float32, "dX0"), _stream_handle(stream)))
+    return dP, dX0
 
 
 def ms_get_state(ctx: Context) -> int:

@@ -135,12 +135,12 @@ k_finalize(unsigned long long* __restrict__ acc, const int32_t* __restrict__ act
             fail = true;
             sstate[slot] = kFailed;
         } else {
-            const double yn = sqrt(ss);
+            const double inv = 1.0 / sqrt(ss);
             float* x = X + (int64_t)slot * Dp;
             double dd = 0.0;
 #pragma unroll
             for (int k = 0; k < Dp; ++k) {
-                const float xn = (float)(y[k] / yn);
+                const float xn = (float)(y[k] * inv);
                 const double diff = (double)xn - (double)x[k];
                 dd += diff * diff;
                 x[k] = xn;

@@ -1,0 +1,82 @@
+"""Smooth-kernel (vMF) form: the CUDA forward and hand-written adjoint against
+the FP64 autograd reference (oracle/vmf_ref.py), plus the autograd.Function.
+
+Tolerances: x_T within 1e-5 (FP32 weights and sums); gradients within 1e-4
+relative L2 (FP32 recomputation of every weight in the reverse sweep)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import vmf_ref
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = a.detach().double().cpu(); b = b.detach().double().cpu()
+    return ((a - b).norm() / b.norm()).item()
+
+
+def _problem(N, M, seed=0, K=16):
+    prob = synth.vmf_problem_c5(seed=seed, N=N, M=M, K=K)
+    return (torch.from_numpy(prob["P"]), torch.from_numpy(prob["X0"]), torch.from_numpy(prob["target"]))
+
+
+@pytest.mark.parametrize("N,M,T", [(4096, 64, 10), (3000, 37, 3), (1000, 300, 1)])
+def test_vmf_forward_matches_fp64(ms_lib, N, M, T):
+    P, X0, _ = _problem(N, M)
+    XT = ms_lib.ms_vmf_forward(P.cuda(), X0.cuda(), 20.0, T)
+    ref = vmf_ref.vmf_forward(P.double(), X0.double(), 20.0, T)
+    assert (XT.cpu().double() - ref).abs().max().item() <= 1e-5
+    assert torch.allclose(XT.norm(dim=1).cpu().double(), torch.ones(M, dtype=torch.float64), atol=1e-6)
+
+
+@pytest.mark.parametrize("N,M,T", [(4096, 64, 10), (3000, 37, 3)])
+def test_vmf_adjoint_matches_fp64_vjp(ms_lib, N, M, T):
+    P, X0, _ = _problem(N, M, seed=1)
+    G = torch.randn(M, 16, generator=torch.Generator().manual_seed(3))
+    dP, dX0 = ms_lib.ms_vmf_backward(P.cuda(), X0.cuda(), 20.0, T, G.cuda())
+    _, rP, rX = vmf_ref.vmf_vjp(P.double(), X0.double(), 20.0, T, G.double())
+    assert rel(dP, rP) <= 1e-4, rel(dP, rP)
+    assert rel(dX0, rX) <= 1e-4, rel(dX0, rX)
+
+
+def test_vmf_zero_steps_is_identity(ms_lib):
+    P, X0, _ = _problem(512, 32, seed=2)
+    XT = ms_lib.ms_vmf_forward(P.cuda(), X0.cuda(), 20.0, 0)
+    assert torch.equal(XT.cpu(), X0)
+    G = torch.ones(32, 16)
+    dP, dX0 = ms_lib.ms_vmf_backward(P.cuda(), X0.cuda(), 20.0, 0, G.cuda())
+    assert torch.equal(dX0.cpu(), G) and dP.abs().max().item() == 0.0
+
+
+def test_autograd_function_loss_gradients(ms_lib):
+    from paper_2007_14283_gb300.autograd import VMFMeanShift
+    P, X0, target = _problem(8192, 96, seed=4)
+    Pg = P.cuda().requires_grad_(True)
+    Xg = X0.cuda().requires_grad_(True)
+    XT = VMFMeanShift.apply(Pg, Xg, 20.0, 10)
+    loss = ((XT - target.cuda()) ** 2).sum()
+    loss.backward()
+    rloss, rP, rX = vmf_ref.vmf_loss_and_grads(P.double(), X0.double(), target.double(), 20.0, 10)
+    assert abs(loss.item() - rloss.item()) <= 1e-4 * abs(rloss.item())
+    assert rel(Pg.grad, rP) <= 1e-4 and rel(Xg.grad, rX) <= 1e-4
+
+
+def test_vmf_full_width_subset_matches_fp64(ms_lib):
+    # the differentiable config's pixel count (65536) with 256 of its seeds
+    P, X0, target = _problem(65536, 256, seed=0, K=32)
+    Pd, Xd = P.cuda(), X0.cuda()
+    G = 2 * (ms_lib.ms_vmf_forward(Pd, Xd, 20.0, 10) - target.cuda())
+    dP, dX0 = ms_lib.ms_vmf_backward(Pd, Xd, 20.0, 10, G)
+    rloss, rP, rX = vmf_ref.vmf_loss_and_grads(P.double(), X0.double(), target.double(), 20.0, 10)
+    assert rel(dP, rP) <= 1e-4 and rel(dX0, rX) <= 1e-4
+
+
+def test_vmf_deterministic(ms_lib):
+    P, X0, _ = _problem(4096, 64, seed=5)
+    G = torch.randn(64, 16, generator=torch.Generator().manual_seed(1)).cuda()
+    a = ms_lib.ms_vmf_backward(P.cuda(), X0.cuda(), 20.0, 5, G)
+    b = ms_lib.ms_vmf_backward(P.cuda(), X0.cuda(), 20.0, 5, G)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])

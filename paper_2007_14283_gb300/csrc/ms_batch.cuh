@@ -1,0 +1,70 @@
+// Batched form: B frames of uneven size clustered together, every frame's
+// OSOP control on the device (a per-frame state machine advanced by one CUDA
+// graph whose body runs until all frames finish).
+#pragma once
+
+#include "ms_internal.cuh"
+
+namespace ms {
+
+// Per-frame phase of the OSOP loop.
+enum BPhase : int32_t { kNeedSeed = 0, kIterating = 1, kRoundDone = 2, kFinished = 3 };
+
+// Per-frame constants, fixed after set-up. Frame f owns the rows
+// [pix0, pix0 + n) of every per-pixel, per-seed, per-candidate and per-mode
+// array, and the Pk rows [pk_row0, pk_row0 + n_ptiles * 128).
+struct BFrame {
+    int64_t pix0;
+    int64_t in0;        // offset of the frame's input pixels (labels, masks)
+    int64_t n_pixels;   // input pixels
+    int32_t n;          // foreground pixels
+    int32_t n_ptiles;   // ceil(n / 128)
+    int32_t pk_row0;
+    int32_t pad;
+    uint64_t perm_a, perm_b;
+    const float* emb;   // borrowed input [n_pixels, d]
+    const uint8_t* mask;
+};
+
+// Per-frame state, advanced only by device code.
+struct BState {
+    DevCounters dc;
+    int64_t N;          // seeds requested next round (Sec. 3.2.4)
+    int32_t phase;
+    int32_t rounds;
+    int32_t k0;         // kept modes before the current merge
+    int32_t pad;
+};
+
+// Work split of the current iteration, computed on the device.
+// item_off / seed_off: exclusive prefix sums over frames (B + 1 entries).
+struct BPlan {
+    int32_t* item_off;
+    int32_t* seed_off;
+    int32_t* chunks;    // per frame
+    int32_t* tpc;       // per frame: pixel tiles (TC) or pixels (FP32) per chunk
+};
+
+// Tensor-core shift over all iterating frames (ms_shift_tc.cu).
+ms_status tc_batch_setup();
+ms_status launch_shift_tc_batch(const CUtensorMap& pmap, const float* P32, const float* X, unsigned long long* acc,
+                                float c_f, const BFrame* frames, const BState* states, BPlan plan,
+                                const int32_t* act0, const int32_t* act1, int nf, int* status,
+                                unsigned long long* band, int grid, cudaStream_t st);
+ms_status encode_pk_map(void* Pk, int rows, CUtensorMap* map);
+// FP32 shift over all iterating frames (ms_shift_fp32.cu).
+ms_status launch_shift_fp32_batch(const float* P32, const float* X, unsigned long long* acc, float c_f, int Dp,
+                                  const BFrame* frames, const BState* states, BPlan plan, const int32_t* act0,
+                                  const int32_t* act1, int nf, int grid, cudaStream_t st);
+
+// Index of the frame whose [off[f], off[f+1]) holds i (off has nf + 1 entries).
+__device__ __forceinline__ int locate(const int32_t* off, int nf, int i) {
+    int lo = 0, hi = nf;  // invariant: off[lo] <= i < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+}  // namespace ms

@@ -14,7 +14,7 @@
 // accumulators (units of 2^-36). Integer addition is associative, so the
 // totals do not depend on the order in which items finish: runs are
 // deterministic, and the finalize step reads one word per component.
-#include "ms_internal.cuh"
+#include "ms_batch.cuh"
 
 namespace ms {
 namespace {
@@ -22,24 +22,55 @@ namespace {
 constexpr float kFixScale = 68719476736.0f;      // 2^36
 constexpr double kFixInv = 1.0 / 68719476736.0;  // 2^-36
 
-template <int Dp>
+// What a work item covers: a tile of the frame's active seeds and the pixel
+// rows [p_begin, p_end) of P32.
+struct F32Item {
+    const int32_t* active;
+    int n_active;
+    int seed0;
+    int64_t p_begin, p_end;
+};
+
+// Work items of one frame: seed tiles of 256 x pixel chunks.
+struct F32SingleMap {
+    const int32_t* active;
+    const DevCounters* dc;
+    int n, target;
+    int n_active;
+    ShiftSplit sp;
+    __device__ __forceinline__ bool init() {
+        if (dc->done) return false;
+        n_active = dc->n_active;
+        sp = shift_split(n_active, n, target);
+        return true;
+    }
+    __device__ __forceinline__ int total() const { return sp.tiles * sp.chunks; }
+    __device__ __forceinline__ F32Item item(int i) const {
+        const int t = i / sp.chunks, ch = i - t * sp.chunks;
+        F32Item it;
+        it.active = active;
+        it.n_active = n_active;
+        it.seed0 = t * kSeedsPerTile;
+        it.p_begin = (int64_t)ch * sp.chunk_len;
+        it.p_end = min((int64_t)n, it.p_begin + sp.chunk_len);
+        return it;
+    }
+};
+
+template <int Dp, class Map>
 __global__ void __launch_bounds__(kShiftThreads)
-k_shift_fp32(const float* __restrict__ P32, int32_t n, const int32_t* __restrict__ active,
-             const float* __restrict__ X, unsigned long long* __restrict__ acc, float c,
-             int target_items, const DevCounters* __restrict__ dc) {
-    if (dc->done) return;
-    const int n_active = dc->n_active;
-    const ShiftSplit sp = shift_split(n_active, n, target_items);
-    const int items = sp.tiles * sp.chunks;
+k_shift_fp32(const float* __restrict__ P32, const float* __restrict__ X, unsigned long long* __restrict__ acc,
+             float c, Map map) {
+    if (!map.init()) return;
+    const int items = map.total();
     __shared__ __align__(16) float tile[kPixTile * Dp];
     const int tid = threadIdx.x;
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
-        const int t = item / sp.chunks;
-        const int ch = item - t * sp.chunks;
-        const int pos0 = t * kSeedsPerTile + tid;
+        const F32Item ii = map.item(item);
+        const int pos0 = ii.seed0 + tid;
         const int pos1 = pos0 + kShiftThreads;
-        const int s0 = pos0 < n_active ? active[pos0] : -1;
-        const int s1 = pos1 < n_active ? active[pos1] : -1;
+        const int s0 = pos0 < ii.n_active ? ii.active[pos0] : -1;
+        const int s1 = pos1 < ii.n_active ? ii.active[pos1] : -1;
         float x0[Dp], x1[Dp], y0[Dp], y1[Dp];
         float c0 = 0.f, c1 = 0.f;
 #pragma unroll
@@ -53,10 +84,9 @@ k_shift_fp32(const float* __restrict__ P32, int32_t n, const int32_t* __restrict
         }
 #pragma unroll
         for (int k = 0; k < Dp; ++k) y0[k] = y1[k] = 0.f;
-        const int p_begin = ch * sp.chunk_len;
-        const int p_end = min(n, p_begin + sp.chunk_len);
-        for (int pb = p_begin; pb < p_end; pb += kPixTile) {
-            const int cnt = min(kPixTile, p_end - pb);
+        const int64_t p_begin = ii.p_begin, p_end = ii.p_end;
+        for (int64_t pb = p_begin; pb < p_end; pb += kPixTile) {
+            const int cnt = (int)min((int64_t)kPixTile, p_end - pb);
             __syncthreads();
             const float4* src = reinterpret_cast<const float4*>(P32 + (int64_t)pb * Dp);
             float4* dst = reinterpret_cast<float4*>(tile);
@@ -195,8 +225,13 @@ ms_status shift_iteration_t(ms_ctx* ctx, int t, int max_iter, cudaEvent_t e0, cu
         ms_status s = launch_shift_tc(ctx, a_in, ctx->tc_grid, 2 * ctx->tc_grid, nullptr);
         if (s != MS_OK) return s;
     } else {
-        k_shift_fp32<Dp><<<ctx->shift_grid, kShiftThreads, 0, ctx->stream>>>(
-            ctx->P32, (int32_t)ctx->n, a_in, ctx->X, ctx->acc, c, ctx->target_items, ctx->dc);
+        F32SingleMap map;
+        map.active = a_in;
+        map.dc = ctx->dc;
+        map.n = (int)ctx->n;
+        map.target = ctx->target_items;
+        k_shift_fp32<Dp, F32SingleMap><<<ctx->shift_grid, kShiftThreads, 0, ctx->stream>>>(ctx->P32, ctx->X,
+                                                                                         ctx->acc, c, map);
         MS_LAUNCH("k_shift_fp32");
     }
     if (e1) MS_CUDA(cudaEventRecord(e1, ctx->stream));
@@ -219,7 +254,7 @@ float ceil_to_float(double c) {
 
 int shift_blocks_per_sm() {
     int b16 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b16, k_shift_fp32<16>, kShiftThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b16, k_shift_fp32<16, F32SingleMap>, kShiftThreads, 0);
     return b16 > 0 ? b16 : 1;
 }
 
@@ -231,8 +266,64 @@ ms_status launch_window_sums_fp32(const float* P32, int32_t n, const int32_t* ac
     MS_CUDA(cudaGetDevice(&dev));
     MS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int grid = sms * per_sm;
-    k_shift_fp32<16><<<grid, kShiftThreads, 0, stream>>>(P32, n, active, X, acc, c, 2 * grid, dc);
+    F32SingleMap map;
+    map.active = active;
+    map.dc = dc;
+    map.n = n;
+    map.target = 2 * grid;
+    k_shift_fp32<16, F32SingleMap><<<grid, kShiftThreads, 0, stream>>>(P32, X, acc, c, map);
     MS_LAUNCH("k_shift_fp32");
+    return MS_OK;
+}
+
+// Work items of every iterating frame (batched form): frame f contributes
+// item_off[f+1] - item_off[f] items, seed tiles of 256 x chunks of tpc[f] pixels.
+struct F32BatchMap {
+    const BFrame* frames;
+    const BState* states;
+    BPlan plan;
+    const int32_t* act0;
+    const int32_t* act1;
+    int nf;
+    int total_;
+    __device__ __forceinline__ bool init() {
+        total_ = plan.item_off[nf];
+        return total_ > 0;
+    }
+    __device__ __forceinline__ int total() const { return total_; }
+    __device__ __forceinline__ F32Item item(int i) const {
+        const int f = locate(plan.item_off, nf, i);
+        const int local = i - plan.item_off[f];
+        const int chunks = plan.chunks[f];
+        const int t = local / chunks, ch = local - t * chunks;
+        const BFrame& fr = frames[f];
+        F32Item it;
+        it.active = ((states[f].dc.iters & 1) ? act1 : act0) + fr.pix0;
+        it.n_active = states[f].dc.n_active;
+        it.seed0 = t * kSeedsPerTile;
+        const int64_t b = (int64_t)ch * plan.tpc[f];
+        it.p_begin = fr.pix0 + b;
+        it.p_end = fr.pix0 + min((int64_t)fr.n, b + plan.tpc[f]);
+        return it;
+    }
+};
+
+ms_status launch_shift_fp32_batch(const float* P32, const float* X, unsigned long long* acc, float c_f, int Dp,
+                                  const BFrame* frames, const BState* states, BPlan plan, const int32_t* act0,
+                                  const int32_t* act1, int nf, int grid, cudaStream_t st) {
+    F32BatchMap map;
+    map.frames = frames;
+    map.states = states;
+    map.plan = plan;
+    map.act0 = act0;
+    map.act1 = act1;
+    map.nf = nf;
+    map.total_ = 0;
+    if (Dp == 16)
+        k_shift_fp32<16, F32BatchMap><<<grid, kShiftThreads, 0, st>>>(P32, X, acc, c_f, map);
+    else
+        k_shift_fp32<32, F32BatchMap><<<grid, kShiftThreads, 0, st>>>(P32, X, acc, c_f, map);
+    MS_LAUNCH("k_shift_fp32(batch)");
     return MS_OK;
 }
 

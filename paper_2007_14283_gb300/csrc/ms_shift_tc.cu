@@ -28,6 +28,7 @@
 // MS_ERR_TIMEOUT through the frame's status word.
 #include <cudaTypedefs.h>
 
+#include "ms_batch.cuh"
 #include "ms_device.cuh"
 #include "ms_tc.cuh"
 
@@ -123,13 +124,53 @@ struct Gemm2Job {
     bool first, last;
 };
 
-template <bool kDebug>
+// What a work item covers, in the frame it belongs to.
+struct TcItem {
+    const int32_t* active;  // seed slots of the frame's active list
+    int n_active;           // length of that list
+    int seed0;              // list position of the item's first seed
+    int pt0, pt1;           // the frame's 128-pixel tiles [pt0, pt1)
+    int pk_row0;            // Pk row of the frame's pixel 0 (multiple of 128)
+    int64_t pix0;           // P32 row of the frame's pixel 0
+    int n;                  // the frame's pixel count
+};
+
+// Work items of one frame: seed tiles of 128 x chunks of 128-pixel tiles.
+struct TcSingleMap {
+    const int32_t* active;
+    const DevCounters* dc;
+    int n, n_ptiles, target;
+    int n_active;
+    TcSplit sp;
+    __device__ __forceinline__ bool init() {
+        if (dc->done) return false;
+        n_active = dc->n_active;
+        sp = tc_split(n_active, n_ptiles, target);
+        return true;
+    }
+    __device__ __forceinline__ int total() const { return sp.tiles * sp.chunks; }
+    __device__ __forceinline__ TcItem item(int i) const {
+        const int t = i / sp.chunks, ch = i - t * sp.chunks;
+        const int pt0 = ch * sp.tpc;
+        TcItem it;
+        it.active = active;
+        it.n_active = n_active;
+        it.seed0 = t * 128;
+        it.pt0 = pt0;
+        it.pt1 = min(n_ptiles, pt0 + sp.tpc);
+        it.pk_row0 = 0;
+        it.pix0 = 0;
+        it.n = n;
+        return it;
+    }
+};
+
+template <bool kDebug, class Map>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P32, int32_t n,
-           int n_ptiles, const int32_t* __restrict__ active, const float* __restrict__ X,
-           unsigned long long* __restrict__ acc, float c_f, int target_items, DevCounters* dc,
-           float* __restrict__ dbg_S) {
-    if (dc->done) return;
+k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P32, const float* __restrict__ X,
+           unsigned long long* __restrict__ acc, float c_f, Map map, int* status,
+           unsigned long long* band_ctr, float* __restrict__ dbg_S, int64_t dbg_stride) {
+    if (!map.init()) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* A1 = smem + kOffA1;
@@ -177,22 +218,19 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int n_active = dc->n_active;
-    const TcSplit sp = tc_split(n_active, n_ptiles, target_items);
-    const int items = sp.tiles * sp.chunks;
+    const int items = map.total();
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             int g = 0;
             for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x) {
-                const int ch = item % sp.chunks;
-                const int pt0 = ch * sp.tpc, pt1 = min(n_ptiles, pt0 + sp.tpc);
-                for (int pt = pt0; pt < pt1; ++pt, ++g) {
+                const TcItem ii = map.item(item);
+                for (int pt = ii.pt0; pt < ii.pt1; ++pt, ++g) {
                     const int s = g % kStages;
                     if (g >= kStages && !mbar_wait(&empty[s], ((g / kStages) - 1) & 1, abort)) break;
                     mbar_arrive_expect_tx(&full[s], kTileBytes);
-                    tma_load_2d(Pst + s * kTileBytes, &pmap, 0, pt * 128, &full[s]);
+                    tma_load_2d(Pst + s * kTileBytes, &pmap, 0, ii.pk_row0 + pt * 128, &full[s]);
                 }
             }
             if (*abort)
@@ -227,8 +265,8 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
             };
             int g = 0, it = 0;
             for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
-                const int ch = item % sp.chunks;
-                const int pt0 = ch * sp.tpc, pt1 = min(n_ptiles, pt0 + sp.tpc);
+                const TcItem ii = map.item(item);
+                const int pt0 = ii.pt0, pt1 = ii.pt1;
                 if (!(ok = mbar_wait(&a1_full[it & 1], (it >> 1) & 1, abort))) break;
                 const uint32_t a = a1 + (it & 1) * kTileBytes;
                 for (int pt = pt0; pt < pt1; ++pt, ++g) {
@@ -264,10 +302,10 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
         int g = 0, it = 0;
         float x[16];
         for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x, ++it) {
-            const int t = item / sp.chunks, ch = item % sp.chunks;
-            const int pt0 = ch * sp.tpc, pt1 = min(n_ptiles, pt0 + sp.tpc);
-            const int pos = t * 128 + r;
-            const int slot = pos < n_active ? active[pos] : -1;
+            const TcItem ii = map.item(item);
+            const int pt0 = ii.pt0, pt1 = ii.pt1;
+            const int pos = ii.seed0 + r;
+            const int slot = pos < ii.n_active ? ii.active[pos] : -1;
             load_x16(X, slot, x);
             if (h == 0) {
                 // A1 for this item (first item only) and the next one; the next
@@ -280,9 +318,10 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                 }
                 const int nitem = item + gridDim.x;
                 if (nitem < items) {
-                    const int npos = (nitem / sp.chunks) * 128 + r;
+                    const TcItem ni = map.item(nitem);
+                    const int npos = ni.seed0 + r;
                     float xn[16];
-                    load_x16(X, npos < n_active ? active[npos] : -1, xn);
+                    load_x16(X, npos < ni.n_active ? ni.active[npos] : -1, xn);
                     write_a1(A1 + ((it + 1) & 1) * kTileBytes, r, xn, c_f);
                     fence_proxy_async();
                     mbar_arrive(&a1_full[(it + 1) & 1]);
@@ -321,8 +360,9 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                     while (todo) {
                         const int i = __ffsll((long long)todo) - 1;
                         todo &= todo - 1;
-                        const int px = pt * 128 + h * 64 + i;
-                        if (px < n) {
+                        const int px_local = pt * 128 + h * 64 + i;
+                        const int64_t px = ii.pix0 + px_local;
+                        if (px_local < ii.n) {
                             ++band_local;
                             float pv[16];
 #pragma unroll
@@ -345,7 +385,7 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                 if (kDebug) {
 #pragma unroll
                     for (int i = 0; i < 64; ++i)
-                        dbg_S[(int64_t)r * n_ptiles * 128 + pt * 128 + h * 64 + i] = __uint_as_float(v[i]);
+                        dbg_S[(int64_t)r * dbg_stride + pt * 128 + h * 64 + i] = __uint_as_float(v[i]);
                 }
                 if (g >= 2 && !mbar_wait(&m_empty[b], ((g >> 1) - 1) & 1, abort)) break;
                 uint8_t* mrow = Mt + b * 2 * kTileBytes + h * kTileBytes;
@@ -381,13 +421,13 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                 }
             }
         }
-        if (band_local) atomicAdd((unsigned long long*)&dc->band_pairs, (unsigned long long)band_local);
+        if (band_local) atomicAdd(band_ctr, (unsigned long long)band_local);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem, kTmemCols);
-    if (threadIdx.x == 0 && *abort) atomicOr(&dc->status, 2);
+    if (threadIdx.x == 0 && *abort) atomicOr(status, 2);
 }
 
 // Pixels as BF16 splits for the tensor cores: row i = [Ph | Pm | Pl | 1 1 1 0..0]
@@ -448,24 +488,92 @@ ms_status tc_prepare(ms_ctx* ctx) {
                                                                               (int)ctx->n_pad, (uint4*)ctx->Pk);
     MS_LAUNCH("k_pack_bf16");
     ctx->launches += 1;
-    MS_CUDA(cudaFuncSetAttribute(k_shift_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    MS_CUDA(cudaFuncSetAttribute(k_shift_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    MS_CUDA(cudaFuncSetAttribute(k_shift_tc<false, TcSingleMap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemBytes));
+    MS_CUDA(cudaFuncSetAttribute(k_shift_tc<true, TcSingleMap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemBytes));
     ctx->tc_grid = ctx->num_sms;  // one CTA per SM: it owns all 512 TMEM columns
     return encode_pmap(ctx->Pk, (int)ctx->n_pad, &ctx->pmap);
 }
 
 ms_status launch_shift_tc(ms_ctx* ctx, const int32_t* active, int grid, int target_items, float* dbg_S) {
     const float c = ceil_to_float(ctx->cfg.bandwidth_cos);
+    TcSingleMap map;
+    map.active = active;
+    map.dc = ctx->dc;
+    map.n = (int)ctx->n;
+    map.n_ptiles = (int)(ctx->n_pad / 128);
+    map.target = target_items;
+    unsigned long long* band = (unsigned long long*)&ctx->dc->band_pairs;
     if (dbg_S)
-        k_shift_tc<true><<<grid, kTcThreads, kSmemBytes, ctx->stream>>>(
-            ctx->pmap, ctx->P32, (int32_t)ctx->n, (int)(ctx->n_pad / 128), active, ctx->X, ctx->acc, c,
-            target_items, ctx->dc, dbg_S);
+        k_shift_tc<true, TcSingleMap><<<grid, kTcThreads, kSmemBytes, ctx->stream>>>(
+            ctx->pmap, ctx->P32, ctx->X, ctx->acc, c, map, &ctx->dc->status, band, dbg_S, ctx->n_pad);
     else
-        k_shift_tc<false><<<grid, kTcThreads, kSmemBytes, ctx->stream>>>(
-            ctx->pmap, ctx->P32, (int32_t)ctx->n, (int)(ctx->n_pad / 128), active, ctx->X, ctx->acc, c,
-            target_items, ctx->dc, nullptr);
+        k_shift_tc<false, TcSingleMap><<<grid, kTcThreads, kSmemBytes, ctx->stream>>>(
+            ctx->pmap, ctx->P32, ctx->X, ctx->acc, c, map, &ctx->dc->status, band, nullptr, 0);
     MS_LAUNCH("k_shift_tc");
     return MS_OK;
 }
+
+// ------------------------------------------------------------ batched form
+// Work items of every iterating frame: frame f contributes
+// item_off[f+1] - item_off[f] items (seed tiles of 128 x chunks).
+struct TcBatchMap {
+    const BFrame* frames;
+    const BState* states;
+    BPlan plan;
+    const int32_t* act0;
+    const int32_t* act1;
+    int nf;
+    int total_;
+    __device__ __forceinline__ bool init() {
+        total_ = plan.item_off[nf];
+        return total_ > 0;
+    }
+    __device__ __forceinline__ int total() const { return total_; }
+    __device__ __forceinline__ TcItem item(int i) const {
+        const int f = locate(plan.item_off, nf, i);
+        const int local = i - plan.item_off[f];
+        const int chunks = plan.chunks[f], tpc = plan.tpc[f];
+        const int t = local / chunks, ch = local - t * chunks;
+        const BFrame& fr = frames[f];
+        TcItem it;
+        it.active = ((states[f].dc.iters & 1) ? act1 : act0) + fr.pix0;
+        it.n_active = states[f].dc.n_active;
+        it.seed0 = t * 128;
+        it.pt0 = ch * tpc;
+        it.pt1 = min(fr.n_ptiles, it.pt0 + tpc);
+        it.pk_row0 = fr.pk_row0;
+        it.pix0 = fr.pix0;
+        it.n = fr.n;
+        return it;
+    }
+};
+
+ms_status tc_batch_setup() {
+    MS_CUDA(cudaFuncSetAttribute(k_shift_tc<false, TcBatchMap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemBytes));
+    return MS_OK;
+}
+
+ms_status launch_shift_tc_batch(const CUtensorMap& pmap, const float* P32, const float* X, unsigned long long* acc,
+                                float c_f, const BFrame* frames, const BState* states, BPlan plan,
+                                const int32_t* act0, const int32_t* act1, int nf, int* status,
+                                unsigned long long* band, int grid, cudaStream_t st) {
+    TcBatchMap map;
+    map.frames = frames;
+    map.states = states;
+    map.plan = plan;
+    map.act0 = act0;
+    map.act1 = act1;
+    map.nf = nf;
+    map.total_ = 0;
+    k_shift_tc<false, TcBatchMap><<<grid, kTcThreads, kSmemBytes, st>>>(pmap, P32, X, acc, c_f, map, status, band,
+                                                                       nullptr, 0);
+    MS_LAUNCH("k_shift_tc(batch)");
+    return MS_OK;
+}
+
+ms_status encode_pk_map(void* Pk, int rows, CUtensorMap* map) { return encode_pmap(Pk, rows, map); }
 
 }  // namespace ms

@@ -83,7 +83,10 @@ typedef struct ms_config {
     int32_t max_rounds;   /* guard on OSOP rounds; default 1000000 */
     double eps_band;      /* BF16 recheck band half-width; 0 = the library's proven bound */
     int32_t all_seeds;    /* 1 = Algorithm 1: every pixel seeds a single round, gamma = 1 */
-    int32_t reserved[7];  /* zero */
+    int32_t batch_split;  /* ms_batch_* only: 0 = each frame split into work items as on its own
+                             (results bit-identical to ms_run on that frame); 1 = the batch's
+                             work items shared out by each frame's seed x pixel work */
+    int32_t reserved[6];  /* zero */
 } ms_config;
 
 /* Per-context counters, filled by ms_stats_get. */
@@ -251,6 +254,53 @@ MS_API ms_status ms_tc_selftest(const float* d_X, const float* d_P, int32_t n_pi
  * race. Work is enqueued on `stream`; the call does not synchronise. */
 MS_API ms_status ms_window_sums_static(const float* d_X, int32_t m, const float* d_P, int32_t n, double c,
                                        int64_t* d_acc_out, void* stream);
+
+/* Batched form: B frames (e.g. the frames of a time-lapse sequence, each its
+ * own vector set S of Algorithm 2) clustered by one CUDA graph. Every frame
+ * runs exactly the single-frame method (same seeds, rounds, modes and labels
+ * as ms_create + ms_run on that frame with cfg->frame_id = cfg->frame_id + f)
+ * but the OSOP control (Sec. 3.2.2-3.2.4: seed batches, early stop at gamma,
+ * merge, coverage, the Eq. 19 schedule) runs on the device, one state
+ * machine per frame, and the shift kernel of each iteration is one launch
+ * over the work of all frames still iterating. Frames of different sizes are
+ * in different rounds at the same time.
+ *
+ * ms_batch_create binds the frames and builds the graph (a set-up stage, a
+ * conditional WHILE node whose body advances every frame by one iteration,
+ * then labelling); it allocates the workspace (one cudaMalloc) and
+ * synchronises `stream`. Arguments:
+ *  cfg       as for ms_create (MS_FLAT; MS_BF16 needs dim <= 16).
+ *  B         1..4096 frames.
+ *  d_embs    host array of B device pointers, frame f float32 [n_pixels[f], dim]. Borrowed.
+ *  d_masks   host array of B device pointers (uint8 [n_pixels[f]], NULL entry = all
+ *            foreground), or NULL for no masks. Borrowed.
+ *  n_pixels  host array of B sizes, each 0 <= n < 2^24, sum < 2^31.
+ *  d_labels  host array of B device pointers, int32 [n_pixels[f]]: written by every
+ *            ms_batch_run (background -1). Borrowed.
+ *  stream    the cudaStream_t the graph is launched on (NULL = legacy default).
+ * The pointer arrays are copied; the buffers they point to must stay alive
+ * and must not move until ms_batch_destroy. MS_ERR_INVALID_ARG for a bad
+ * cfg or frame.
+ *
+ * ms_batch_run launches the graph once on `stream` (the whole method on all
+ * frames, from the embeddings as they are now). With sync = 0 it returns at
+ * once; with sync != 0 it waits, reads the per-frame counters back, and
+ * returns MS_ERR_INVALID_ARG if a foreground vector had zero or non-finite
+ * norm, MS_ERR_TIMEOUT if a bounded device wait gave up.
+ * ms_batch_stats fills *out for frame f (or summed over all frames for
+ * f = -1) from the last synchronised run; launches = kernels in one pass of
+ * the loop body. ms_batch_modes copies frame f's K kept modes, float32
+ * [K, dim], to h_out (cap >= K; h_out NULL only reports K). ms_batch_destroy
+ * synchronises the stream and frees everything. */
+typedef struct ms_batch ms_batch;
+MS_API ms_status ms_batch_create(const ms_config* cfg, int32_t B, const float* const* d_embs,
+                                 const uint8_t* const* d_masks, const int64_t* n_pixels,
+                                 int32_t* const* d_labels, void* stream, ms_batch** out);
+MS_API ms_status ms_batch_run(ms_batch* b, int32_t sync);
+MS_API ms_status ms_batch_stats(const ms_batch* b, int32_t frame, ms_stats* out);
+MS_API ms_status ms_batch_modes(const ms_batch* b, int32_t frame, float* h_out, int32_t cap,
+                                int32_t* n_modes_out);
+MS_API void ms_batch_destroy(ms_batch* b);
 
 #ifdef __cplusplus
 }

@@ -41,7 +41,7 @@ class ms_config(ctypes.Structure):
         ("H", ctypes.c_double), ("P_target", ctypes.c_double), ("alpha", ctypes.c_double),
         ("merge_cos", ctypes.c_double), ("seed", ctypes.c_uint64), ("frame_id", ctypes.c_uint64),
         ("precision", ctypes.c_int32), ("max_rounds", ctypes.c_int32), ("eps_band", ctypes.c_double),
-        ("all_seeds", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7),
+        ("all_seeds", ctypes.c_int32), ("batch_split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6),
     ]
 
 
@@ -82,6 +82,12 @@ _SIGNATURES = {
     "ms_vmf_backward": (_i32, [_vp, _i64, _vp, _i32, _i32, ctypes.c_double, _i32, _vp, _vp, _vp, _vp]),
     "ms_run_host": (_i32, [ctypes.POINTER(ms_config), _vp, _vp, _i64, _vp, _vp, _vp, _i32, _pi32,
                            ctypes.POINTER(ms_stats)]),
+    "ms_batch_create": (_i32, [ctypes.POINTER(ms_config), _i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                               _pi64, ctypes.POINTER(_vp), _vp, ctypes.POINTER(_vp)]),
+    "ms_batch_run": (_i32, [_vp, _i32]),
+    "ms_batch_stats": (_i32, [_vp, _i32, ctypes.POINTER(ms_stats)]),
+    "ms_batch_modes": (_i32, [_vp, _i32, _vp, _i32, _pi32]),
+    "ms_batch_destroy": (None, [_vp]),
 }
 
 
@@ -313,6 +319,70 @@ def ms_inspect(ctx: Context, what: int, dim: int = 16):
         _check(load().ms_inspect(ctx.handle, what, out.ctypes.data_as(ctypes.c_void_p), cnt.value,
                                  ctypes.byref(cnt)))
     return out if width > 1 else out[:, 0]
+
+
+class Batch:
+    """Owns an ms_batch; keeps the borrowed embeddings, masks and label buffers alive."""
+
+    def __init__(self, handle, embs, masks, labels, dim):
+        self.handle = handle
+        self.labels = labels
+        self.dim = dim
+        self._keep = (embs, masks)
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ms_batch_destroy(self.handle)
+            self.handle = None
+
+
+def ms_batch_create(cfg: ms_config, embs, masks=None, stream=None) -> Batch:
+    """embs: list of CUDA float32 [n_pixels_f, dim]; masks: None or a list of
+    CUDA uint8 [n_pixels_f] (entries may be None). Label buffers (CUDA int32
+    [n_pixels_f]) are allocated here and exposed as Batch.labels."""
+    import torch
+    B = len(embs)
+    ptr_arr = _vp * max(B, 1)
+    e = ptr_arr(*[_dptr(t, torch.float32, "emb") for t in embs])
+    m = None
+    if masks is not None:
+        m = ptr_arr(*[_dptr(t, torch.uint8, "mask") if t is not None else None for t in masks])
+    labels = [torch.empty(t.shape[0], dtype=torch.int32, device=t.device) for t in embs]
+    lab = ptr_arr(*[ctypes.c_void_p(t.data_ptr()) for t in labels])
+    n = (ctypes.c_int64 * max(B, 1))(*[int(t.shape[0]) for t in embs])
+    h = ctypes.c_void_p()
+    _check(load().ms_batch_create(ctypes.byref(cfg), B, e, m, n, lab, _stream_handle(stream),
+                                  ctypes.byref(h)))
+    return Batch(h, list(embs), masks, labels, cfg.dim)
+
+
+def ms_batch_run(b: Batch, sync: bool = True):
+    _check(load().ms_batch_run(b.handle, 1 if sync else 0))
+
+
+def ms_batch_stats(b: Batch, frame: int = -1) -> dict:
+    st = ms_stats()
+    _check(load().ms_batch_stats(b.handle, frame, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in ms_stats._fields_}
+
+
+def ms_batch_modes(b: Batch, frame: int):
+    """Frame `frame`'s kept modes as a numpy float32 [K, dim] array (last synchronised run)."""
+    import numpy as np
+    k = ctypes.c_int32()
+    _check(load().ms_batch_modes(b.handle, frame, None, 0, ctypes.byref(k)))
+    out = np.zeros((k.value, b.dim), dtype=np.float32)
+    if k.value:
+        _check(load().ms_batch_modes(b.handle, frame, out.ctypes.data_as(ctypes.c_void_p), k.value,
+                                     ctypes.byref(k)))
+    return out
+
+
+def ms_batch_destroy(b: Batch):
+    b.close()
 
 
 # ------------------------------------------------------------ convenience

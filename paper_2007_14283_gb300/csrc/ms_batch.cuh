@@ -33,7 +33,10 @@ struct BState {
     int32_t phase;
     int32_t rounds;
     int32_t k0;         // kept modes before the current merge
-    int32_t pad;
+    int32_t iters_total;
+    int64_t seeds_total;
+    int64_t cands_total;
+    int64_t dropped_total;
 };
 
 // Work split of the current iteration, computed on the device.

@@ -1,0 +1,153 @@
+"""Batched form: B uneven frames in one CUDA graph with the OSOP control on the
+device. Each frame of a batch must reproduce, bit for bit, the single-frame
+path on that frame (same seed order with frame_id = base + f, same rounds,
+modes, supports and labels): the two share the per-seed arithmetic and the
+window sums are order-independent fixed point. The single-frame path is
+itself parity-tested against the FP64 oracle; the batch is also checked
+against the oracle directly on small frames."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity_util import matched_agreement, mode_errors, same_order_errors
+
+pytestmark = pytest.mark.gpu
+
+MODE_TOL = 1e-5
+
+
+def _frames_mixed(d=16):
+    frames = synth.batch_c4(seed=5, B=6, d=d, n_lo=500, n_hi=20000)
+    out = [(f.emb, f.mask) for f in frames]
+    rng = np.random.default_rng(9)
+    one = rng.standard_normal((1, d)).astype(np.float32)
+    bg = rng.standard_normal((300, d)).astype(np.float32)
+    out.insert(2, (one, None))                                    # a single pixel
+    out.insert(4, (bg, np.zeros(300, dtype=np.uint8)))            # all background
+    out.append((np.zeros((0, d), dtype=np.float32), None))        # no pixels at all
+    return out
+
+
+def _to_dev(frames):
+    import torch
+    embs = [torch.from_numpy(np.ascontiguousarray(e)).cuda() for e, _ in frames]
+    masks = [None if m is None else torch.from_numpy(np.ascontiguousarray(m)).cuda() for _, m in frames]
+    return embs, masks
+
+
+def _single(ms, emb, mask, frame_id, **cfg):
+    import torch
+    if emb.shape[0] == 0:
+        return np.zeros(0, np.int32), np.zeros((0, emb.shape[1]), np.float32), None
+    res = ms.cluster(emb, mask, frame_id=frame_id, **cfg)
+    torch.cuda.synchronize()
+    return res.labels.cpu().numpy(), res.modes.cpu().numpy(), res.stats
+
+
+def _batch(ms, embs, masks, **cfg):
+    c = ms.ms_config_default(dim=int(embs[0].shape[1]), **cfg)
+    b = ms.ms_batch_create(c, embs, masks if any(m is not None for m in masks) else None)
+    ms.ms_batch_run(b)
+    return b
+
+
+def _compare_to_single(ms, frames, **cfg):
+    embs, masks = _to_dev(frames)
+    b = _batch(ms, embs, masks, **cfg)
+    try:
+        for f in range(len(frames)):
+            lab_b = b.labels[f].cpu().numpy()
+            modes_b = ms.ms_batch_modes(b, f)
+            st_b = ms.ms_batch_stats(b, f)
+            lab_s, modes_s, st_s = _single(ms, embs[f], masks[f], f, **cfg)
+            assert np.array_equal(modes_b, modes_s), f
+            assert np.array_equal(lab_b, lab_s), f
+            if st_s is not None:
+                for k in ("rounds", "n_modes", "seeds", "seed_iters", "candidates", "dropped", "n_fg",
+                          "iters_total", "uncovered"):
+                    assert st_b[k] == st_s[k], (f, k, st_b[k], st_s[k])
+            else:
+                assert st_b["n_fg"] == 0 and st_b["n_modes"] == 0
+        tot = ms.ms_batch_stats(b, -1)
+        assert tot["n_fg"] == sum(ms.ms_batch_stats(b, f)["n_fg"] for f in range(len(frames)))
+    finally:
+        b.close()
+
+
+def test_batch_equals_single_frames_fp32(ms_lib):
+    _compare_to_single(ms_lib, _frames_mixed())
+
+
+def test_batch_equals_single_frames_bf16(ms_lib):
+    _compare_to_single(ms_lib, _frames_mixed(), precision=ms_lib.MS_BF16)
+
+
+def test_batch_equals_single_frames_d32(ms_lib):
+    frames = [(f.emb, f.mask) for f in synth.batch_c4(seed=6, B=3, d=32, n_lo=800, n_hi=6000)]
+    _compare_to_single(ms_lib, frames)
+
+
+def test_batch_all_seeds_algorithm1(ms_lib):
+    frames = [(synth.frame_c1_separable(seed=s).emb, None) for s in (1, 2)]
+    _compare_to_single(ms_lib, frames, all_seeds=1)
+
+
+def test_batch_matches_oracle(ms_lib):
+    fs = synth.batch_c4(seed=7, B=3, n_lo=600, n_hi=4000)
+    embs, masks = _to_dev([(f.emb, f.mask) for f in fs])
+    b = _batch(ms_lib, embs, masks)
+    try:
+        for i, f in enumerate(fs):
+            ref = oracle.run(f.emb, f.mask, frame_id=i)
+            labels = b.labels[i].cpu().numpy()
+            modes = ms_lib.ms_batch_modes(b, i)
+            st = ms_lib.ms_batch_stats(b, i)
+            assert modes.shape[0] > 0
+            assert mode_errors(modes, ref.modes).max() <= MODE_TOL
+            assert matched_agreement(ref.labels, labels) >= 0.999
+            assert ((labels == -1) == (ref.labels == -1)).all()
+            if modes.shape[0] == ref.modes.shape[0] and same_order_errors(modes, ref.modes).max() <= MODE_TOL:
+                safe = ref.label_margin > 1e-5
+                assert np.array_equal(labels[safe], ref.labels[safe])
+                assert st["seeds"] == ref.stats["seeds"] and st["rounds"] == ref.stats["rounds"]
+    finally:
+        b.close()
+
+
+def test_batch_rerun_and_new_inputs(ms_lib):
+    import torch
+    fs = synth.batch_c4(seed=8, B=4, n_lo=1000, n_hi=8000)
+    embs, masks = _to_dev([(f.emb, f.mask) for f in fs])
+    b = _batch(ms_lib, embs, masks)
+    try:
+        first = [t.clone() for t in b.labels]
+        ms_lib.ms_batch_run(b)
+        for a, c in zip(first, b.labels):
+            assert torch.equal(a, c)
+        # new embeddings in the same buffers: the graph reads them at launch
+        g = torch.Generator().manual_seed(3)
+        for t in embs:
+            t.copy_(torch.randn(t.shape, generator=g))
+        ms_lib.ms_batch_run(b)
+        for f in range(len(fs)):
+            lab_s, modes_s, _ = _single(ms_lib, embs[f], masks[f], f)
+            assert np.array_equal(ms_lib.ms_batch_modes(b, f), modes_s)
+            assert np.array_equal(b.labels[f].cpu().numpy(), lab_s)
+    finally:
+        b.close()
+
+
+def test_batch_rejects_bad_frames(ms_lib):
+    import torch
+    c = ms_lib.ms_config_default(dim=16)
+    e = torch.zeros((10, 16), device="cuda")
+    e[3, 0] = 1.0  # nine foreground vectors of zero norm
+    b = ms_lib.ms_batch_create(c, [e])
+    with pytest.raises(ms_lib.MsError) as err:
+        ms_lib.ms_batch_run(b)
+    assert err.value.status == ms_lib.MS_ERR_INVALID_ARG
+    b.close()
+    bad = ms_lib.ms_config_default(dim=32, precision=ms_lib.MS_BF16)
+    with pytest.raises(ms_lib.MsError):
+        ms_lib.ms_batch_create(bad, [torch.zeros((4, 32), device="cuda")])

@@ -4,10 +4,14 @@
 One step = B synthetic frames (512x512, 131072 foreground pixels, 60 vMF
 cells, kappa ~ U[20, 200], 2% outliers) clustered end to end on the GPU:
 ingest, every OSOP round (seed selection, shift iterations, merge, coverage,
-schedule) and labelling. Embeddings are resident in HBM before timing; L2 is
-flushed between steps. Prints one JSON line.
+N schedule) and labelling. The headline form is BF16-batched: all B frames in
+one CUDA graph (ms_batch_run), BF16 tensor-core shift with the FP32 recheck
+band. The plain FP32 form (one frame at a time, host round loop) is measured
+in the same run for comparison. Embeddings are resident in HBM before timing;
+L2 is flushed between steps. Prints one JSON line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--frames B] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--frames B]
+                  [--form bf16-batched|fp32-batched|fp32|bf16] [--impl ours|reference]
 
 With N > 1 (launched by torchrun) every rank clusters its own frames: replicas,
 weak scaling, no collective on the data path.
@@ -37,6 +41,8 @@ SHIFT_SRC = os.path.join(ROOT, "paper_2007_14283_gb300", "csrc", "ms_shift_fp32.
 SHIFT_TC_SRC = os.path.join(ROOT, "paper_2007_14283_gb300", "csrc", "ms_shift_tc.cu")
 C2_STATS = os.path.join(ROOT, "tests", "golden", "c2_oracle_stats.json")
 FP32_LANES_PER_SM = 128
+N_FG, DIM = 131072, 16
+FORMS = ("bf16-batched", "fp32-batched", "fp32", "bf16")
 
 
 def parse():
@@ -44,17 +50,22 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--frames", type=int, default=8, help="frames per step (per GPU)")
+    ap.add_argument("--frames", type=int, default=64, help="frames per step (per GPU)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--form", choices=["fp32", "bf16"], default="fp32")
-    ap.add_argument("--cpu-seeds", type=int, default=8192, help="seeds in the oracle's timed sample")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", choices=FORMS, default="bf16-batched")
+    ap.add_argument("--compare", default="fp32",
+                    help="comma-separated other forms measured on --compare-frames frames ('' for none)")
+    ap.add_argument("--compare-frames", type=int, default=8)
+    ap.add_argument("--compare-steps", type=int, default=2)
+    ap.add_argument("--cpu", choices=["full", "sample", "none"], default="full",
+                    help="oracle baseline: one full frame (also gives the label match), a seed sample, or none")
+    ap.add_argument("--cpu-seeds", type=int, default=8192, help="seeds in the oracle's sampled run")
     ap.add_argument("--e2e-steps", type=int, default=2)
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------ helpers
-def dist_setup(n_gpus):
+def dist_setup():
     import torch
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -74,23 +85,13 @@ def barrier(ws):
         dist.barrier()
 
 
-def max_over_ranks(v, ws):
+def reduce_over_ranks(v, ws, op):
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
     t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def sum_over_ranks(v, ws):
-    if ws == 1:
-        return v
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
 
 
@@ -139,6 +140,7 @@ class Clocks:
                 return None
         sm = [num(r[1]) for r in rows if num(r[1]) is not None]
         smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        power = [num(r[3]) for r in rows if num(r[3]) is not None]
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
@@ -146,6 +148,7 @@ class Clocks:
                 if v.lower() in ("active", "1", "yes"):
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_median": statistics.median(power) if power else None,
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
@@ -156,17 +159,17 @@ def load_peaks():
         return {}
 
 
-def shift_traffic_per_unit(form):
-    """dram bytes per seed-iteration of the shift kernel from the committed ncu
+def shift_traffic_per_unit(kernel):
+    """DRAM bytes per seed-iteration of the shift kernel from the committed ncu
     summary, valid only while the kernel source is unchanged."""
-    name, src = (("k_shift_tc", SHIFT_TC_SRC) if form == "bf16" else ("k_shift_fp32", SHIFT_SRC))
+    src = SHIFT_TC_SRC if kernel == "k_shift_tc" else SHIFT_SRC
     try:
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         for line in open(TRAFFIC):
             if line.startswith("#") or not line.strip():
                 continue
-            kernel, per_unit, src_hash = line.split()[:3]
-            if kernel == name and src_hash == h:
+            name, per_unit, src_hash = line.split()[:3]
+            if name == kernel and src_hash == h:
                 return float(per_unit)
     except (OSError, ValueError):
         pass
@@ -185,9 +188,13 @@ def c2_seed_iters_per_frame():
         return None
 
 
+def host_threads():
+    return int(os.environ.get("OMP_NUM_THREADS", "0")) or len(os.sched_getaffinity(0))
+
+
 def oracle_sample(frame, n_seeds):
     """Time the oracle's shift rounds on the first n_seeds positions of the
-    frame's seed order; returns (seconds, seed-iterations, threads)."""
+    frame's seed order; returns (seconds, seed-iterations)."""
     import numpy as np
     import oracle
     P, pn, _ = oracle.normalize(frame.emb, frame.mask)
@@ -195,15 +202,52 @@ def oracle_sample(frame, n_seeds):
     X0 = P[np.asarray(perm)]
     t0 = time.perf_counter()
     r = oracle.shift_round(P, pn, X0, gamma=0.9)
-    dt = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or len(os.sched_getaffinity(0))
-    return dt, r["seed_iters"], threads
+    return time.perf_counter() - t0, r["seed_iters"]
 
 
-# ------------------------------------------------------------------ arms
-def run_reference(args, rank, ws):
+def label_match(gpu_labels, ref_labels, gpu_modes, ref_modes):
+    """Share of foreground pixels labelled identically. Both sides keep modes
+    in the same deterministic order, so when the mode lists agree one to one
+    (same count, 1 - cos <= 1e-5 pairwise in order) the maps are compared
+    index by index; otherwise clusters are matched greedily by overlap (a
+    lower bound on the optimal matching)."""
+    import numpy as np
+    a, b = np.asarray(ref_labels), np.asarray(gpu_labels)
+    fg = a >= 0
+    bg_ok = bool(((a < 0) == (b < 0)).all())
+    a, b = a[fg], b[fg]
+    g = np.asarray(gpu_modes, np.float64)
+    r = np.asarray(ref_modes, np.float64)
+    errs = None
+    if g.shape == r.shape and g.size:
+        errs = 1.0 - (g * r).sum(1) / (np.linalg.norm(g, axis=1) * np.linalg.norm(r, axis=1))
+    if errs is not None and errs.max() <= 1e-5:
+        return float((a == b).mean()), "same mode order", float(errs.max()), bg_ok
+    pairs = a.astype(np.int64) * (int(b.max()) + 1) + b
+    key, cnt = np.unique(pairs, return_counts=True)
+    order = np.argsort(-cnt, kind="stable")
+    used_a, used_b, hit = set(), set(), 0
+    nb = int(b.max()) + 1
+    for k, c in zip(key[order], cnt[order]):
+        ia, ib = int(k // nb), int(k % nb)
+        if ia in used_a or ib in used_b:
+            continue
+        used_a.add(ia)
+        used_b.add(ib)
+        hit += int(c)
+    err = None
+    if g.size and r.size:
+        gn = g / np.linalg.norm(g, axis=1, keepdims=True)
+        rn = r / np.linalg.norm(r, axis=1, keepdims=True)
+        err = float((1.0 - (gn @ rn.T).max(axis=1)).max())
+    return hit / max(1, a.size), "greedy overlap matching", err, bg_ok
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank):
     """The FP64 oracle as it stands on the host cores: each step times a
-    bounded sample and scales it to frames/s."""
+    bounded sample (the first --cpu-seeds seeds of a frame's order shifted to
+    the gamma stop) and scales it to frames/s."""
     if rank != 0:
         return
     frame = c2_frames(0, 1)[0]
@@ -212,11 +256,10 @@ def run_reference(args, rank, ws):
         oracle_sample(frame, max(16, args.cpu_seeds // 8))
     times, its = [], []
     for _ in range(args.steps):
-        dt, si, threads = oracle_sample(frame, args.cpu_seeds)
+        dt, si = oracle_sample(frame, args.cpu_seeds)
         times.append(dt)
         its.append(si)
-    sec_per_si = sum(times) / sum(its)
-    frame_s = sec_per_si * per_frame if per_frame else float("nan")
+    frame_s = sum(times) / sum(its) * per_frame if per_frame else float("nan")
     value = 1.0 / frame_s
     sample = (f"{args.cpu_seeds} seeds of the frame's seed order shifted to the gamma stop by the oracle "
               f"({sum(its) // args.steps} seed-iterations per step), scaled by the oracle's "
@@ -225,158 +268,242 @@ def run_reference(args, rank, ws):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic vMF frames", "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": threads, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": host_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, rank, ws, local):
-    import numpy as np
-    import torch
+# ------------------------------------------------------------------ our arm
+class Runner:
+    """One form of the method over a fixed list of device-resident frames."""
 
-    import paper_2007_14283_gb300 as ms
-    ms.load()
-    dev = torch.device("cuda", torch.cuda.current_device())
-    frames = c2_frames(rank, args.frames)
-    embs = [torch.from_numpy(f.emb).to(dev) for f in frames]
-    masks = [torch.from_numpy(f.mask).to(dev) for f in frames]
-    labels = [torch.empty(f.emb.shape[0], dtype=torch.int32, device=dev) for f in frames]
-    cfg = ms.ms_config_default(dim=16, precision=ms.MS_BF16 if args.form == "bf16" else ms.MS_FP32)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
+    def __init__(self, ms, form, frames, dev):
+        import torch
+        self.ms, self.form, self.frames = ms, form, frames
+        self.batched = form.endswith("batched")
+        prec = ms.MS_BF16 if form.startswith("bf16") else ms.MS_FP32
+        self.cfg = ms.ms_config_default(dim=DIM, precision=prec)
+        self.embs = [torch.from_numpy(f.emb).to(dev) for f in frames]
+        self.masks = [torch.from_numpy(f.mask).to(dev) for f in frames]
+        if self.batched:
+            self.batch = ms.ms_batch_create(self.cfg, self.embs, self.masks)
+            ms.ms_batch_profile(self.batch, True)
+            self.labels = self.batch.labels
+        else:
+            self.labels = [torch.empty(f.emb.shape[0], dtype=torch.int32, device=dev) for f in frames]
 
-    def one_step(profile):
-        agg = {"frames": 0, "launches": 0, "shift_ms": 0.0, "shift_launches": 0, "seed_iters": 0, "modes": 0}
-        for e, m, l in zip(embs, masks, labels):
-            ctx = ms.ms_create(cfg, e, m)
-            if profile:
-                ms.ms_profile(ctx, True)
+    def step(self):
+        """Cluster every frame once; returns counters of this step."""
+        ms = self.ms
+        if self.batched:
+            ms.ms_batch_run(self.batch)
+            st = ms.ms_batch_stats(self.batch, -1)
+            return {"frames": len(self.frames), "launches": st["launches"], "shift_ms": st["shift_ms"],
+                    "shift_launches": st["shift_launches"], "seed_iters": st["seed_iters"],
+                    "modes": st["n_modes"], "passes": st["reserved0"]}
+        agg = {"frames": 0, "launches": 0, "shift_ms": 0.0, "shift_launches": 0, "seed_iters": 0, "modes": 0,
+               "passes": 0}
+        for f, (e, m, l) in enumerate(zip(self.embs, self.masks, self.labels)):
+            self.cfg.frame_id = f  # the batch gives frame f the seed order of frame_id f
+            ctx = ms.ms_create(self.cfg, e, m)
+            ms.ms_profile(ctx, True)
             ms.ms_run(ctx, l)
             st = ms.ms_stats_get(ctx)
             ctx.close()
             agg["frames"] += 1
-            agg["launches"] += st["launches"]
-            agg["shift_ms"] += st["shift_ms"]
-            agg["shift_launches"] += st["shift_launches"]
-            agg["seed_iters"] += st["seed_iters"]
+            for k in ("launches", "shift_ms", "shift_launches", "seed_iters"):
+                agg[k] += st[k]
             agg["modes"] += st["n_modes"]
         return agg
 
-    for _ in range(args.warmup):
-        one_step(False)
-    torch.cuda.synchronize()
+    def modes(self, f):
+        ms = self.ms
+        if self.batched:
+            return ms.ms_batch_modes(self.batch, f)
+        return ms.cluster(self.embs[f], self.masks[f], precision=self.cfg.precision,
+                          frame_id=f).modes.cpu().numpy()
 
-    clocks = Clocks(local)
-    clocks.start()
-    step_ms = []
-    tot = {"frames": 0, "launches": 0, "shift_ms": 0.0, "shift_launches": 0, "seed_iters": 0, "modes": 0}
-    for _ in range(args.steps):
+    def close(self):
+        if self.batched:
+            self.batch.close()
+
+
+def timed(runner, steps, warmup, ws, flush, stream):
+    import torch
+    for _ in range(warmup):
+        runner.step()
+    torch.cuda.synchronize()
+    step_ms, tot = [], {}
+    for _ in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
         barrier(ws)
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        agg = one_step(True)
+        agg = runner.step()
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier(ws)
         step_ms.append(ev0.elapsed_time(ev1))
-        for k in tot:
-            tot[k] += agg[k]
-    clk = clocks.stop()
-    t_total = max_over_ranks(sum(step_ms) / 1e3, ws)
-    frames_all = sum_over_ranks(tot["frames"], ws)
-    value = frames_all / t_total
+        for k, v in agg.items():
+            tot[k] = tot.get(k, 0) + v
+    return step_ms, tot
 
-    # roofline of the dominant kernel (shift): algorithmic flops 4*d*n per seed-iteration
-    n_fg, d = 131072, 16
-    flops = 4.0 * d * n_fg * tot["seed_iters"]
+
+def roofline_of(form, tot, step_ms, clk, n_sm):
+    flops = 4.0 * DIM * N_FG * tot["seed_iters"]
     achieved = flops / (tot["shift_ms"] / 1e3) / 1e12 if tot["shift_ms"] > 0 else None
     sm_mhz = clk.get("sm_mhz") or 1455.0
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    tpu = shift_traffic_per_unit(args.form)
-    if args.form == "bf16":
+    if form.startswith("bf16"):
         peaks = load_peaks()
         peak = peaks.get("bf16_tflops_sustained") or 1700.0
         bound, kernel = "tensor", "k_shift_tc"
-        peak_source = ("measured cuBLAS bf16 dense, sustained (MEASURED_PEAKS.json)"
-                       if peaks.get("bf16_tflops_sustained") else "fallback 1.7 PFLOP/s sustained")
+        peak_source = ("of measured: cuBLAS bf16 dense, sustained (MEASURED_PEAKS.json)"
+                       if peaks.get("bf16_tflops_sustained") else "of fallback: 1.7 PFLOP/s sustained")
     else:
         peak = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
         bound, kernel = "alu", "k_shift_fp32"
         peak_source = (f"FP32 FMA peak = {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_mhz:.0f} MHz "
                        "(median SM clock sampled under load)")
-    roofline = {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                "traffic": (tpu * tot["seed_iters"] / tot["shift_launches"]) if (tpu and tot["shift_launches"]) else None,
-                "peak_source": peak_source,
-                "algorithmic": "4*d*n flops per seed-iteration (d=16, n=131072)",
-                "shift_share_of_step": (tot["shift_ms"] / sum(step_ms)) if step_ms else None,
-                "shift_launches": tot["shift_launches"], "avg_launch_ms": tot["shift_ms"] / max(1, tot["shift_launches"])}
-
-    # end to end through the host-buffer entry point (pinned buffers)
-    e2e = None
-    if args.e2e_steps > 0:
-        e2e = e2e_leg(args, ms, cfg, frames, labels, ws)
-
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        per_frame = c2_seed_iters_per_frame()
-        dt, si, threads = oracle_sample(frames[0], args.cpu_seeds)
-        if per_frame:
-            cpu = {"value": 1.0 / (dt / si * per_frame), "unit": "frames/s", "cores": threads, "kind": "oracle",
-                   "sample": f"{args.cpu_seeds} seeds of frame 0's seed order shifted to the gamma stop "
-                             f"({si} seed-iterations, {dt:.1f} s), scaled by the oracle's {int(per_frame)} "
-                             f"seed-iterations per full frame; merge/cover/label not included"}
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32" if args.form == "bf16" else "f32",
-                "data": "synthetic vMF frames shaped like 512x512 microscopy (seeded generator)",
-                "config": {"workload": WORKLOAD, "form": args.form, "frames_per_step": args.frames,
-                           "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{ws}",
-                           "seed_iters_per_frame": tot["seed_iters"] / max(1, tot["frames"]),
-                           "modes_per_frame": tot["modes"] / max(1, tot["frames"])},
-                "roofline": roofline, "cpu_baseline": cpu,
-                "e2e": e2e,
-                "gpu_launches": int(sum_over_ranks(tot["launches"], ws)), "clocks": clk}
-        print(json.dumps(line), flush=True)
+    tpu = shift_traffic_per_unit(kernel)
+    per_launch_si = tot["seed_iters"] / max(1, tot["shift_launches"])
+    return {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": (tpu * per_launch_si) if tpu else None,
+            "peak_source": peak_source,
+            "algorithmic": f"4*d*n flops per seed-iteration (d={DIM}, n={N_FG}); "
+                           f"{per_launch_si:.0f} seed-iterations per launch on average",
+            "timing": ("GPU global-timer ticks in one-thread kernels around each shift launch inside the graph "
+                       "(includes one launch gap per launch)" if form.endswith("batched")
+                       else "CUDA events around each shift launch on the library's stream"),
+            "shift_share_of_step": (tot["shift_ms"] / sum(step_ms)) if step_ms else None,
+            "shift_launches": tot["shift_launches"],
+            "avg_launch_ms": tot["shift_ms"] / max(1, tot["shift_launches"])}
 
 
-def e2e_leg(args, ms, cfg, frames, labels, ws):
-    """Frames/s through ms_run_host: pinned host buffers in, labels out."""
+def e2e_leg(args, runner, ws):
+    """Frames/s through the host-buffer entry points (pinned buffers in, labels out)."""
     import torch
+    ms = runner.ms
+    frames = runner.frames
     h_embs = [torch.from_numpy(f.emb).pin_memory() for f in frames]
     h_masks = [torch.from_numpy(f.mask).pin_memory() for f in frames]
     h_labels = [torch.empty(f.emb.shape[0], dtype=torch.int32).pin_memory() for f in frames]
     h2d = sum(e.numel() * 4 + m.numel() for e, m in zip(h_embs, h_masks))
     d2h = sum(l.numel() * 4 for l in h_labels)
-    ms.ms_run_host(cfg, h_embs[0], h_masks[0], h_labels[0])
+
+    def one():
+        if runner.batched:
+            ms.ms_batch_run_host(runner.batch, h_embs, h_masks, h_labels)
+        else:
+            for e, m, l in zip(h_embs, h_masks, h_labels):
+                ms.ms_run_host(runner.cfg, e, m, l)
+    one()
     torch.cuda.synchronize()
     barrier(ws)
     t0 = time.perf_counter()
-    e2e_steps = args.e2e_steps
-    for _ in range(e2e_steps):
-        for e, m, l in zip(h_embs, h_masks, h_labels):
-            ms.ms_run_host(cfg, e, m, l)
+    for _ in range(args.e2e_steps):
+        one()
     torch.cuda.synchronize()
-    t_e2e = max_over_ranks(time.perf_counter() - t0, ws)
-    e2e_value = sum_over_ranks(e2e_steps * len(frames), ws) / t_e2e
-    # the host-buffer labels equal the device-resident run's labels
-    assert torch.equal(h_labels[0], labels[0].cpu()), "host-buffer run disagrees with the device run"
+    t = reduce_over_ranks(time.perf_counter() - t0, ws, "max")
+    value = reduce_over_ranks(args.e2e_steps * len(frames), ws, "sum") / t
+    assert torch.equal(h_labels[0], runner.labels[0].cpu()), "host-buffer run disagrees with the device run"
+    api = "ms_batch_run_host" if runner.batched else "ms_run_host"
+    return {"value": value, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "api": api, "steps": args.e2e_steps}
 
-    return {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+def run_ours(args, rank, ws, local):
+    import torch
+
+    import paper_2007_14283_gb300 as ms
+    ms.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    frames = c2_frames(rank, args.frames)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    main = Runner(ms, args.form, frames, dev)
+    clocks = Clocks(local)
+    clocks.start()
+    step_ms, tot = timed(main, args.steps, args.warmup, ws, flush, stream)
+    clk = clocks.stop()
+    t_total = reduce_over_ranks(sum(step_ms) / 1e3, ws, "max")
+    value = reduce_over_ranks(tot["frames"], ws, "sum") / t_total
+    roofline = roofline_of(args.form, tot, step_ms, clk, n_sm)
+    forms = {args.form: {"value": value, "frames_per_step": args.frames, "steps": args.steps,
+                         "ms_per_frame": sum(step_ms) / max(1, tot["frames"]),
+                         "roofline_frac": roofline["frac"]}}
+    e2e = e2e_leg(args, main, ws) if args.e2e_steps > 0 else None
+
+    for other in [f for f in args.compare.split(",") if f and f != args.form]:
+        r = Runner(ms, other, frames[: args.compare_frames], dev)
+        c_clocks = Clocks(local)
+        c_clocks.start()
+        sm_, tt = timed(r, args.compare_steps, 1, ws, flush, stream)
+        c_clk = c_clocks.stop()
+        v = reduce_over_ranks(tt["frames"], ws, "sum") / reduce_over_ranks(sum(sm_) / 1e3, ws, "max")
+        rf = roofline_of(other, tt, sm_, c_clk, n_sm)
+        same = all(torch.equal(a, b) for a, b in zip(r.labels, main.labels)) if other.split("-")[0] == \
+            args.form.split("-")[0] else None
+        forms[other] = {"value": v, "frames_per_step": len(r.frames), "steps": args.compare_steps,
+                        "ms_per_frame": sum(sm_) / max(1, tt["frames"]), "roofline_frac": rf["frac"],
+                        "roofline_bound": rf["bound"], "labels_identical_to_headline": same,
+                        "clocks_sm_mhz": c_clk.get("sm_mhz")}
+        r.close()
+
+    cpu, parity = None, None
+    if rank == 0 and args.cpu != "none":
+        import oracle
+        if args.cpu == "full":
+            f0 = frames[0]
+            t0 = time.perf_counter()
+            ref = oracle.run(f0.emb, f0.mask)
+            dt = time.perf_counter() - t0
+            cpu = {"value": 1.0 / dt, "unit": "frames/s", "cores": host_threads(), "kind": "oracle",
+                   "sample": f"one full frame (frame 0 of the step): every OSOP round, merge, coverage and "
+                             f"labelling in FP64, {dt:.1f} s"}
+            match, how, err, bg_ok = label_match(main.labels[0].cpu().numpy(), ref.labels, main.modes(0),
+                                                 ref.modes)
+            parity = {"frame": 0, "label_match": match, "method": how, "mode_err_max": err,
+                      "background_identical": bg_ok, "modes_gpu": int(main.modes(0).shape[0]),
+                      "modes_oracle": int(ref.modes.shape[0])}
+        else:
+            per_frame = c2_seed_iters_per_frame()
+            dt, si = oracle_sample(frames[0], args.cpu_seeds)
+            if per_frame:
+                cpu = {"value": 1.0 / (dt / si * per_frame), "unit": "frames/s", "cores": host_threads(),
+                       "kind": "oracle",
+                       "sample": f"{args.cpu_seeds} seeds of frame 0's seed order shifted to the gamma stop "
+                                 f"({si} seed-iterations, {dt:.1f} s), scaled by the oracle's {int(per_frame)} "
+                                 f"seed-iterations per full frame; merge/cover/label not included"}
+    main.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16+f32" if args.form.startswith("bf16") else "f32",
+                "data": "synthetic vMF frames shaped like 512x512 microscopy (seeded generator)",
+                "config": {"workload": WORKLOAD, "form": args.form, "frames_per_step": args.frames,
+                           "l2": "flushed (256 MB write) before every step; inputs also exceed L2",
+                           "parallelism": f"replicas x{ws}",
+                           "seed_iters_per_frame": tot["seed_iters"] / max(1, tot["frames"]),
+                           "modes_per_frame": tot["modes"] / max(1, tot["frames"]),
+                           "graph_passes_per_step": tot.get("passes", 0) / max(1, args.steps)},
+                "roofline": roofline, "forms": forms, "parity_vs_oracle": parity, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": int(reduce_over_ranks(tot["launches"], ws, "sum")), "clocks": clk}
+        print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
     if args.impl == "reference":
-        rank = int(os.environ.get("RANK", "0"))
-        run_reference(args, rank, int(os.environ.get("WORLD_SIZE", "1")))
+        run_reference(args, int(os.environ.get("RANK", "0")))
         return
-    rank, ws, local = dist_setup(args.gpus)
+    rank, ws, local = dist_setup()
     run_ours(args, rank, ws, local)
     if ws > 1:
         import torch.distributed as dist

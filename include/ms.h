@@ -288,8 +288,13 @@ MS_API ms_status ms_window_sums_static(const float* d_X, int32_t m, const float*
  * returns MS_ERR_INVALID_ARG if a foreground vector had zero or non-finite
  * norm, MS_ERR_TIMEOUT if a bounded device wait gave up.
  * ms_batch_stats fills *out for frame f (or summed over all frames for
- * f = -1) from the last synchronised run; launches = kernels in one pass of
- * the loop body. ms_batch_modes copies frame f's K kept modes, float32
+ * f = -1) from the last synchronised run; for f = -1 it also gives launches
+ * (kernels the graph ran), reserved0 (passes of the loop body), band_pairs
+ * and, with profiling on, shift_ms / shift_launches (time of the shift
+ * kernels that had work, from the GPU global timer read by one-thread
+ * kernels placed before and after each shift launch; includes one launch gap
+ * each). ms_batch_profile(b, 1) rebuilds the graph with those timer kernels
+ * (0 removes them); it synchronises the stream. ms_batch_modes copies frame f's K kept modes, float32
  * [K, dim], to h_out (cap >= K; h_out NULL only reports K). ms_batch_destroy
  * synchronises the stream and frees everything. */
 typedef struct ms_batch ms_batch;
@@ -297,7 +302,17 @@ MS_API ms_status ms_batch_create(const ms_config* cfg, int32_t B, const float* c
                                  const uint8_t* const* d_masks, const int64_t* n_pixels,
                                  int32_t* const* d_labels, void* stream, ms_batch** out);
 MS_API ms_status ms_batch_run(ms_batch* b, int32_t sync);
+/* ms_batch_run from HOST memory: copies every frame's embeddings (and mask,
+ * for frames bound with one) from h_embs[f] / h_masks[f] into the device
+ * buffers bound at ms_batch_create, runs the graph, copies each frame's
+ * labels into h_labels[f] (int32 [n_pixels[f]]), and synchronises. One
+ * cudaMemcpyAsync per buffer on the batch's stream; pinned host buffers make
+ * them asynchronous. Host arrays as for ms_batch_create (entries of empty
+ * frames are ignored). Errors as ms_batch_run with sync. */
+MS_API ms_status ms_batch_run_host(ms_batch* b, const float* const* h_embs, const uint8_t* const* h_masks,
+                                   int32_t* const* h_labels);
 MS_API ms_status ms_batch_stats(const ms_batch* b, int32_t frame, ms_stats* out);
+MS_API ms_status ms_batch_profile(ms_batch* b, int32_t enable);
 MS_API ms_status ms_batch_modes(const ms_batch* b, int32_t frame, float* h_out, int32_t cap,
                                 int32_t* n_modes_out);
 MS_API void ms_batch_destroy(ms_batch* b);

@@ -85,7 +85,9 @@ _SIGNATURES = {
     "ms_batch_create": (_i32, [ctypes.POINTER(ms_config), _i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                _pi64, ctypes.POINTER(_vp), _vp, ctypes.POINTER(_vp)]),
     "ms_batch_run": (_i32, [_vp, _i32]),
+    "ms_batch_run_host": (_i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "ms_batch_stats": (_i32, [_vp, _i32, ctypes.POINTER(ms_stats)]),
+    "ms_batch_profile": (_i32, [_vp, _i32]),
     "ms_batch_modes": (_i32, [_vp, _i32, _vp, _i32, _pi32]),
     "ms_batch_destroy": (None, [_vp]),
 }
@@ -363,10 +365,33 @@ def ms_batch_run(b: Batch, sync: bool = True):
     _check(load().ms_batch_run(b.handle, 1 if sync else 0))
 
 
+def ms_batch_run_host(b: Batch, h_embs, h_masks, h_labels):
+    """Host tensors (CPU, ideally pinned): h_embs float32 [n_f, dim], h_masks
+    uint8 [n_f] or None, h_labels int32 [n_f] (written)."""
+    import torch
+
+    def hp(t, dtype, what):
+        if t is None:
+            return None
+        if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+            raise ValueError(f"{what} must be a contiguous CPU tensor of {dtype}")
+        return ctypes.c_void_p(t.data_ptr())
+    B = len(h_embs)
+    arr = _vp * max(B, 1)
+    e = arr(*[hp(t, torch.float32, "emb") for t in h_embs])
+    m = None if h_masks is None else arr(*[hp(t, torch.uint8, "mask") for t in h_masks])
+    lab = arr(*[hp(t, torch.int32, "labels") for t in h_labels])
+    _check(load().ms_batch_run_host(b.handle, e, m, lab))
+
+
 def ms_batch_stats(b: Batch, frame: int = -1) -> dict:
     st = ms_stats()
     _check(load().ms_batch_stats(b.handle, frame, ctypes.byref(st)))
     return {k: getattr(st, k) for k, _ in ms_stats._fields_}
+
+
+def ms_batch_profile(b: Batch, enable: bool = True):
+    _check(load().ms_batch_profile(b.handle, 1 if enable else 0))
 
 
 def ms_batch_modes(b: Batch, frame: int):

@@ -38,7 +38,7 @@ struct ms_batch {
     ms::BState* h_states;     // pinned copy for statistics
     ms::BPlan plan;
     int32_t* blk_off;         // [B + 1] block work list of the current merge/cover/label kernel
-    int32_t* misc;            // [0] passes, [1] status, [2..3] band pairs (u64)
+    int32_t* misc;            // [0] passes, [1] status, u64 at [2] band pairs, [4] tick, [6] shift ns, [8] shift launches
     float* P32;
     int32_t* pix;
     uint8_t* covered;
@@ -62,7 +62,12 @@ struct ms_batch {
     CUtensorMap pmap;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
-    int64_t launches_per_run;
+    int64_t body_launches;    // kernels per pass of the loop body
+    int64_t fixed_launches;   // set-up and labelling kernels
+    bool prof;                // body brackets the shift launch with timer ticks
+    int32_t h_misc[16];       // host copy of misc after the last synchronised run
+    std::vector<ms::BFrame> hf;   // host copy of the frame table (device pointers of every frame)
+    std::vector<int32_t*> h_labels;  // device label buffers
 };
 
 namespace ms {
@@ -863,6 +868,21 @@ __global__ void k_b_schedule(BState* states, int B, double P, double L, double H
     st.phase = fin ? kFinished : kNeedSeed;
 }
 
+// Profiling ticks around the shift launch (kernels of one stream run in
+// order, so stop - start spans the shift kernel plus one launch gap). The
+// global timer counts nanoseconds.
+__global__ void k_b_tick(int* misc, const int32_t* __restrict__ item_total, int stop) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    unsigned long long* m = reinterpret_cast<unsigned long long*>(misc);
+    if (!stop) {
+        m[2] = t;
+    } else if (*item_total > 0) {
+        m[3] += t - m[2];
+        m[4] += 1ull;
+    }
+}
+
 __global__ void k_b_cond(const BState* __restrict__ states, int B, int* misc, cudaGraphConditionalHandle h) {
     if (threadIdx.x != 0) return;
     int live = 0;
@@ -941,6 +961,10 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     k_b_plan<<<1, kIT, 0, s>>>(b->frames, b->states, B, b->plan, target, b->cfg.batch_split ? 0 : target,
                                b->tc ? 1 : 0);
     LAUNCHED("k_b_plan");
+    if (b->prof) {
+        k_b_tick<<<1, 1, 0, s>>>(b->misc, b->plan.item_off + B, 0);
+        LAUNCHED("k_b_tick");
+    }
     ms_status st;
     if (b->tc)
         st = launch_shift_tc_batch(b->pmap, b->P32, b->X, b->acc, cf, b->frames, b->states, b->plan, b->act[0],
@@ -950,6 +974,10 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
                                      b->act[1], B, b->f32_grid, s);
     if (st != MS_OK) return st;
     ++nl;
+    if (b->prof) {
+        k_b_tick<<<1, 1, 0, s>>>(b->misc, b->plan.item_off + B, 1);
+        LAUNCHED("k_b_tick");
+    }
     k_b_finalize<Dp><<<G, 256, 0, s>>>(b->frames, b->states, B, b->plan, b->act[0], b->act[1], b->acc, b->X,
                                        b->sstate, b->support, b->cfg.tol);
     LAUNCHED("k_b_finalize");
@@ -1074,8 +1102,17 @@ ms_status build_graph(ms_batch* b) {
     if (st != MS_OK) return st;
     if (st2 != MS_OK) return st2;
     MS_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
-    b->launches_per_run = nl;
+    b->body_launches = nl;
+    b->fixed_launches = (b->tc ? 5 : 4) + 2;
     return MS_OK;
+}
+
+ms_status rebuild_graph(ms_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    return b->Dp == 16 ? build_graph<16>(b) : build_graph<32>(b);
 }
 
 void free_batch(ms_batch* b) {
@@ -1142,6 +1179,8 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
         free_batch(b);
         return set_error(MS_ERR_INVALID_ARG, "batch too large");
     }
+    b->hf = hf;
+    b->h_labels.assign(d_labels, d_labels + B);
     b->total_px = px > 0 ? px : 1;
     b->total_pk_rows = rows > 0 ? rows : 128;
     b->max_pk_rows = (b->max_np + 127) / 128 * 128;
@@ -1208,7 +1247,7 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
     if (s == MS_OK) s = cuda_check(cudaStreamSynchronize(b->stream), "sync");
     if (s == MS_OK && b->tc) s = tc_batch_setup();
     if (s == MS_OK && b->tc) s = encode_pk_map(b->Pk, (int)b->total_pk_rows, &b->pmap);
-    if (s == MS_OK) s = Dp == 16 ? build_graph<16>(b) : build_graph<32>(b);
+    if (s == MS_OK) s = rebuild_graph(b);
     if (s != MS_OK) {
         free_batch(b);
         return s;
@@ -1222,11 +1261,45 @@ extern "C" ms_status ms_batch_run(ms_batch* b, int32_t sync) {
     MS_CUDA(cudaGraphLaunch(b->exec, b->stream));
     if (!sync) return MS_OK;
     MS_CUDA(cudaMemcpyAsync(b->h_states, b->states, sizeof(BState) * b->B, cudaMemcpyDeviceToHost, b->stream));
-    int32_t misc[2] = {0, 0};
-    MS_CUDA(cudaMemcpyAsync(misc, b->misc, sizeof(misc), cudaMemcpyDeviceToHost, b->stream));
+    MS_CUDA(cudaMemcpyAsync(b->h_misc, b->misc, sizeof(b->h_misc), cudaMemcpyDeviceToHost, b->stream));
     MS_CUDA(cudaStreamSynchronize(b->stream));
+    const int32_t* misc = b->h_misc;
     if (misc[1] & 1) return set_error(MS_ERR_INVALID_ARG, "a foreground embedding has zero or non-finite norm");
     if (misc[1] & 2) return set_error(MS_ERR_TIMEOUT, "a bounded device wait or the pass limit was hit");
+    return MS_OK;
+}
+
+extern "C" ms_status ms_batch_run_host(ms_batch* b, const float* const* h_embs, const uint8_t* const* h_masks,
+                                      int32_t* const* h_labels) {
+    if (!b || !h_embs || !h_labels) return set_error(MS_ERR_INVALID_ARG, "NULL argument");
+    for (int f = 0; f < b->B; ++f) {
+        const BFrame& fr = b->hf[f];
+        if (fr.n_pixels == 0) continue;
+        if (!h_embs[f] || !h_labels[f]) return set_error(MS_ERR_INVALID_ARG, "frame %d: NULL host buffer", f);
+        if (fr.mask && (!h_masks || !h_masks[f]))
+            return set_error(MS_ERR_INVALID_ARG, "frame %d is masked: its host mask is required", f);
+    }
+    for (int f = 0; f < b->B; ++f) {
+        const BFrame& fr = b->hf[f];
+        if (fr.n_pixels == 0) continue;
+        MS_CUDA(cudaMemcpyAsync((void*)fr.emb, h_embs[f], sizeof(float) * (size_t)fr.n_pixels * b->d,
+                                cudaMemcpyHostToDevice, b->stream));
+        if (fr.mask)
+            MS_CUDA(cudaMemcpyAsync((void*)fr.mask, h_masks[f], (size_t)fr.n_pixels, cudaMemcpyHostToDevice,
+                                    b->stream));
+    }
+    MS_CUDA(cudaGraphLaunch(b->exec, b->stream));
+    for (int f = 0; f < b->B; ++f) {
+        const BFrame& fr = b->hf[f];
+        if (fr.n_pixels == 0) continue;
+        MS_CUDA(cudaMemcpyAsync(h_labels[f], b->h_labels[f], sizeof(int32_t) * (size_t)fr.n_pixels,
+                                cudaMemcpyDeviceToHost, b->stream));
+    }
+    MS_CUDA(cudaMemcpyAsync(b->h_states, b->states, sizeof(BState) * b->B, cudaMemcpyDeviceToHost, b->stream));
+    MS_CUDA(cudaMemcpyAsync(b->h_misc, b->misc, sizeof(b->h_misc), cudaMemcpyDeviceToHost, b->stream));
+    MS_CUDA(cudaStreamSynchronize(b->stream));
+    if (b->h_misc[1] & 1) return set_error(MS_ERR_INVALID_ARG, "a foreground embedding has zero or non-finite norm");
+    if (b->h_misc[1] & 2) return set_error(MS_ERR_TIMEOUT, "a bounded device wait or the pass limit was hit");
     return MS_OK;
 }
 
@@ -1247,8 +1320,23 @@ extern "C" ms_status ms_batch_stats(const ms_batch* b, int32_t frame, ms_stats* 
         out->uncovered += st.dc.n_uncovered;
     }
     out->workspace_bytes = (int64_t)b->ws_bytes;
-    out->launches = b->launches_per_run;
+    if (frame < 0) {
+        const unsigned long long* m = reinterpret_cast<const unsigned long long*>(b->h_misc);
+        out->launches = (int64_t)b->h_misc[0] * b->body_launches + b->fixed_launches;
+        out->band_pairs = (int64_t)m[1];
+        out->shift_ms = (double)m[3] * 1e-6;
+        out->shift_launches = (int64_t)m[4];
+        out->reserved0 = b->h_misc[0];  // loop passes
+    }
     return MS_OK;
+}
+
+extern "C" ms_status ms_batch_profile(ms_batch* b, int32_t enable) {
+    if (!b) return set_error(MS_ERR_INVALID_ARG, "batch is NULL");
+    if ((enable != 0) == b->prof) return MS_OK;
+    MS_CUDA(cudaStreamSynchronize(b->stream));
+    b->prof = enable != 0;
+    return rebuild_graph(b);
 }
 
 extern "C" ms_status ms_batch_modes(const ms_batch* b, int32_t frame, float* h_out, int32_t cap,

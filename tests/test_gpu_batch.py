@@ -93,10 +93,14 @@ def test_batch_all_seeds_algorithm1(ms_lib):
     _compare_to_single(ms_lib, frames, all_seeds=1)
 
 
-def test_batch_matches_oracle(ms_lib):
+@pytest.mark.parametrize("split,bf16", [(0, False), (1, False), (1, True)])
+def test_batch_matches_oracle(ms_lib, split, bf16):
+    # batch_split = 1 shares work items across frames by load, so window sums
+    # are cut differently from a single-frame run: held to the oracle bar only
     fs = synth.batch_c4(seed=7, B=3, n_lo=600, n_hi=4000)
     embs, masks = _to_dev([(f.emb, f.mask) for f in fs])
-    b = _batch(ms_lib, embs, masks)
+    b = _batch(ms_lib, embs, masks, batch_split=split,
+               precision=ms_lib.MS_BF16 if bf16 else ms_lib.MS_FP32)
     try:
         for i, f in enumerate(fs):
             ref = oracle.run(f.emb, f.mask, frame_id=i)
@@ -151,3 +155,29 @@ def test_batch_rejects_bad_frames(ms_lib):
     bad = ms_lib.ms_config_default(dim=32, precision=ms_lib.MS_BF16)
     with pytest.raises(ms_lib.MsError):
         ms_lib.ms_batch_create(bad, [torch.zeros((4, 32), device="cuda")])
+
+
+def test_batch_host_buffers_and_profile(ms_lib):
+    import torch
+    fs = synth.batch_c4(seed=10, B=3, n_lo=1000, n_hi=5000)
+    embs, masks = _to_dev([(f.emb, f.mask) for f in fs])
+    b = _batch(ms_lib, embs, masks, precision=ms_lib.MS_BF16)
+    try:
+        ref = [t.cpu().clone() for t in b.labels]
+        st0 = ms_lib.ms_batch_stats(b, -1)
+        assert st0["shift_launches"] == 0 and st0["launches"] > 0
+        ms_lib.ms_batch_profile(b, True)
+        h_e = [torch.from_numpy(f.emb).pin_memory() for f in fs]
+        h_m = [torch.from_numpy(f.mask).pin_memory() for f in fs]
+        h_l = [torch.full((f.emb.shape[0],), 7, dtype=torch.int32).pin_memory() for f in fs]
+        for t in embs:
+            t.zero_()  # the host call must copy the inputs in again
+        ms_lib.ms_batch_run_host(b, h_e, h_m, h_l)
+        for a, c in zip(ref, h_l):
+            assert torch.equal(a, c)
+        st = ms_lib.ms_batch_stats(b, -1)
+        assert st["shift_launches"] > 0 and st["shift_ms"] > 0.0
+        assert st["seed_iters"] == st0["seed_iters"] and st["n_modes"] == st0["n_modes"]
+        assert st["launches"] > st0["launches"]  # two timer kernels per pass
+    finally:
+        b.close()

@@ -301,9 +301,9 @@ class Runner:
             st = ms.ms_batch_stats(self.batch, -1)
             return {"frames": len(self.frames), "launches": st["launches"], "shift_ms": st["shift_ms"],
                     "shift_launches": st["shift_launches"], "seed_iters": st["seed_iters"],
-                    "modes": st["n_modes"], "passes": st["reserved0"]}
+                    "modes": st["n_modes"], "passes": st["reserved0"], "band_pairs": st["band_pairs"]}
         agg = {"frames": 0, "launches": 0, "shift_ms": 0.0, "shift_launches": 0, "seed_iters": 0, "modes": 0,
-               "passes": 0}
+               "passes": 0, "band_pairs": 0}
         for f, (e, m, l) in enumerate(zip(self.embs, self.masks, self.labels)):
             self.cfg.frame_id = f  # the batch gives frame f the seed order of frame_id f
             ctx = ms.ms_create(self.cfg, e, m)
@@ -312,7 +312,7 @@ class Runner:
             st = ms.ms_stats_get(ctx)
             ctx.close()
             agg["frames"] += 1
-            for k in ("launches", "shift_ms", "shift_launches", "seed_iters"):
+            for k in ("launches", "shift_ms", "shift_launches", "seed_iters", "band_pairs"):
                 agg[k] += st[k]
             agg["modes"] += st["n_modes"]
         return agg
@@ -492,7 +492,9 @@ def run_ours(args, rank, ws, local):
                            "parallelism": f"replicas x{ws}",
                            "seed_iters_per_frame": tot["seed_iters"] / max(1, tot["frames"]),
                            "modes_per_frame": tot["modes"] / max(1, tot["frames"]),
-                           "graph_passes_per_step": tot.get("passes", 0) / max(1, args.steps)},
+                           "graph_passes_per_step": tot.get("passes", 0) / max(1, args.steps),
+                           "fp32_rechecked_pair_fraction": tot.get("band_pairs", 0) /
+                           max(1.0, float(tot["seed_iters"]) * N_FG)},
                 "roofline": roofline, "forms": forms, "parity_vs_oracle": parity, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": int(reduce_over_ranks(tot["launches"], ws, "sum")), "clocks": clk}
         print(json.dumps(line), flush=True)

@@ -248,7 +248,7 @@ __global__ void k_b_compact(const BFrame* __restrict__ frames, int nblk_max, con
         nrm = 1.f;
     }
     float* p = P32 + pos * Dp;
-    for (int k = 0; k < d; ++k) p[k] = e[k] / nrm;
+    for (int k = 0; k < d; ++k) p[k] = flush_tiny(e[k] / nrm);
     for (int k = d; k < Dp; ++k) p[k] = 0.f;
     pix[pos] = (int32_t)i;
 }

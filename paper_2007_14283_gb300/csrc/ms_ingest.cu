@@ -87,7 +87,7 @@ __global__ void k_compact_normalise(const float* __restrict__ emb, const uint8_t
         nrm = 1.f;
     }
     float* p = P32 + (int64_t)pos * Dp;
-    for (int k = 0; k < d; ++k) p[k] = e[k] / nrm;
+    for (int k = 0; k < d; ++k) p[k] = flush_tiny(e[k] / nrm);
     for (int k = d; k < Dp; ++k) p[k] = 0.f;
     pix[pos] = (int32_t)i;
 }

@@ -20,6 +20,13 @@ inline int padded_dim(int d) { return d <= 16 ? 16 : 32; }
 // error of both operands, is within 2.3e-6 of the exact value.
 constexpr float kEpsF32 = 1e-5f;
 
+// Normalised pixel components below 2^-100 in magnitude are stored as 0. This
+// changes no dot product by more than 2^-95 and keeps every stored component
+// in the range where its three-term BF16 split (tensor-core form) rebuilds
+// the FP32 value exactly.
+constexpr float kTinyComponent = 7.8886090522101181e-31f;  // 2^-100
+__host__ __device__ inline float flush_tiny(float v) { return fabsf(v) < kTinyComponent ? 0.f : v; }
+
 constexpr int kShiftThreads = 128;
 constexpr int kSeedsPerThread = 2;
 constexpr int kSeedsPerTile = kShiftThreads * kSeedsPerThread;  // 256

@@ -9,23 +9,25 @@
 //          (measured <= 6e-6 against an exact reconstruction).
 //   mask   a pair is in the window when S' >= 0 (sign bit clear). Pairs with
 //          |S'| < kBand = 2^-14 are re-decided with the same sequential FP32
-//          dot product as the FP32 form, so every decision equals the FP32
-//          form's, whose dot product is within 1e-6 of x.p.
+//          dot product as the FP32 form, against the pixel's exact FP32 value
+//          rebuilt from its BF16 parts in the shared-memory tile, so every
+//          decision equals the FP32 form's, whose dot product is within 1e-6
+//          of x.p.
 //   GEMM2  Y += Mask . [Ph | Pm | Pl | 1]    (8 tcgen05 MMAs, mask exact in BF16;
 //          the ones column yields the window size)
-// The seed-by-pixel matrix lives only in TMEM, registers and a shared-memory
-// mask tile. After the item's last tile the Y sums are added to the per-seed
+// The seed-by-pixel matrix lives only in TMEM and registers. After the item's last tile the Y sums are added to the per-seed
 // fixed-point accumulators shared with the FP32 form, and the same finalize
 // kernel normalises the seeds and tests convergence in FP64.
 //
-// Warp roles (320 threads, one CTA per SM): warp 0 issues TMA loads of pixel
-// tiles into a 4-stage ring; warp 1 owns TMEM (512 columns: two S buffers and
-// Y) and issues MMAs, GEMM1 of tile g+1 before GEMM2 of tile g so the tensor
-// cores work while the mask of tile g is built; warps 2-9 build the mask, two
-// warps per 32-lane TMEM quadrant, 64 pixels each. Seed operands (A1) and
-// mask tiles are double-buffered. All waits are bounded; a timeout raises the
-// CTA's abort flag, drains what is in flight, frees TMEM and reports
-// MS_ERR_TIMEOUT through the frame's status word.
+// Warp roles (608 threads, one CTA per SM): warp 0 issues TMA loads of pixel
+// tiles into an 11-stage ring; warp 1 owns TMEM (512 columns: two S, two Y and
+// two mask buffers) and issues GEMM1, running ahead of the mask warps as far
+// as the S buffers allow; warp 2 issues GEMM2 as each mask tile lands; warps
+// 3-18 build the mask, four warps per 32-lane TMEM quadrant, 32 pixels each,
+// and store it to TMEM, where GEMM2 reads it as its A operand. Seed operands (A1), S, masks and Y
+// are double-buffered. All waits are bounded; a timeout
+// raises the CTA's abort flag, drains what is in flight, frees TMEM and
+// reports MS_ERR_TIMEOUT through the frame's status word.
 #include <cudaTypedefs.h>
 
 #include "ms_batch.cuh"
@@ -37,20 +39,24 @@ namespace {
 
 using namespace tc;
 
-constexpr int kTcThreads = 320;
-constexpr int kStages = 4;
+constexpr int kMaskWarps = 16;
+constexpr int kMaskWarp0 = 3;         // warps 0-2: TMA, GEMM1, GEMM2
+constexpr int kTcThreads = (kMaskWarp0 + kMaskWarps) * 32;  // 608
+constexpr int kStages = 11;            // pixel-tile ring
 constexpr int kTileBytes = 128 * 128;  // 128 rows x 128 bytes
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColY = 256;        // S buffers at columns 0 and 128
+constexpr uint32_t kColS = 0;          // two S accumulators, 128 columns each
+constexpr uint32_t kColY = 256;        // two Y accumulators, 64 columns each
+constexpr uint32_t kColM = 384;        // two mask tiles (GEMM2's A), 64 columns each
 constexpr float kBand = 6.103515625e-05f;    // 2^-14
 constexpr float kFixScale = 68719476736.0f;  // 2^36
 
 constexpr int kOffA1 = 0;                              // 2 x 16 KB
 constexpr int kOffP = 2 * kTileBytes;                  // kStages x 16 KB
-constexpr int kOffM = kOffP + kStages * kTileBytes;    // 2 x 32 KB
-constexpr int kOffBar = kOffM + 4 * kTileBytes;
-constexpr int kNumBars = 2 * kStages + 14;
+constexpr int kOffBar = kOffP + kStages * kTileBytes;
+constexpr int kNumBars = 2 * kStages + 7 * 2 + 2;
 constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 16 + 1024;  // + alignment slack
+static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
 struct TcSplit {
     int tiles, chunks, tpc;  // seed tiles, pixel chunks, pixel tiles per chunk
@@ -117,13 +123,6 @@ __device__ __forceinline__ void write_a1(uint8_t* A1, int r, const float (&x)[16
         *reinterpret_cast<uint4*>(A1 + sw128_offset(r, cidx)) = make_uint4(0u, 0u, 0u, 0u);
 }
 
-struct Gemm2Job {
-    int g;       // CTA-local tile counter
-    int stage;   // pixel-tile stage
-    int it;      // CTA-local item counter
-    bool first, last;
-};
-
 // What a work item covers, in the frame it belongs to.
 struct TcItem {
     const int32_t* active;  // seed slots of the frame's active list
@@ -165,6 +164,33 @@ struct TcSingleMap {
     }
 };
 
+// FP32 value of pixel row `row` of a pixel stage, rebuilt exactly from its
+// three BF16 parts (h + m) + l: the split of an FP32 value into three
+// round-to-nearest BF16 terms is exact, and so is this sum.
+__device__ __forceinline__ void stage_pixel(const uint8_t* stage, int row, float (&p)[16]) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const uint4 hv = *reinterpret_cast<const uint4*>(stage + sw128_offset(row, c));
+        const uint4 mv = *reinterpret_cast<const uint4*>(stage + sw128_offset(row, c + 2));
+        const uint4 lv = *reinterpret_cast<const uint4*>(stage + sw128_offset(row, c + 4));
+        const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, mw[4] = {mv.x, mv.y, mv.z, mv.w},
+                       lw[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            p[c * 8 + 2 * k] = __fadd_rn(__fadd_rn(__uint_as_float(hw[k] << 16), __uint_as_float(mw[k] << 16)),
+                                         __uint_as_float(lw[k] << 16));
+            p[c * 8 + 2 * k + 1] =
+                __fadd_rn(__fadd_rn(__uint_as_float(hw[k] & 0xFFFF0000u), __uint_as_float(mw[k] & 0xFFFF0000u)),
+                          __uint_as_float(lw[k] & 0xFFFF0000u));
+        }
+    }
+}
+
+// Warp-uniform bounded wait: every lane polls, all lanes get the same answer.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort));
+}
+
 template <bool kDebug, class Map>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P32, const float* __restrict__ X,
@@ -175,18 +201,17 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* A1 = smem + kOffA1;
     uint8_t* Pst = smem + kOffP;
-    uint8_t* Mt = smem + kOffM;
     uint64_t* bars = (uint64_t*)(smem + kOffBar);
-    uint64_t* full = bars;
-    uint64_t* empty = bars + kStages;
-    uint64_t* s_full = bars + 2 * kStages;       // [2]
-    uint64_t* s_empty = s_full + 2;              // [2]
-    uint64_t* m_full = s_empty + 2;              // [2]
-    uint64_t* m_empty = m_full + 2;              // [2]
-    uint64_t* a1_full = m_empty + 2;             // [2]
-    uint64_t* d_full = a1_full + 2;
-    uint64_t* d_empty = d_full + 1;
-    uint64_t* aux = d_empty + 1;
+    uint64_t* full = bars;                        // [kStages] pixel tile landed
+    uint64_t* empty = full + kStages;             // [kStages] pixel tile consumed by GEMM2
+    uint64_t* s_full = empty + kStages;           // [2] GEMM1 done
+    uint64_t* s_empty = s_full + 2;               // [2] S read by the mask warps
+    uint64_t* m_full = s_empty + 2;               // [2] mask tile stored to TMEM by every mask warp
+    uint64_t* m_empty = m_full + 2;               // [2] mask tile consumed by GEMM2
+    uint64_t* a1_full = m_empty + 2;              // [2] seed operand written
+    uint64_t* d_full = a1_full + 2;               // [2] Y of an item complete
+    uint64_t* d_empty = d_full + 2;               // [2] Y read by the epilogue
+    uint64_t* aux = d_empty + 2;                  // [2] drain barriers of the two MMA issuers
     uint32_t* tmem_slot = (uint32_t*)(bars + kNumBars);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
 
@@ -198,14 +223,15 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&s_full[b], 1);
-            mbar_init(&s_empty[b], 256);
-            mbar_init(&m_full[b], 256);
+            mbar_init(&s_empty[b], kMaskWarps);
+            mbar_init(&m_full[b], kMaskWarps);
             mbar_init(&m_empty[b], 1);
             mbar_init(&a1_full[b], 128);
+            mbar_init(&d_full[b], 1);
+            mbar_init(&d_empty[b], 128);
         }
-        mbar_init(d_full, 1);
-        mbar_init(d_empty, 128);
-        mbar_init(aux, 1);
+        mbar_init(&aux[0], 1);
+        mbar_init(&aux[1], 1);
         *abort = 0;
         fence_mbar_init();
     }
@@ -237,71 +263,87 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                 for (int q = max(0, g - kStages); q < g; ++q) drain_wait(&full[q % kStages], (q / kStages) & 1);
         }
     } else if (warp == 1) {
-        // ------------------------------------------------ MMA issuer
+        // ------------------------------------------------ GEMM1 issuer
+        // Runs ahead of the mask warps as far as the two S buffers allow.
         if (lane == 0) {
-            const uint32_t tY = tmem + kColY;
-            const uint32_t a1 = smem_u32(A1), mt = smem_u32(Mt), pst = smem_u32(Pst);
+            // Descriptors are built once; moving an operand by b bytes adds
+            // b >> 4 to the descriptor's start-address field (no carry: shared
+            // addresses stay below 2^18).
+            const uint64_t dA1 = desc_sw128(smem_u32(A1), 16, 1024);   // seed operand, K-major
+            const uint64_t dP1 = desc_sw128(smem_u32(Pst), 16, 1024);  // pixel tile, K-major
             constexpr uint32_t id1 = idesc_bf16(128, 128, 0, 0);
-            constexpr uint32_t id2 = idesc_bf16(128, 64, 0, 1);
+            constexpr uint64_t kT = kTileBytes >> 4;
             bool ok = true;
-            bool pending = false;
-            Gemm2Job job{0, 0, 0, false, false};
-            auto gemm2 = [&](const Gemm2Job& j) -> bool {
-                if (!mbar_wait(&m_full[j.g & 1], (j.g >> 1) & 1, abort)) return false;
-                if (j.first && j.it > 0 && !mbar_wait(d_empty, (j.it - 1) & 1, abort)) return false;
-                tc_fence_after();
-                const uint32_t mb = mt + (j.g & 1) * 2 * kTileBytes;
-                const uint32_t pb = pst + j.stage * kTileBytes;
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const uint64_t ad = desc_sw128(mb + (k >> 2) * kTileBytes + (k & 3) * 32, 16, 1024);
-                    const uint64_t bd = desc_sw128(pb + k * 2048, kTileBytes, 1024);
-                    mma_bf16(tY, ad, bd, id2, (j.first && k == 0) ? 0u : 1u);
-                }
-                mma_commit(&m_empty[j.g & 1]);
-                mma_commit(&empty[j.stage]);
-                if (j.last) mma_commit(d_full);
-                return true;
-            };
             int g = 0, it = 0;
             for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
                 const TcItem ii = map.item(item);
-                const int pt0 = ii.pt0, pt1 = ii.pt1;
                 if (!(ok = mbar_wait(&a1_full[it & 1], (it >> 1) & 1, abort))) break;
-                const uint32_t a = a1 + (it & 1) * kTileBytes;
-                for (int pt = pt0; pt < pt1; ++pt, ++g) {
-                    const int s = g % kStages;
+                const uint64_t a = dA1 + (uint64_t)(it & 1) * kT;
+                for (int pt = ii.pt0; pt < ii.pt1; ++pt, ++g) {
+                    const int s = g % kStages, b = g & 1;
                     if (!(ok = mbar_wait(&full[s], (g / kStages) & 1, abort))) break;
-                    if (g >= 2 && !(ok = mbar_wait(&s_empty[g & 1], ((g >> 1) - 1) & 1, abort))) break;
+                    if (g >= 2 && !(ok = mbar_wait(&s_empty[b], ((g >> 1) - 1) & 1, abort))) break;
                     tc_fence_after();
-                    const uint32_t tS = tmem + (g & 1) * 128;
-                    const uint32_t pb = pst + s * kTileBytes;
-                    mma_bf16(tS, desc_sw128(a, 16, 1024), desc_sw128(pb, 16, 1024), id1, 0);
-                    mma_bf16(tS, desc_sw128(a, 16, 1024), desc_sw128(pb + 32, 16, 1024), id1, 1);
-                    mma_bf16(tS, desc_sw128(a + 32, 16, 1024), desc_sw128(pb, 16, 1024), id1, 1);
-                    mma_bf16(tS, desc_sw128(a + 64, 16, 1024), desc_sw128(pb + 96, 16, 1024), id1, 1);
-                    mma_commit(&s_full[g & 1]);
-                    if (pending && !(ok = gemm2(job))) break;
-                    job = Gemm2Job{g, s, it, pt == pt0, pt == pt1 - 1};
-                    pending = true;
+                    const uint32_t tS = tmem + kColS + b * 128;
+                    const uint64_t pb = dP1 + (uint64_t)s * kT;
+                    mma_bf16(tS, a, pb, id1, 0);            // Xh . Ph
+                    mma_bf16(tS, a, pb + 2, id1, 1);        // Xh . Pm
+                    mma_bf16(tS, a + 2, pb, id1, 1);        // Xl . Ph
+                    mma_bf16(tS, a + 4, pb + 6, id1, 1);    // -c split . ones
+                    mma_commit(&s_full[b]);
                 }
             }
-            if (ok && pending) ok = gemm2(job);
             if (*abort) {
-                mma_commit(aux);
-                drain_wait(aux, 0);
+                mma_commit(&aux[0]);
+                drain_wait(&aux[0], 0);
+            }
+        }
+    } else if (warp == 2) {
+        // ------------------------------------------------ GEMM2 issuer
+        // Y += Mask . P as soon as a mask tile is in TMEM; the pixel stage is
+        // released when these MMAs complete.
+        if (lane == 0) {
+            const uint64_t dP2 = desc_sw128(smem_u32(Pst), kTileBytes, 1024);  // pixel tile, MN-major
+            constexpr uint32_t id2 = idesc_bf16(128, 64, 0, 1);
+            constexpr uint64_t kT = kTileBytes >> 4;
+            bool ok = true;
+            int g = 0, it = 0;
+            for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
+                const TcItem ii = map.item(item);
+                for (int pt = ii.pt0; pt < ii.pt1; ++pt, ++g) {
+                    const int s = g % kStages, b = g & 1;
+                    const bool first = pt == ii.pt0;
+                    if (!(ok = mbar_wait(&m_full[b], (g >> 1) & 1, abort))) break;
+                    if (!(ok = mbar_wait(&full[s], (g / kStages) & 1, abort))) break;
+                    if (first && it >= 2 && !(ok = mbar_wait(&d_empty[it & 1], ((it >> 1) - 1) & 1, abort))) break;
+                    tc_fence_after();
+                    const uint32_t tY = tmem + kColY + (it & 1) * 64;
+                    const uint32_t tM = tmem + kColM + b * 64;
+                    const uint64_t pb = dP2 + (uint64_t)s * kT;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        mma_bf16_ts(tY, tM + 8 * k, pb + k * 128, id2, (first && k == 0) ? 0u : 1u);
+                    mma_commit(&m_empty[b]);
+                    mma_commit(&empty[s]);
+                    if (pt == ii.pt1 - 1) mma_commit(&d_full[it & 1]);
+                }
+            }
+            if (*abort) {
+                mma_commit(&aux[1]);
+                drain_wait(&aux[1], 0);
             }
         }
     } else {
-        // ------------------------------------------------ mask warps (2..9)
-        const int q = warp & 3;             // TMEM lane quadrant
-        const int h = (warp - 2) >> 2;      // which 64 pixels of a tile
-        const int r = q * 32 + lane;        // seed row
+        // ------------------------------------------------ mask warps (3..18)
+        const int q = warp & 3;                   // TMEM lane quadrant (a warp reaches lanes 32 * (warp % 4) + 0..31)
+        const int h = (warp - kMaskWarp0) >> 2;   // which 32 pixels of a tile
+        const int r = q * 32 + lane;              // seed row
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         long long band_local = 0;
         int g = 0, it = 0;
         float x[16];
-        for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x, ++it) {
+        for (int item = blockIdx.x; item < items; item += gridDim.x, ++it) {
+            if (__any_sync(0xffffffffu, *abort)) break;
             const TcItem ii = map.item(item);
             const int pt0 = ii.pt0, pt1 = ii.pt1;
             const int pos = ii.seed0 + r;
@@ -309,8 +351,9 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
             load_x16(X, slot, x);
             if (h == 0) {
                 // A1 for this item (first item only) and the next one; the next
-                // one's buffer was last read by item it-1, whose MMAs completed
-                // before d_full(it-1) was observed.
+                // one's buffer was last read by the GEMM1s of item it-1, which
+                // completed before this warp observed s_full of that item's
+                // last tile (a commit covers every earlier MMA of its thread).
                 if (it == 0) {
                     write_a1(A1, r, x, c_f);
                     fence_proxy_async();
@@ -327,56 +370,51 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                     mbar_arrive(&a1_full[(it + 1) & 1]);
                 }
             }
+            bool ok = true;
             for (int pt = pt0; pt < pt1; ++pt, ++g) {
                 const int b = g & 1;
-                if (!mbar_wait(&s_full[b], (g >> 1) & 1, abort)) break;
+                if (!(ok = warp_wait(&s_full[b], (g >> 1) & 1, abort))) break;
                 tc_fence_after();
-                uint32_t v[64];
-                {
-                    uint32_t (&v0)[32] = *reinterpret_cast<uint32_t(*)[32]>(&v[0]);
-                    uint32_t (&v1)[32] = *reinterpret_cast<uint32_t(*)[32]>(&v[32]);
-                    const uint32_t ta = tmem + b * 128 + lane_base + h * 64;
-                    tmem_ld32(ta, v0);
-                    tmem_ld32(ta + 32, v1);
-                    tmem_ld_wait();
-                }
+                uint32_t v[32];
+                tmem_ld32(tmem + kColS + b * 128 + lane_base + h * 32, v);
+                tmem_ld_wait();
                 tc_fence_before();
-                mbar_arrive(&s_empty[b]);
-                uint32_t w[32];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&s_empty[b]);
+                uint32_t w[16];
                 float mn = INFINITY;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
+                for (int i = 0; i < 16; ++i) {
                     w[i] = ~sign_halves(v[2 * i], v[2 * i + 1]) & 0x3F803F80u;
                     mn = fminf(mn, fminf(fabsf(__uint_as_float(v[2 * i])), fabsf(__uint_as_float(v[2 * i + 1]))));
                 }
-                if (mn < kBand) {
+                if (__any_sync(0xffffffffu, mn < kBand)) {
                     // Re-decide near-boundary pairs with the FP32 form's dot
-                    // product. Bit masks keep every register-array index static.
-                    uint64_t bandm = 0;
+                    // product against the exact FP32 pixel rebuilt from the
+                    // tile in shared memory. Bit masks keep register-array
+                    // indices static.
+                    const int s = g % kStages;
+                    if (!(ok = warp_wait(&full[s], (g / kStages) & 1, abort))) break;
+                    const uint8_t* stage = Pst + s * kTileBytes;
+                    uint32_t bandm = 0;
 #pragma unroll
-                    for (int i = 0; i < 64; ++i)
-                        bandm |= (uint64_t)(fabsf(__uint_as_float(v[i])) < kBand) << i;
-                    uint64_t inm = 0, todo = bandm;
+                    for (int i = 0; i < 32; ++i) bandm |= (uint32_t)(fabsf(__uint_as_float(v[i])) < kBand) << i;
+                    uint32_t inm = 0, todo = bandm;
                     while (todo) {
-                        const int i = __ffsll((long long)todo) - 1;
+                        const int i = __ffs(todo) - 1;
                         todo &= todo - 1;
-                        const int px_local = pt * 128 + h * 64 + i;
-                        const int64_t px = ii.pix0 + px_local;
-                        if (px_local < ii.n) {
+                        const int row = h * 32 + i;
+                        if (pt * 128 + row < ii.n) {
                             ++band_local;
                             float pv[16];
-#pragma unroll
-                            for (int k = 0; k < 16; k += 4) {
-                                const float4 u = *reinterpret_cast<const float4*>(P32 + (int64_t)px * 16 + k);
-                                pv[k] = u.x; pv[k + 1] = u.y; pv[k + 2] = u.z; pv[k + 3] = u.w;
-                            }
-                            if (dot_seq<16>(x, pv) >= c_f) inm |= 1ull << i;
+                            stage_pixel(stage, row, pv);
+                            if (dot_seq<16>(x, pv) >= c_f) inm |= 1u << i;
                         }
                     }
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const uint32_t bm = (uint32_t)(bandm >> (2 * j)) & 3u;
-                        const uint32_t im = (uint32_t)(inm >> (2 * j)) & 3u;
+                    for (int j = 0; j < 16; ++j) {
+                        const uint32_t bm = (bandm >> (2 * j)) & 3u;
+                        const uint32_t im = (inm >> (2 * j)) & 3u;
                         const uint32_t clear = ((bm & 1u) ? 0x3F80u : 0u) | ((bm & 2u) ? 0x3F800000u : 0u);
                         const uint32_t set = ((im & 1u) ? 0x3F80u : 0u) | ((im & 2u) ? 0x3F800000u : 0u);
                         w[j] = (w[j] & ~clear) | set;
@@ -384,31 +422,30 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                 }
                 if (kDebug) {
 #pragma unroll
-                    for (int i = 0; i < 64; ++i)
-                        dbg_S[(int64_t)r * dbg_stride + pt * 128 + h * 64 + i] = __uint_as_float(v[i]);
+                    for (int i = 0; i < 32; ++i)
+                        dbg_S[(int64_t)r * dbg_stride + pt * 128 + h * 32 + i] = __uint_as_float(v[i]);
                 }
-                if (g >= 2 && !mbar_wait(&m_empty[b], ((g >> 1) - 1) & 1, abort)) break;
-                uint8_t* mrow = Mt + b * 2 * kTileBytes + h * kTileBytes;
-#pragma unroll
-                for (int cidx = 0; cidx < 8; ++cidx)
-                    *reinterpret_cast<uint4*>(mrow + sw128_offset(r, cidx)) =
-                        make_uint4(w[4 * cidx], w[4 * cidx + 1], w[4 * cidx + 2], w[4 * cidx + 3]);
-                fence_proxy_async();
-                mbar_arrive(&m_full[b]);
+                if (g >= 2 && !(ok = warp_wait(&m_empty[b], ((g >> 1) - 1) & 1, abort))) break;
+                tc_fence_after();
+                tmem_st16(tmem + kColM + b * 64 + lane_base + h * 16, w);
+                tmem_st_wait();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&m_full[b]);
             }
-            if (*abort) break;
+            if (!ok) break;
             if (h == 0) {
-                if (!mbar_wait(d_full, it & 1, abort)) break;
+                if (!warp_wait(&d_full[it & 1], (it >> 1) & 1, abort)) break;
                 tc_fence_after();
                 uint32_t yh[16], ym[16], yl[16], yc[16];
-                const uint32_t ty = tmem + kColY + lane_base;
+                const uint32_t ty = tmem + kColY + (it & 1) * 64 + lane_base;
                 tmem_ld16(ty, yh);
                 tmem_ld16(ty + 16, ym);
                 tmem_ld16(ty + 32, yl);
                 tmem_ld16(ty + 48, yc);
                 tmem_ld_wait();
                 tc_fence_before();
-                mbar_arrive(d_empty);
+                mbar_arrive(&d_empty[it & 1]);
                 const float cntf = __uint_as_float(yc[0]);
                 if (slot >= 0 && cntf > 0.f) {
                     unsigned long long* a = acc + (int64_t)slot * 17;

@@ -62,7 +62,7 @@ __global__ void k_static_prepare(const float* __restrict__ P, int n, int m, unsi
         for (int k = 0; k < kStaticDim; ++k) s = fmaf(e[k], e[k], s);
         const float nrm = sqrtf(s);
         float* p = P32 + (int64_t)i * kStaticDim;
-        for (int k = 0; k < kStaticDim; ++k) p[k] = e[k] / nrm;
+        for (int k = 0; k < kStaticDim; ++k) p[k] = flush_tiny(e[k] / nrm);
         if (!(nrm > 0.f) || !isfinite(nrm)) atomicOr(&dc->status, 1);
     }
     if (i < m) {

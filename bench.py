@@ -61,6 +61,12 @@ def parse():
                     help="oracle baseline: one full frame (also gives the label match), a seed sample, or none")
     ap.add_argument("--cpu-seeds", type=int, default=8192, help="seeds in the oracle's sampled run")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched forms: skip the work-split autotuner (keep the canonical split)")
+    ap.add_argument("--eager", action="store_true",
+                    help="batched forms: issue the graph's kernels as plain launches (for profilers)")
+    ap.add_argument("--shift-only", type=int, default=0, metavar="SEEDS",
+                    help="time one shift iteration of SEEDS seeds on frame 0 (fp32 or bf16 form) and exit")
     return ap.parse_args()
 
 
@@ -160,8 +166,9 @@ def load_peaks():
 
 
 def shift_traffic_per_unit(kernel):
-    """DRAM bytes per seed-iteration of the shift kernel from the committed ncu
-    summary, valid only while the kernel source is unchanged."""
+    """DRAM bytes per frame-iteration (one launch's pass over one frame) of the
+    shift kernel from the committed ncu summary, valid only while the kernel
+    source is unchanged."""
     src = SHIFT_TC_SRC if kernel == "k_shift_tc" else SHIFT_SRC
     try:
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -278,7 +285,7 @@ def run_reference(args, rank):
 class Runner:
     """One form of the method over a fixed list of device-resident frames."""
 
-    def __init__(self, ms, form, frames, dev):
+    def __init__(self, ms, form, frames, dev, eager=False, autotune=False):
         import torch
         self.ms, self.form, self.frames = ms, form, frames
         self.batched = form.endswith("batched")
@@ -286,9 +293,17 @@ class Runner:
         self.cfg = ms.ms_config_default(dim=DIM, precision=prec)
         self.embs = [torch.from_numpy(f.emb).to(dev) for f in frames]
         self.masks = [torch.from_numpy(f.mask).to(dev) for f in frames]
+        self.eager_passes = 0
+        self.tuning = None
         if self.batched:
             self.batch = ms.ms_batch_create(self.cfg, self.embs, self.masks)
-            ms.ms_batch_profile(self.batch, True)
+            if autotune:
+                self.tuning = ms.ms_batch_autotune(self.batch, reps=2)
+            if eager:
+                ms.ms_batch_run(self.batch)
+                self.eager_passes = ms.ms_batch_stats(self.batch, -1)["reserved0"]
+            else:
+                ms.ms_batch_profile(self.batch, True)
             self.labels = self.batch.labels
         else:
             self.labels = [torch.empty(f.emb.shape[0], dtype=torch.int32, device=dev) for f in frames]
@@ -297,13 +312,17 @@ class Runner:
         """Cluster every frame once; returns counters of this step."""
         ms = self.ms
         if self.batched:
-            ms.ms_batch_run(self.batch)
+            if self.eager_passes:
+                ms.ms_batch_run_eager(self.batch, self.eager_passes)
+            else:
+                ms.ms_batch_run(self.batch)
             st = ms.ms_batch_stats(self.batch, -1)
             return {"frames": len(self.frames), "launches": st["launches"], "shift_ms": st["shift_ms"],
                     "shift_launches": st["shift_launches"], "seed_iters": st["seed_iters"],
-                    "modes": st["n_modes"], "passes": st["reserved0"], "band_pairs": st["band_pairs"]}
+                    "modes": st["n_modes"], "passes": st["reserved0"], "band_pairs": st["band_pairs"],
+                    "frame_iters": st["iters_total"]}
         agg = {"frames": 0, "launches": 0, "shift_ms": 0.0, "shift_launches": 0, "seed_iters": 0, "modes": 0,
-               "passes": 0, "band_pairs": 0}
+               "passes": 0, "band_pairs": 0, "frame_iters": 0}
         for f, (e, m, l) in enumerate(zip(self.embs, self.masks, self.labels)):
             self.cfg.frame_id = f  # the batch gives frame f the seed order of frame_id f
             ctx = ms.ms_create(self.cfg, e, m)
@@ -314,6 +333,7 @@ class Runner:
             agg["frames"] += 1
             for k in ("launches", "shift_ms", "shift_launches", "seed_iters", "band_pairs"):
                 agg[k] += st[k]
+            agg["frame_iters"] += st["iters_total"]
             agg["modes"] += st["n_modes"]
         return agg
 
@@ -369,9 +389,12 @@ def roofline_of(form, tot, step_ms, clk, n_sm):
                        "(median SM clock sampled under load)")
     tpu = shift_traffic_per_unit(kernel)
     per_launch_si = tot["seed_iters"] / max(1, tot["shift_launches"])
+    per_launch_fi = tot.get("frame_iters", 0) / max(1, tot["shift_launches"])
     return {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None,
-            "traffic": (tpu * per_launch_si) if tpu else None,
+            "traffic": (tpu * per_launch_fi) if (tpu and per_launch_fi) else None,
+            "traffic_basis": "ncu dram bytes of one frame-iteration (profiles/ncu_traffic.txt) x "
+                             f"{per_launch_fi:.2f} frame-iterations per launch",
             "peak_source": peak_source,
             "algorithmic": f"4*d*n flops per seed-iteration (d={DIM}, n={N_FG}); "
                            f"{per_launch_si:.0f} seed-iterations per launch on average",
@@ -426,7 +449,8 @@ def run_ours(args, rank, ws, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    main = Runner(ms, args.form, frames, dev)
+    main = Runner(ms, args.form, frames, dev, eager=args.eager,
+                  autotune=args.form.endswith("batched") and not args.no_autotune)
     clocks = Clocks(local)
     clocks.start()
     step_ms, tot = timed(main, args.steps, args.warmup, ws, flush, stream)
@@ -487,12 +511,14 @@ def run_ours(args, rank, ws, local):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "bf16+f32" if args.form.startswith("bf16") else "f32",
                 "data": "synthetic vMF frames shaped like 512x512 microscopy (seeded generator)",
-                "config": {"workload": WORKLOAD, "form": args.form, "frames_per_step": args.frames,
+                "config": {"workload": WORKLOAD, "form": args.form + (" (eager launches)" if args.eager else ""),
+                           "frames_per_step": args.frames,
                            "l2": "flushed (256 MB write) before every step; inputs also exceed L2",
                            "parallelism": f"replicas x{ws}",
                            "seed_iters_per_frame": tot["seed_iters"] / max(1, tot["frames"]),
                            "modes_per_frame": tot["modes"] / max(1, tot["frames"]),
                            "graph_passes_per_step": tot.get("passes", 0) / max(1, args.steps),
+                           "autotune": main.tuning,
                            "fp32_rechecked_pair_fraction": tot.get("band_pairs", 0) /
                            max(1.0, float(tot["seed_iters"]) * N_FG)},
                 "roofline": roofline, "forms": forms, "parity_vs_oracle": parity, "cpu_baseline": cpu,
@@ -500,8 +526,45 @@ def run_ours(args, rank, ws, local):
         print(json.dumps(line), flush=True)
 
 
+def run_shift_only(args):
+    """One shift launch (Algorithm 2, lines 4-9, one iteration) of a fixed seed
+    batch through the public API: the dominant kernel alone, with a known
+    number of seed-iterations per launch."""
+    import torch
+
+    import paper_2007_14283_gb300 as ms
+    ms.load()
+    torch.cuda.set_device(0)
+    f = c2_frames(0, 1)[0]
+    e = torch.from_numpy(f.emb).cuda()
+    m = torch.from_numpy(f.mask).cuda()
+    prec = ms.MS_BF16 if args.form.startswith("bf16") else ms.MS_FP32
+    cfg = ms.ms_config_default(dim=DIM, precision=prec)
+    times = []
+    for rep in range(args.warmup + args.steps):
+        ctx = ms.ms_create(cfg, e, m)
+        ms.ms_profile(ctx, True)
+        seeded = ms.ms_seed_batch(ctx, args.shift_only)
+        try:
+            ms.ms_iterate(ctx, 1)
+        except ms.MsError as err:  # one iteration rarely converges a seed
+            if err.status != ms.MS_ERR_NOT_CONVERGED:
+                raise
+        st = ms.ms_stats_get(ctx)
+        ctx.close()
+        if rep >= args.warmup:
+            times.append(st["shift_ms"])
+    t = statistics.median(times)
+    flops = 4.0 * DIM * N_FG * seeded
+    print(json.dumps({"shift_only": True, "form": args.form, "seeds": seeded, "n": N_FG,
+                      "median_ms": t, "algorithmic_tflops": flops / (t * 1e-3) / 1e12}), flush=True)
+
+
 def main():
     args = parse()
+    if args.shift_only > 0:
+        run_shift_only(args)
+        return
     if args.impl == "reference":
         run_reference(args, int(os.environ.get("RANK", "0")))
         return

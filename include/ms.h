@@ -312,10 +312,39 @@ MS_API ms_status ms_batch_run(ms_batch* b, int32_t sync);
 MS_API ms_status ms_batch_run_host(ms_batch* b, const float* const* h_embs, const uint8_t* const* h_masks,
                                    int32_t* const* h_labels);
 MS_API ms_status ms_batch_stats(const ms_batch* b, int32_t frame, ms_stats* out);
+/* The same work as one ms_batch_run, issued as ordinary kernel launches on
+ * the batch's stream instead of the graph: set-up, `passes` passes of the
+ * loop body and labelling (for profilers that do not look inside conditional
+ * graph nodes). Passes after every frame has finished change nothing, so
+ * results equal ms_batch_run's when passes >= the loop's pass count
+ * (ms_batch_stats(-1).reserved0 after a graph run). Synchronises;
+ * MS_ERR_STATE if a frame is still unfinished after `passes`. */
+MS_API ms_status ms_batch_run_eager(ms_batch* b, int32_t passes);
 MS_API ms_status ms_batch_profile(ms_batch* b, int32_t enable);
 MS_API ms_status ms_batch_modes(const ms_batch* b, int32_t frame, float* h_out, int32_t cap,
                                 int32_t* n_modes_out);
 MS_API void ms_batch_destroy(ms_batch* b);
+
+/* Work split of a batch's shift launches (the autotuned parameters):
+ * batch_split 0 gives every frame the single-frame split (results equal
+ * ms_run's frame by frame; target_mult is then unused); batch_split 1 shares
+ * target_mult x (shift grid) work items across the iterating frames in
+ * proportion to their seed x pixel work (target_mult 1..64). The tile shape
+ * itself (128 seeds x 128 pixels, 11 pipeline stages) is fixed by the kernel.
+ * ms_batch_configure rebuilds the graph (synchronises the stream).
+ * ms_batch_autotune times ms_batch_run on the batch's own frames for each
+ * candidate -- (0, 2), (1, 1), (1, 2), (1, 4), (1, 8) -- as the median of
+ * `reps` graph launches (CUDA events on the batch's stream, after one
+ * warm-up launch), keeps the fastest, runs it once more so the batch's
+ * outputs come from it, and writes min(cap, 5) results to `results` (host). */
+typedef struct ms_tune_result {
+    int32_t batch_split;
+    int32_t target_mult;
+    double ms;
+} ms_tune_result;
+MS_API ms_status ms_batch_configure(ms_batch* b, int32_t batch_split, int32_t target_mult);
+MS_API ms_status ms_batch_autotune(ms_batch* b, int32_t reps, ms_tune_result* results, int32_t cap,
+                                   int32_t* n_results);
 
 #ifdef __cplusplus
 }

@@ -55,6 +55,10 @@ class ms_stats(ctypes.Structure):
     ]
 
 
+class ms_tune_result(ctypes.Structure):
+    _fields_ = [("batch_split", ctypes.c_int32), ("target_mult", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i32, _i64 = ctypes.c_int32, ctypes.c_int64
@@ -88,6 +92,9 @@ _SIGNATURES = {
     "ms_batch_run_host": (_i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "ms_batch_stats": (_i32, [_vp, _i32, ctypes.POINTER(ms_stats)]),
     "ms_batch_profile": (_i32, [_vp, _i32]),
+    "ms_batch_run_eager": (_i32, [_vp, _i32]),
+    "ms_batch_configure": (_i32, [_vp, _i32, _i32]),
+    "ms_batch_autotune": (_i32, [_vp, _i32, ctypes.POINTER(ms_tune_result), _i32, _pi32]),
     "ms_batch_modes": (_i32, [_vp, _i32, _vp, _i32, _pi32]),
     "ms_batch_destroy": (None, [_vp]),
 }
@@ -388,6 +395,23 @@ def ms_batch_stats(b: Batch, frame: int = -1) -> dict:
     st = ms_stats()
     _check(load().ms_batch_stats(b.handle, frame, ctypes.byref(st)))
     return {k: getattr(st, k) for k, _ in ms_stats._fields_}
+
+
+def ms_batch_run_eager(b: Batch, passes: int):
+    _check(load().ms_batch_run_eager(b.handle, passes))
+
+
+def ms_batch_configure(b: Batch, batch_split: int, target_mult: int = 2):
+    _check(load().ms_batch_configure(b.handle, batch_split, target_mult))
+
+
+def ms_batch_autotune(b: Batch, reps: int = 3) -> list:
+    """Time every work-split candidate on the batch's frames and keep the
+    fastest; returns [{batch_split, target_mult, ms}] in candidate order."""
+    res = (ms_tune_result * 8)()
+    n = ctypes.c_int32()
+    _check(load().ms_batch_autotune(b.handle, reps, res, 8, ctypes.byref(n)))
+    return [{"batch_split": r.batch_split, "target_mult": r.target_mult, "ms": r.ms} for r in res[:n.value]]
 
 
 def ms_batch_profile(b: Batch, enable: bool = True):

@@ -16,6 +16,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -37,7 +38,8 @@ struct ms_batch {
     ms::BState* states;
     ms::BState* h_states;     // pinned copy for statistics
     ms::BPlan plan;
-    int32_t* blk_off;         // [B + 1] block work list of the current merge/cover/label kernel
+    int32_t* blk_off;         // [B + 2] block work list of the current merge/cover/label kernel
+    int32_t* blk_split;       // [B + 2] block work list with the inner loop split (slices at [B + 1])
     int32_t* misc;            // [0] passes, [1] status, u64 at [2] band pairs, [4] tick, [6] shift ns, [8] shift launches
     float* P32;
     int32_t* pix;
@@ -63,6 +65,8 @@ struct ms_batch {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     int64_t body_launches;    // kernels per pass of the loop body
+    int split;                // 0: each frame split as on its own; 1: work items shared by load
+    int target_mult;          // shift work items per launch = target_mult x shift grid
     int64_t fixed_launches;   // set-up and labelling kernels
     bool prof;                // body brackets the shift launch with timer ticks
     int32_t h_misc[16];       // host copy of misc after the last synchronised run
@@ -558,21 +562,60 @@ __global__ void k_b_check(BState* states, int B, double gamma, int max_iter) {
 }
 
 // ------------------------------------------------------------ merge
-// Block work list: frame f contributes ceil(count_f / per_block) blocks.
+// Block work list: frame f contributes ceil(count_f / per_block) blocks, times
+// S slices of an inner loop when split_target > 0 (S chosen so the list holds
+// about split_target blocks, 1..64; stored at off[B + 1]).
 __global__ void k_b_blocks(const BFrame* __restrict__ frames, const BState* __restrict__ states, int B, int sel,
-                           int per_block, int32_t* __restrict__ off) {
+                           int per_block, int split_target, int32_t* __restrict__ off) {
     if (threadIdx.x != 0) return;
-    int acc_blocks = 0;
+    int outer = 0;
     for (int f = 0; f < B; ++f) {
-        off[f] = acc_blocks;
         const BState& st = states[f];
         int cnt = 0;
         if (sel == kSelAllPixels) cnt = frames[f].n;
         else if (st.phase == kRoundDone) cnt = sel == kSelDoneSeeds ? st.dc.m_round
                                              : sel == kSelDoneCands ? st.dc.n_cand : frames[f].n;
-        acc_blocks += (cnt + per_block - 1) / per_block;
+        off[f] = outer;
+        outer += (cnt + per_block - 1) / per_block;
     }
-    off[B] = acc_blocks;
+    int S = 1;
+    if (split_target > 0 && outer > 0) {
+        S = (split_target + outer - 1) / outer;
+        S = S < 1 ? 1 : (S > 64 ? 64 : S);
+    }
+    for (int f = 0; f < B; ++f) off[f] *= S;
+    off[B] = outer * S;
+    off[B + 1] = S;
+}
+
+// Merge scratch of the frames whose round ended starts from zero ranks,
+// undecided candidates and empty conflict lists.
+__global__ void k_b_merge_zero(const BFrame* __restrict__ frames, const BState* __restrict__ states, int B,
+                               const int32_t* __restrict__ off, int32_t* __restrict__ cand_rank,
+                               uint8_t* __restrict__ cand_state, int32_t* __restrict__ conf_deg) {
+    for (int bb = blockIdx.x; bb < off[B]; bb += gridDim.x) {
+        const int f = locate(off, B, bb);
+        const int a = (bb - off[f]) * kMT + threadIdx.x;
+        if (a < states[f].dc.n_cand) {
+            const int64_t i = frames[f].pix0 + a;
+            cand_rank[i] = 0;
+            cand_state[i] = kUndecided;
+            conf_deg[i] = 0;
+        }
+    }
+}
+
+__global__ void k_b_rank_invert(const BFrame* __restrict__ frames, const BState* __restrict__ states, int B,
+                                const int32_t* __restrict__ off, const int32_t* __restrict__ cand_rank,
+                                int32_t* __restrict__ rank_cand) {
+    for (int bb = blockIdx.x; bb < off[B]; bb += gridDim.x) {
+        const int f = locate(off, B, bb);
+        const int a = (bb - off[f]) * kMT + threadIdx.x;
+        if (a < states[f].dc.n_cand) {
+            const int64_t base = frames[f].pix0;
+            rank_cand[base + cand_rank[base + a]] = a;
+        }
+    }
 }
 
 __global__ void k_b_collect(const BFrame* __restrict__ frames, BState* states, int B, const int32_t* __restrict__ off,
@@ -593,38 +636,39 @@ __global__ void k_b_collect(const BFrame* __restrict__ frames, BState* states, i
     }
 }
 
+// Rank in (support desc, seed order asc): block (candidate block, slice) adds
+// its partial count of candidates ahead (ranks start at 0, k_b_merge_zero).
 __global__ void k_b_rank(const BFrame* __restrict__ frames, const BState* __restrict__ states, int B,
                          const int32_t* __restrict__ off, const int32_t* __restrict__ cand,
                          const int32_t* __restrict__ support, const int32_t* __restrict__ order,
-                         int32_t* __restrict__ cand_rank, int32_t* __restrict__ rank_cand) {
+                         int32_t* __restrict__ cand_rank) {
     __shared__ int32_t s_sup[kMT], s_ord[kMT];
+    const int S = off[B + 1];
     for (int bb = blockIdx.x; bb < off[B]; bb += gridDim.x) {
         const int f = locate(off, B, bb);
-        const int lb = bb - off[f];
+        const int lb = bb - off[f], sl = lb % S;
         const int64_t base = frames[f].pix0;
         const int k = states[f].dc.n_cand;
-        const int a = lb * kMT + threadIdx.x;
+        const int a = (lb / S) * kMT + threadIdx.x;
+        const int lo = (int)((int64_t)sl * k / S), hi = (int)((int64_t)(sl + 1) * k / S);
         int sa = 0, oa = 0;
         if (a < k) {
             sa = support[cand[base + a]];
             oa = order[cand[base + a]];
         }
         int r = 0;
-        for (int t0 = 0; t0 < k; t0 += kMT) {
+        for (int t0 = lo; t0 < hi; t0 += kMT) {
             const int j = t0 + threadIdx.x;
             __syncthreads();
-            if (j < k) {
+            if (j < hi) {
                 s_sup[threadIdx.x] = support[cand[base + j]];
                 s_ord[threadIdx.x] = order[cand[base + j]];
             }
             __syncthreads();
-            const int lim = min(kMT, k - t0);
+            const int lim = min(kMT, hi - t0);
             for (int q = 0; q < lim; ++q) r += (s_sup[q] > sa) || (s_sup[q] == sa && s_ord[q] < oa);
         }
-        if (a < k) {
-            cand_rank[base + a] = r;
-            rank_cand[base + r] = a;
-        }
+        if (a < k && r) atomicAdd(&cand_rank[base + a], r);
         __syncthreads();
     }
 }
@@ -635,18 +679,20 @@ k_b_merge_old(const BFrame* __restrict__ frames, const BState* __restrict__ stat
               const int32_t* __restrict__ off, const float* __restrict__ X, const int32_t* __restrict__ cand,
               const float* __restrict__ modes, float thr_f, double thr, uint8_t* __restrict__ cand_state) {
     __shared__ __align__(16) float tile[kVT * Dp];
+    const int S = off[B + 1];
     for (int bb = blockIdx.x; bb < off[B]; bb += gridDim.x) {
         const int f = locate(off, B, bb);
-        const int lb = bb - off[f];
+        const int lb = bb - off[f], sl = lb % S;
         const int64_t base = frames[f].pix0;
         const int k = states[f].dc.n_cand;
         const int K_old = states[f].dc.n_kept;
-        const int a = lb * kMT + threadIdx.x;
+        const int a = (lb / S) * kMT + threadIdx.x;
+        const int lo = (int)((int64_t)sl * K_old / S), hi = (int)((int64_t)(sl + 1) * K_old / S);
         float x[Dp];
         if (a < k) ldv<Dp>(x, X + (int64_t)cand[base + a] * Dp);
         bool removed = false;
-        for (int t0 = 0; t0 < K_old; t0 += kVT) {
-            const int cnt = min(kVT, K_old - t0);
+        for (int t0 = lo; t0 < hi; t0 += kVT) {
+            const int cnt = min(kVT, hi - t0);
             __syncthreads();
             for (int q = threadIdx.x; q < cnt * Dp; q += kMT) tile[q] = modes[(base + t0) * Dp + q];
             __syncthreads();
@@ -657,7 +703,7 @@ k_b_merge_old(const BFrame* __restrict__ frames, const BState* __restrict__ stat
                         break;
                     }
         }
-        if (a < k) cand_state[base + a] = removed ? kRemoved : kUndecided;
+        if (a < k && removed) cand_state[base + a] = kRemoved;
         __syncthreads();
     }
 }
@@ -671,19 +717,20 @@ k_b_merge_pairs(const BFrame* __restrict__ frames, const BState* __restrict__ st
     __shared__ __align__(16) float tile[kVT * Dp];
     __shared__ int32_t s_rank[kVT];
     __shared__ uint8_t s_state[kVT];
+    const int S = off[B + 1];
     for (int bb = blockIdx.x; bb < off[B]; bb += gridDim.x) {
         const int f = locate(off, B, bb);
-        const int lb = bb - off[f];
+        const int lb = bb - off[f], sl = lb % S;
         const int64_t base = frames[f].pix0;
         const int k = states[f].dc.n_cand;
-        const int a = lb * kMT + threadIdx.x;
+        const int a = (lb / S) * kMT + threadIdx.x;
+        const int lo = (int)((int64_t)sl * k / S), hi = (int)((int64_t)(sl + 1) * k / S);
         const bool act = a < k && cand_state[base + a] == kUndecided;
         const int ra = a < k ? cand_rank[base + a] : 0;
         float x[Dp];
         if (act) ldv<Dp>(x, X + (int64_t)cand[base + a] * Dp);
-        int deg = 0;
-        for (int t0 = 0; t0 < k; t0 += kVT) {
-            const int cnt = min(kVT, k - t0);
+        for (int t0 = lo; t0 < hi; t0 += kVT) {
+            const int cnt = min(kVT, hi - t0);
             __syncthreads();
             for (int q = threadIdx.x; q < cnt * Dp; q += kMT) {
                 const int j = q / Dp, kk = q - j * Dp;
@@ -698,12 +745,11 @@ k_b_merge_pairs(const BFrame* __restrict__ frames, const BState* __restrict__ st
                 for (int j = 0; j < cnt; ++j) {
                     if (s_rank[j] >= ra || s_state[j] == kRemoved) continue;
                     if (cos_at_least<Dp>(x, tile + j * Dp, thr_f, thr)) {
-                        if (deg < kMergeCap) conf[(base + a) * kMergeCap + deg] = t0 + j;
-                        ++deg;
+                        const int slot = atomicAdd(&conf_deg[base + a], 1);
+                        if (slot < kMergeCap) conf[(base + a) * kMergeCap + slot] = t0 + j;
                     }
                 }
         }
-        if (a < k) conf_deg[base + a] = act ? deg : 0;
         __syncthreads();
     }
 }
@@ -945,7 +991,7 @@ k_b_label(const BFrame* __restrict__ frames, const BState* __restrict__ states, 
 float ceil_f(double c) { return ceil_to_float(c); }
 
 template <int Dp>
-ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h, int64_t* nlaunch) {
+ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h, bool with_cond, int64_t* nlaunch) {
     const int B = b->B;
     const float cf = ceil_f(b->cfg.bandwidth_cos);
     const float mf = (float)b->cfg.merge_cos;
@@ -957,9 +1003,12 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     k_b_seed<<<B, kIT, 0, s>>>(b->frames, b->states, b->P32, Dp, b->covered, b->X, b->seed_pix, b->seed_order,
                                b->act[0], b->sstate, b->cfg.max_rounds, b->cfg.all_seeds);
     LAUNCHED("k_b_seed");
-    const int target = b->tc ? 2 * b->tc_grid : 2 * b->f32_grid;
-    k_b_plan<<<1, kIT, 0, s>>>(b->frames, b->states, B, b->plan, target, b->cfg.batch_split ? 0 : target,
-                               b->tc ? 1 : 0);
+    // Split 0 gives every frame the single-frame target (2 x grid), so each
+    // frame's results equal a single-frame run's; split 1 shares
+    // target_mult x grid items across the iterating frames by their work.
+    const int grid_shift = b->tc ? b->tc_grid : b->f32_grid;
+    k_b_plan<<<1, kIT, 0, s>>>(b->frames, b->states, B, b->plan, b->target_mult * grid_shift,
+                               b->split ? 0 : 2 * grid_shift, b->tc ? 1 : 0);
     LAUNCHED("k_b_plan");
     if (b->prof) {
         k_b_tick<<<1, 1, 0, s>>>(b->misc, b->plan.item_off + B, 0);
@@ -984,19 +1033,26 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     k_b_check<<<(B + 255) / 256, 256, 0, s>>>(b->states, B, gamma, b->cfg.max_iter);
     LAUNCHED("k_b_check");
     // merge chain for the frames whose round ended
-    k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, B, kSelDoneSeeds, 256, b->blk_off);
+    k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, B, kSelDoneSeeds, 256, 0, b->blk_off);
     LAUNCHED("k_b_blocks");
     k_b_collect<<<G, 256, 0, s>>>(b->frames, b->states, B, b->blk_off, b->sstate, b->cand);
     LAUNCHED("k_b_collect");
-    k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, B, kSelDoneCands, kMT, b->blk_off);
+    k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, B, kSelDoneCands, kMT, 0, b->blk_off);
     LAUNCHED("k_b_blocks");
-    k_b_rank<<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_off, b->cand, b->support, b->seed_order,
-                               b->cand_rank, b->rank_cand);
+    k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, B, kSelDoneCands, kMT, 4 * b->num_sms, b->blk_split);
+    LAUNCHED("k_b_blocks");
+    k_b_merge_zero<<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_off, b->cand_rank, b->cand_state,
+                                     b->conf_deg);
+    LAUNCHED("k_b_merge_zero");
+    k_b_rank<<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_split, b->cand, b->support, b->seed_order,
+                               b->cand_rank);
     LAUNCHED("k_b_rank");
-    k_b_merge_old<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_off, b->X, b->cand, b->modes, mf,
+    k_b_rank_invert<<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_off, b->cand_rank, b->rank_cand);
+    LAUNCHED("k_b_rank_invert");
+    k_b_merge_old<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_split, b->X, b->cand, b->modes, mf,
                                         b->cfg.merge_cos, b->cand_state);
     LAUNCHED("k_b_merge_old");
-    k_b_merge_pairs<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_off, b->X, b->cand, b->cand_rank,
+    k_b_merge_pairs<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_split, b->X, b->cand, b->cand_rank,
                                           b->cand_state, mf, b->cfg.merge_cos, b->conf_deg, b->conf);
     LAUNCHED("k_b_merge_pairs");
     for (int sw = 0; sw < 8; ++sw) {
@@ -1010,7 +1066,7 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     k_b_merge_append<Dp><<<B, kIT, 0, s>>>(b->frames, b->states, b->X, b->cand, b->rank_cand, b->cand_state,
                                            b->modes);
     LAUNCHED("k_b_merge_append");
-    k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, B, kSelDonePixels, kPT, b->blk_off);
+    k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, B, kSelDonePixels, kPT, 0, b->blk_off);
     LAUNCHED("k_b_blocks");
     k_b_cover<Dp><<<G, kPT, 0, s>>>(b->frames, b->states, B, b->blk_off, b->d, b->P32, b->pix, b->covered, b->modes,
                                     (float)b->cfg.bandwidth_cos, b->cfg.bandwidth_cos);
@@ -1018,8 +1074,10 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     k_b_schedule<<<(B + 255) / 256, 256, 0, s>>>(b->states, B, b->cfg.P_target, L, b->cfg.H, b->cfg.max_rounds,
                                                  b->cfg.all_seeds);
     LAUNCHED("k_b_schedule");
-    k_b_cond<<<1, 32, 0, s>>>(b->states, B, b->misc, h);
-    LAUNCHED("k_b_cond");
+    if (with_cond) {
+        k_b_cond<<<1, 32, 0, s>>>(b->states, B, b->misc, h);
+        LAUNCHED("k_b_cond");
+    }
 #undef LAUNCHED
     *nlaunch = nl;
     return MS_OK;
@@ -1052,7 +1110,7 @@ ms_status enqueue_setup(ms_batch* b, cudaStream_t s) {
 
 template <int Dp>
 ms_status enqueue_label(ms_batch* b, cudaStream_t s) {
-    k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, b->B, kSelAllPixels, kPT, b->blk_off);
+    k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, b->B, kSelAllPixels, kPT, 0, b->blk_off);
     MS_LAUNCH("k_b_blocks");
     k_b_label<Dp><<<b->grid, kPT, 0, s>>>(b->frames, b->states, b->B, b->blk_off, b->d, b->P32, b->pix, b->modes,
                                           b->label_ptrs);
@@ -1092,7 +1150,7 @@ ms_status build_graph(ms_batch* b) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     MS_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     int64_t nl = 0;
-    st = enqueue_body<Dp>(b, s, h, &nl);
+    st = enqueue_body<Dp>(b, s, h, true, &nl);
     st2 = cuda_check(cudaStreamEndCapture(s, &tmp), "end capture (body)");
     if (st != MS_OK) return st;
     if (st2 != MS_OK) return st2;
@@ -1105,6 +1163,19 @@ ms_status build_graph(ms_batch* b) {
     b->body_launches = nl;
     b->fixed_launches = (b->tc ? 5 : 4) + 2;
     return MS_OK;
+}
+
+// The graph's kernels as ordinary launches on the batch's stream: set-up,
+// `passes` loop bodies (without the loop-control kernel) and labelling.
+template <int Dp>
+ms_status enqueue_eager(ms_batch* b, int passes) {
+    ms_status st = enqueue_setup<Dp>(b, b->stream);
+    for (int p = 0; st == MS_OK && p < passes; ++p) {
+        int64_t nl = 0;
+        st = enqueue_body<Dp>(b, b->stream, cudaGraphConditionalHandle{}, false, &nl);
+    }
+    if (st == MS_OK) st = enqueue_label<Dp>(b, b->stream);
+    return st;
 }
 
 ms_status rebuild_graph(ms_batch* b) {
@@ -1155,6 +1226,8 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
     b->grid = b->num_sms * 8;
+    b->split = cfg->batch_split;
+    b->target_mult = 2;
     b->tc_grid = b->num_sms;
     b->f32_grid = b->num_sms * shift_blocks_per_sm();
     std::vector<BFrame> hf((size_t)B);
@@ -1188,7 +1261,7 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
     const int Dp = b->Dp;
     const size_t n = (size_t)b->total_px;
     const size_t sizes[] = {
-        sizeof(BFrame) * B, sizeof(BState) * B, sizeof(int32_t) * (B + 1) * 5, 64,
+        sizeof(BFrame) * B, sizeof(BState) * B, sizeof(int32_t) * ((B + 1) * 4 + (B + 2) * 2), 64,
         n * Dp * 4, n * 4, n, n * Dp * 4, n * 4, n * 4, n, n * 4, n * 4, n * 4,
         n * (Dp + 1) * 8, n * Dp * 4, n * 4, n * 4, n * 4, n, n * 4, n * kMergeCap * 4,
         (size_t)B * b->nblk_max * 4 + 4, b->tc ? (size_t)b->total_pk_rows * 128 : 0, sizeof(int32_t*) * B};
@@ -1213,6 +1286,7 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
     b->plan.chunks = planmem + 2 * (B + 1);
     b->plan.tpc = planmem + 3 * (B + 1);
     b->blk_off = planmem + 4 * (B + 1);
+    b->blk_split = b->blk_off + (B + 2);
     b->misc = (int32_t*)(w + offs[3]);
     b->P32 = (float*)(w + offs[4]);
     b->pix = (int32_t*)(w + offs[5]);
@@ -1301,6 +1375,76 @@ extern "C" ms_status ms_batch_run_host(ms_batch* b, const float* const* h_embs, 
     if (b->h_misc[1] & 1) return set_error(MS_ERR_INVALID_ARG, "a foreground embedding has zero or non-finite norm");
     if (b->h_misc[1] & 2) return set_error(MS_ERR_TIMEOUT, "a bounded device wait or the pass limit was hit");
     return MS_OK;
+}
+
+extern "C" ms_status ms_batch_run_eager(ms_batch* b, int32_t passes) {
+    if (!b || passes < 0) return set_error(MS_ERR_INVALID_ARG, "bad arguments");
+    ms_status st = b->Dp == 16 ? enqueue_eager<16>(b, passes) : enqueue_eager<32>(b, passes);
+    if (st != MS_OK) return st;
+    MS_CUDA(cudaMemcpyAsync(b->h_states, b->states, sizeof(BState) * b->B, cudaMemcpyDeviceToHost, b->stream));
+    MS_CUDA(cudaMemcpyAsync(b->h_misc, b->misc, sizeof(b->h_misc), cudaMemcpyDeviceToHost, b->stream));
+    MS_CUDA(cudaStreamSynchronize(b->stream));
+    b->h_misc[0] = passes;
+    if (b->h_misc[1] & 1) return set_error(MS_ERR_INVALID_ARG, "a foreground embedding has zero or non-finite norm");
+    if (b->h_misc[1] & 2) return set_error(MS_ERR_TIMEOUT, "a bounded device wait gave up");
+    for (int f = 0; f < b->B; ++f)
+        if (b->h_states[f].phase != kFinished) return set_error(MS_ERR_STATE, "frame %d unfinished after %d passes", f, passes);
+    return MS_OK;
+}
+
+extern "C" ms_status ms_batch_configure(ms_batch* b, int32_t batch_split, int32_t target_mult) {
+    if (!b || (batch_split != 0 && batch_split != 1) || target_mult < 1 || target_mult > 64)
+        return set_error(MS_ERR_INVALID_ARG, "bad arguments");
+    if (batch_split == b->split && target_mult == b->target_mult) return MS_OK;
+    MS_CUDA(cudaStreamSynchronize(b->stream));
+    b->split = batch_split;
+    b->target_mult = target_mult;
+    return rebuild_graph(b);
+}
+
+extern "C" ms_status ms_batch_autotune(ms_batch* b, int32_t reps, ms_tune_result* results, int32_t cap,
+                                       int32_t* n_results) {
+    if (!b || reps < 1 || reps > 100) return set_error(MS_ERR_INVALID_ARG, "bad arguments");
+    static const int kCand[][2] = {{0, 2}, {1, 1}, {1, 2}, {1, 4}, {1, 8}};
+    const int nc = (int)(sizeof(kCand) / sizeof(kCand[0]));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MS_CUDA(cudaEventCreate(&e0));
+    ms_status st = cuda_check(cudaEventCreate(&e1), "cudaEventCreate");
+    int best = -1;
+    double best_ms = 0.0;
+    for (int c = 0; st == MS_OK && c < nc; ++c) {
+        st = ms_batch_configure(b, kCand[c][0], kCand[c][1]);
+        if (st == MS_OK) st = ms_batch_run(b, 1);  // warm-up, and the error check
+        std::vector<float> t;
+        for (int r = 0; st == MS_OK && r < reps; ++r) {
+            st = cuda_check(cudaEventRecord(e0, b->stream), "cudaEventRecord");
+            if (st == MS_OK) st = cuda_check(cudaGraphLaunch(b->exec, b->stream), "cudaGraphLaunch");
+            if (st == MS_OK) st = cuda_check(cudaEventRecord(e1, b->stream), "cudaEventRecord");
+            if (st == MS_OK) st = cuda_check(cudaEventSynchronize(e1), "cudaEventSynchronize");
+            float ms_ = 0.f;
+            if (st == MS_OK) st = cuda_check(cudaEventElapsedTime(&ms_, e0, e1), "cudaEventElapsedTime");
+            t.push_back(ms_);
+        }
+        if (st != MS_OK) break;
+        std::sort(t.begin(), t.end());
+        const double med = t[t.size() / 2];
+        if (results && c < cap) {
+            results[c].batch_split = kCand[c][0];
+            results[c].target_mult = kCand[c][1];
+            results[c].ms = med;
+        }
+        if (best < 0 || med < best_ms) {
+            best = c;
+            best_ms = med;
+        }
+    }
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != MS_OK) return st;
+    if (n_results) *n_results = nc < cap ? nc : cap;
+    st = ms_batch_configure(b, kCand[best][0], kCand[best][1]);
+    if (st == MS_OK) st = ms_batch_run(b, 1);  // leave the batch's outputs from the chosen configuration
+    return st;
 }
 
 extern "C" ms_status ms_batch_stats(const ms_batch* b, int32_t frame, ms_stats* out) {

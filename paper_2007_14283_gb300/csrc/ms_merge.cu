@@ -33,9 +33,11 @@ __global__ void k_collect(const uint8_t* __restrict__ sstate, int m, int32_t* __
     if (c) cand[base + __popc(b & ((1u << lane) - 1u))] = s;
 }
 
+// Rank of every candidate in (support desc, seed order asc): the count of
+// candidates ahead of it. Block (x, y) counts candidate block x against slice y
+// of all candidates and adds its partial count (ranks start at 0).
 __global__ void k_rank(const int32_t* __restrict__ cand, int k, const int32_t* __restrict__ support,
-                       const int32_t* __restrict__ order, int32_t* __restrict__ cand_rank,
-                       int32_t* __restrict__ rank_cand) {
+                       const int32_t* __restrict__ order, int32_t* __restrict__ cand_rank) {
     __shared__ int32_t s_sup[256], s_ord[256];
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     int sa = 0, oa = 0;
@@ -43,23 +45,26 @@ __global__ void k_rank(const int32_t* __restrict__ cand, int k, const int32_t* _
         sa = support[cand[a]];
         oa = order[cand[a]];
     }
+    const int lo = (int)((int64_t)blockIdx.y * k / gridDim.y), hi = (int)((int64_t)(blockIdx.y + 1) * k / gridDim.y);
     int r = 0;
-    for (int base = 0; base < k; base += 256) {
+    for (int base = lo; base < hi; base += 256) {
         const int b = base + threadIdx.x;
-        if (b < k) {
+        if (b < hi) {
             s_sup[threadIdx.x] = support[cand[b]];
             s_ord[threadIdx.x] = order[cand[b]];
         }
         __syncthreads();
-        const int lim = min(256, k - base);
+        const int lim = min(256, hi - base);
         for (int j = 0; j < lim; ++j)
             r += (s_sup[j] > sa) || (s_sup[j] == sa && s_ord[j] < oa);
         __syncthreads();
     }
-    if (a < k) {
-        cand_rank[a] = r;
-        rank_cand[r] = a;
-    }
+    if (a < k && r) atomicAdd(&cand_rank[a], r);
+}
+
+__global__ void k_rank_invert(const int32_t* __restrict__ cand_rank, int k, int32_t* __restrict__ rank_cand) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < k) rank_cand[cand_rank[a]] = a;
 }
 
 template <int Dp>
@@ -71,7 +76,9 @@ __device__ __forceinline__ void load_vec(float* dst, const float* src) {
     }
 }
 
-// Candidates within merge_cos of a mode kept in an earlier round are removed.
+// Candidates within merge_cos of a mode kept in an earlier round are removed
+// (cand_state starts at kUndecided). Block (x, y): candidate block x against
+// slice y of the old modes.
 template <int Dp>
 __global__ void __launch_bounds__(kMT)
 k_merge_old(const float* __restrict__ X, const int32_t* __restrict__ cand, int k,
@@ -82,8 +89,10 @@ k_merge_old(const float* __restrict__ X, const int32_t* __restrict__ cand, int k
     float x[Dp];
     if (a < k) load_vec<Dp>(x, X + (int64_t)cand[a] * Dp);
     bool removed = false;
-    for (int base = 0; base < K_old; base += kVT) {
-        const int cnt = min(kVT, K_old - base);
+    const int lo = (int)((int64_t)blockIdx.y * K_old / gridDim.y);
+    const int hi = (int)((int64_t)(blockIdx.y + 1) * K_old / gridDim.y);
+    for (int base = lo; base < hi; base += kVT) {
+        const int cnt = min(kVT, hi - base);
         for (int q = threadIdx.x; q < cnt * Dp; q += kMT) tile[q] = modes[(int64_t)base * Dp + q];
         __syncthreads();
         if (a < k && !removed) {
@@ -95,11 +104,13 @@ k_merge_old(const float* __restrict__ X, const int32_t* __restrict__ cand, int k
         }
         __syncthreads();
     }
-    if (a < k) cand_state[a] = removed ? kRemoved : kUndecided;
+    if (a < k && removed) cand_state[a] = kRemoved;
 }
 
 // Higher-ranked conflicting candidates of each undecided candidate: the first
-// kMergeCap are stored, conf_deg counts all of them.
+// kMergeCap found are stored (in no particular order; the resolve step treats
+// them as a set), conf_deg (starting at 0) counts all of them. Block (x, y):
+// candidate block x against slice y of all candidates.
 template <int Dp>
 __global__ void __launch_bounds__(kMT)
 k_merge_pairs(const float* __restrict__ X, const int32_t* __restrict__ cand, int k,
@@ -113,9 +124,9 @@ k_merge_pairs(const float* __restrict__ X, const int32_t* __restrict__ cand, int
     const int ra = a < k ? cand_rank[a] : 0;
     float x[Dp];
     if (act) load_vec<Dp>(x, X + (int64_t)cand[a] * Dp);
-    int deg = 0;
-    for (int base = 0; base < k; base += kVT) {
-        const int cnt = min(kVT, k - base);
+    const int lo = (int)((int64_t)blockIdx.y * k / gridDim.y), hi = (int)((int64_t)(blockIdx.y + 1) * k / gridDim.y);
+    for (int base = lo; base < hi; base += kVT) {
+        const int cnt = min(kVT, hi - base);
         for (int q = threadIdx.x; q < cnt * Dp; q += kMT) {
             const int j = q / Dp, kk = q - j * Dp;
             tile[q] = X[(int64_t)cand[base + j] * Dp + kk];
@@ -129,14 +140,13 @@ k_merge_pairs(const float* __restrict__ X, const int32_t* __restrict__ cand, int
             for (int j = 0; j < cnt; ++j) {
                 if (s_rank[j] >= ra || s_state[j] == kRemoved) continue;
                 if (cos_at_least<Dp>(x, tile + j * Dp, thr_f, thr)) {
-                    if (deg < kMergeCap) conf[(int64_t)a * kMergeCap + deg] = base + j;
-                    ++deg;
+                    const int slot = atomicAdd(&conf_deg[a], 1);
+                    if (slot < kMergeCap) conf[(int64_t)a * kMergeCap + slot] = base + j;
                 }
             }
         }
         __syncthreads();
     }
-    if (a < k) conf_deg[a] = act ? deg : 0;
 }
 
 template <int Dp>
@@ -292,21 +302,38 @@ k_cover(const float* __restrict__ P32, const float* __restrict__ emb, int d,
     if (threadIdx.x == 0 && newly) atomicSub(&dc->n_uncovered, newly);
 }
 
+// Slices of an O(outer x inner) loop so that the grid fills about four waves
+// of the GPU: the candidate blocks alone are often fewer than the SMs.
+unsigned inner_slices(int outer_blocks, int inner, int num_sms) {
+    int sl = (4 * num_sms + outer_blocks - 1) / outer_blocks;
+    const int max_sl = (inner + kVT - 1) / kVT;
+    sl = sl > max_sl ? max_sl : sl;
+    sl = sl > 64 ? 64 : sl;
+    return (unsigned)(sl < 1 ? 1 : sl);
+}
+
 template <int Dp>
 ms_status merge_prepare_t(ms_ctx* ctx, int32_t k) {
     const float thr_f = (float)ctx->cfg.merge_cos;
     const double thr = ctx->cfg.merge_cos;
     const unsigned g256 = (unsigned)((k + 255) / 256), gm = (unsigned)((k + kMT - 1) / kMT);
-    k_rank<<<g256, 256, 0, ctx->stream>>>(ctx->cand, k, ctx->support, ctx->seed_order, ctx->cand_rank,
-                                          ctx->rank_cand);
+    MS_CUDA(cudaMemsetAsync(ctx->cand_rank, 0, sizeof(int32_t) * (size_t)k, ctx->stream));
+    MS_CUDA(cudaMemsetAsync(ctx->cand_state, kUndecided, (size_t)k, ctx->stream));
+    MS_CUDA(cudaMemsetAsync(ctx->conf_deg, 0, sizeof(int32_t) * (size_t)k, ctx->stream));
+    k_rank<<<dim3(g256, inner_slices((int)g256, k, ctx->num_sms)), 256, 0, ctx->stream>>>(
+        ctx->cand, k, ctx->support, ctx->seed_order, ctx->cand_rank);
     MS_LAUNCH("k_rank");
-    k_merge_old<Dp><<<gm, kMT, 0, ctx->stream>>>(ctx->X, ctx->cand, k, ctx->modes, ctx->n_kept, thr_f,
-                                                 thr, ctx->cand_state);
-    MS_LAUNCH("k_merge_old");
-    k_merge_pairs<Dp><<<gm, kMT, 0, ctx->stream>>>(ctx->X, ctx->cand, k, ctx->cand_rank, ctx->cand_state,
-                                                   thr_f, thr, ctx->conf_deg, ctx->conf);
+    k_rank_invert<<<g256, 256, 0, ctx->stream>>>(ctx->cand_rank, k, ctx->rank_cand);
+    MS_LAUNCH("k_rank_invert");
+    if (ctx->n_kept > 0) {
+        k_merge_old<Dp><<<dim3(gm, inner_slices((int)gm, ctx->n_kept, ctx->num_sms)), kMT, 0, ctx->stream>>>(
+            ctx->X, ctx->cand, k, ctx->modes, ctx->n_kept, thr_f, thr, ctx->cand_state);
+        MS_LAUNCH("k_merge_old");
+    }
+    k_merge_pairs<Dp><<<dim3(gm, inner_slices((int)gm, k, ctx->num_sms)), kMT, 0, ctx->stream>>>(
+        ctx->X, ctx->cand, k, ctx->cand_rank, ctx->cand_state, thr_f, thr, ctx->conf_deg, ctx->conf);
     MS_LAUNCH("k_merge_pairs");
-    ctx->launches += 3;
+    ctx->launches += 4;
     return MS_OK;
 }
 

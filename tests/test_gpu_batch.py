@@ -181,3 +181,49 @@ def test_batch_host_buffers_and_profile(ms_lib):
         assert st["launches"] > st0["launches"]  # two timer kernels per pass
     finally:
         b.close()
+
+
+def test_batch_eager_launches_equal_graph(ms_lib):
+    import torch
+    fs = synth.batch_c4(seed=11, B=3, n_lo=800, n_hi=6000)
+    embs, masks = _to_dev([(f.emb, f.mask) for f in fs])
+    b = _batch(ms_lib, embs, masks, precision=ms_lib.MS_BF16)
+    try:
+        ref = [t.clone() for t in b.labels]
+        passes = ms_lib.ms_batch_stats(b, -1)["reserved0"]
+        st_ref = [ms_lib.ms_batch_stats(b, f) for f in range(3)]
+        for t in b.labels:
+            t.fill_(7)
+        ms_lib.ms_batch_run_eager(b, passes + 2)
+        for a, c in zip(ref, b.labels):
+            assert torch.equal(a, c)
+        for f in range(3):
+            assert ms_lib.ms_batch_stats(b, f)["seed_iters"] == st_ref[f]["seed_iters"]
+        with pytest.raises(ms_lib.MsError):
+            ms_lib.ms_batch_run_eager(b, 1)  # too few passes to finish
+    finally:
+        b.close()
+
+
+def test_batch_autotune_picks_a_candidate_and_keeps_results_valid(ms_lib):
+    fs = synth.batch_c4(seed=12, B=4, n_lo=1000, n_hi=8000)
+    embs, masks = _to_dev([(f.emb, f.mask) for f in fs])
+    b = _batch(ms_lib, embs, masks, precision=ms_lib.MS_BF16)
+    try:
+        res = ms_lib.ms_batch_autotune(b, reps=2)
+        assert [(r["batch_split"], r["target_mult"]) for r in res] == [(0, 2), (1, 1), (1, 2), (1, 4), (1, 8)]
+        assert all(r["ms"] > 0 for r in res)
+        # the batch now holds the fastest candidate's outputs: still within the oracle bar
+        for i, f in enumerate(fs[:2]):
+            ref = oracle.run(f.emb, f.mask, frame_id=i)
+            modes = ms_lib.ms_batch_modes(b, i)
+            assert mode_errors(modes, ref.modes).max() <= MODE_TOL
+            assert matched_agreement(ref.labels, b.labels[i].cpu().numpy()) >= 0.999
+        # configuring the canonical split again reproduces single-frame results exactly
+        ms_lib.ms_batch_configure(b, 0, 2)
+        ms_lib.ms_batch_run(b)
+        lab_s, modes_s, _ = _single(ms_lib, embs[0], masks[0], 0, precision=ms_lib.MS_BF16)
+        assert np.array_equal(ms_lib.ms_batch_modes(b, 0), modes_s)
+        assert np.array_equal(b.labels[0].cpu().numpy(), lab_s)
+    finally:
+        b.close()

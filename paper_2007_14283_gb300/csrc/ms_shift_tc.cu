@@ -20,12 +20,14 @@
 // kernel normalises the seeds and tests convergence in FP64.
 //
 // Warp roles (608 threads, one CTA per SM): warp 0 issues TMA loads of pixel
-// tiles into an 11-stage ring; warp 1 owns TMEM (512 columns: two S, two Y and
-// two mask buffers) and issues GEMM1, running ahead of the mask warps as far
+// tiles into an 11-stage ring; warp 1 owns TMEM (512 columns: two S, one Y and
+// three mask buffers) and issues GEMM1, running ahead of the mask warps as far
 // as the S buffers allow; warp 2 issues GEMM2 as each mask tile lands; warps
 // 3-18 build the mask, four warps per 32-lane TMEM quadrant, 32 pixels each,
-// and store it to TMEM, where GEMM2 reads it as its A operand. Seed operands (A1), S, masks and Y
-// are double-buffered. All waits are bounded; a timeout
+// and store it to TMEM, where GEMM2 reads it as its A operand. Seed operands
+// (A1) and S are double-buffered, masks triple-buffered (the mask warps would
+// otherwise wait for GEMM2's commit round trip), Y single (one item at a time;
+// the next item's first GEMM2 waits for the epilogue's read). All waits are bounded; a timeout
 // raises the CTA's abort flag, drains what is in flight, frees TMEM and
 // reports MS_ERR_TIMEOUT through the frame's status word.
 #include <cudaTypedefs.h>
@@ -45,16 +47,17 @@ constexpr int kTcThreads = (kMaskWarp0 + kMaskWarps) * 32;  // 608
 constexpr int kStages = 11;            // pixel-tile ring
 constexpr int kTileBytes = 128 * 128;  // 128 rows x 128 bytes
 constexpr uint32_t kTmemCols = 512;
+constexpr int kMBufs = 3;              // mask tiles in TMEM
 constexpr uint32_t kColS = 0;          // two S accumulators, 128 columns each
-constexpr uint32_t kColY = 256;        // two Y accumulators, 64 columns each
-constexpr uint32_t kColM = 384;        // two mask tiles (GEMM2's A), 64 columns each
+constexpr uint32_t kColY = 256;        // one Y accumulator, 64 columns
+constexpr uint32_t kColM = 320;        // three mask tiles (GEMM2's A), 64 columns each
 constexpr float kBand = 6.103515625e-05f;    // 2^-14
 constexpr float kFixScale = 68719476736.0f;  // 2^36
 
 constexpr int kOffA1 = 0;                              // 2 x 16 KB
 constexpr int kOffP = 2 * kTileBytes;                  // kStages x 16 KB
 constexpr int kOffBar = kOffP + kStages * kTileBytes;
-constexpr int kNumBars = 2 * kStages + 7 * 2 + 2;
+constexpr int kNumBars = 2 * kStages + 2 * 2 + 2 * kMBufs + 2 + 2 + 2;
 constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 16 + 1024;  // + alignment slack
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
@@ -206,12 +209,12 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
     uint64_t* empty = full + kStages;             // [kStages] pixel tile consumed by GEMM2
     uint64_t* s_full = empty + kStages;           // [2] GEMM1 done
     uint64_t* s_empty = s_full + 2;               // [2] S read by the mask warps
-    uint64_t* m_full = s_empty + 2;               // [2] mask tile stored to TMEM by every mask warp
-    uint64_t* m_empty = m_full + 2;               // [2] mask tile consumed by GEMM2
-    uint64_t* a1_full = m_empty + 2;              // [2] seed operand written
-    uint64_t* d_full = a1_full + 2;               // [2] Y of an item complete
-    uint64_t* d_empty = d_full + 2;               // [2] Y read by the epilogue
-    uint64_t* aux = d_empty + 2;                  // [2] drain barriers of the two MMA issuers
+    uint64_t* m_full = s_empty + 2;               // [kMBufs] mask tile stored to TMEM by every mask warp
+    uint64_t* m_empty = m_full + kMBufs;          // [kMBufs] mask tile consumed by GEMM2
+    uint64_t* a1_full = m_empty + kMBufs;         // [2] seed operand written
+    uint64_t* d_full = a1_full + 2;               // Y of an item complete
+    uint64_t* d_empty = d_full + 1;               // Y read by the epilogue
+    uint64_t* aux = d_empty + 1;                  // [2] drain barriers of the two MMA issuers
     uint32_t* tmem_slot = (uint32_t*)(bars + kNumBars);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
 
@@ -224,12 +227,14 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
         for (int b = 0; b < 2; ++b) {
             mbar_init(&s_full[b], 1);
             mbar_init(&s_empty[b], kMaskWarps);
+            mbar_init(&a1_full[b], 128);
+        }
+        for (int b = 0; b < kMBufs; ++b) {
             mbar_init(&m_full[b], kMaskWarps);
             mbar_init(&m_empty[b], 1);
-            mbar_init(&a1_full[b], 128);
-            mbar_init(&d_full[b], 1);
-            mbar_init(&d_empty[b], 128);
         }
+        mbar_init(d_full, 1);
+        mbar_init(d_empty, 128);
         mbar_init(&aux[0], 1);
         mbar_init(&aux[1], 1);
         *abort = 0;
@@ -311,21 +316,21 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
             for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
                 const TcItem ii = map.item(item);
                 for (int pt = ii.pt0; pt < ii.pt1; ++pt, ++g) {
-                    const int s = g % kStages, b = g & 1;
+                    const int s = g % kStages, mb = g % kMBufs;
                     const bool first = pt == ii.pt0;
-                    if (!(ok = mbar_wait(&m_full[b], (g >> 1) & 1, abort))) break;
+                    if (!(ok = mbar_wait(&m_full[mb], (g / kMBufs) & 1, abort))) break;
                     if (!(ok = mbar_wait(&full[s], (g / kStages) & 1, abort))) break;
-                    if (first && it >= 2 && !(ok = mbar_wait(&d_empty[it & 1], ((it >> 1) - 1) & 1, abort))) break;
+                    if (first && it >= 1 && !(ok = mbar_wait(d_empty, (it - 1) & 1, abort))) break;
                     tc_fence_after();
-                    const uint32_t tY = tmem + kColY + (it & 1) * 64;
-                    const uint32_t tM = tmem + kColM + b * 64;
+                    const uint32_t tY = tmem + kColY;
+                    const uint32_t tM = tmem + kColM + mb * 64;
                     const uint64_t pb = dP2 + (uint64_t)s * kT;
 #pragma unroll
                     for (int k = 0; k < 8; ++k)
                         mma_bf16_ts(tY, tM + 8 * k, pb + k * 128, id2, (first && k == 0) ? 0u : 1u);
-                    mma_commit(&m_empty[b]);
+                    mma_commit(&m_empty[mb]);
                     mma_commit(&empty[s]);
-                    if (pt == ii.pt1 - 1) mma_commit(&d_full[it & 1]);
+                    if (pt == ii.pt1 - 1) mma_commit(d_full);
                 }
             }
             if (*abort) {
@@ -425,27 +430,28 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                     for (int i = 0; i < 32; ++i)
                         dbg_S[(int64_t)r * dbg_stride + pt * 128 + h * 32 + i] = __uint_as_float(v[i]);
                 }
-                if (g >= 2 && !(ok = warp_wait(&m_empty[b], ((g >> 1) - 1) & 1, abort))) break;
+                const int mb = g % kMBufs;
+                if (g >= kMBufs && !(ok = warp_wait(&m_empty[mb], ((g / kMBufs) - 1) & 1, abort))) break;
                 tc_fence_after();
-                tmem_st16(tmem + kColM + b * 64 + lane_base + h * 16, w);
+                tmem_st16(tmem + kColM + mb * 64 + lane_base + h * 16, w);
                 tmem_st_wait();
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&m_full[b]);
+                if (lane == 0) mbar_arrive(&m_full[mb]);
             }
             if (!ok) break;
             if (h == 0) {
-                if (!warp_wait(&d_full[it & 1], (it >> 1) & 1, abort)) break;
+                if (!warp_wait(d_full, it & 1, abort)) break;
                 tc_fence_after();
                 uint32_t yh[16], ym[16], yl[16], yc[16];
-                const uint32_t ty = tmem + kColY + (it & 1) * 64 + lane_base;
+                const uint32_t ty = tmem + kColY + lane_base;
                 tmem_ld16(ty, yh);
                 tmem_ld16(ty + 16, ym);
                 tmem_ld16(ty + 32, yl);
                 tmem_ld16(ty + 48, yc);
                 tmem_ld_wait();
                 tc_fence_before();
-                mbar_arrive(&d_empty[it & 1]);
+                mbar_arrive(d_empty);
                 const float cntf = __uint_as_float(yc[0]);
                 if (slot >= 0 && cntf > 0.f) {
                     unsigned long long* a = acc + (int64_t)slot * 17;

@@ -61,6 +61,7 @@ def parse():
                     help="oracle baseline: one full frame (also gives the label match), a seed sample, or none")
     ap.add_argument("--cpu-seeds", type=int, default=8192, help="seeds in the oracle's sampled run")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-vmf", action="store_true", help="skip the smooth-kernel (vMF) forward/adjoint leg")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched forms: skip the work-split autotuner (keep the canonical split)")
     ap.add_argument("--eager", action="store_true",
@@ -406,6 +407,50 @@ def roofline_of(form, tot, step_ms, clk, n_sm):
             "avg_launch_ms": tot["shift_ms"] / max(1, tot["shift_launches"])}
 
 
+def vmf_leg(n_sm, clk):
+    """Smooth-kernel form on the differentiable configuration: N = 65536 pixels,
+    M = 1024 seeds, d = 16, kappa = 20, T = 10. Times ms_vmf_forward and
+    ms_vmf_backward (CUDA events, median of 5 after 2 warm-ups). Bound: one exp
+    per seed-pixel pair and step on the special-function units; the backward
+    re-runs the forward and evaluates each weight once more per step."""
+    import torch
+
+    import paper_2007_14283_gb300 as ms
+    import synth
+    prob = synth.vmf_problem_c5(seed=0, N=65536, M=1024, K=32)
+    P = torch.from_numpy(prob["P"]).cuda()
+    X0 = torch.from_numpy(prob["X0"]).cuda()
+    G = (torch.from_numpy(prob["target"]).cuda() - X0) * 2.0
+    kappa, T = 20.0, 10
+    stream = torch.cuda.current_stream()
+
+    def timed_ms(fn):
+        for _ in range(2):
+            fn()
+        ts = []
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+    fwd = timed_ms(lambda: ms.ms_vmf_forward(P, X0, kappa, T))
+    bwd = timed_ms(lambda: ms.ms_vmf_backward(P, X0, kappa, T, G))
+    pairs = 65536 * 1024 * T
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    mufu_peak = n_sm * 16 * sm_mhz * 1e6  # exp results per second: 16 per SM per clock
+    return {"config": "N=65536 pixels, M=1024 seeds, d=16, kappa=20, T=10 (synthetic vMF cells)",
+            "forward_ms": fwd, "backward_ms": bwd,
+            "forward_exp_per_s": pairs / (fwd * 1e-3), "backward_exp_per_s": 2 * pairs / (bwd * 1e-3),
+            "mufu_peak_exp_per_s": mufu_peak,
+            "forward_frac": pairs / (fwd * 1e-3) / mufu_peak,
+            "backward_frac": 2 * pairs / (bwd * 1e-3) / mufu_peak,
+            "peak_source": f"{n_sm} SMs x 16 exp/clock/SM x {sm_mhz:.0f} MHz (assumed SFU rate)"}
+
+
 def e2e_leg(args, runner, ws):
     """Frames/s through the host-buffer entry points (pinned buffers in, labels out)."""
     import torch
@@ -479,6 +524,9 @@ def run_ours(args, rank, ws, local):
                         "clocks_sm_mhz": c_clk.get("sm_mhz")}
         r.close()
 
+    vmf = None
+    if rank == 0 and not args.no_vmf:
+        vmf = vmf_leg(n_sm, clk)
     cpu, parity = None, None
     if rank == 0 and args.cpu != "none":
         import oracle
@@ -521,7 +569,8 @@ def run_ours(args, rank, ws, local):
                            "autotune": main.tuning,
                            "fp32_rechecked_pair_fraction": tot.get("band_pairs", 0) /
                            max(1.0, float(tot["seed_iters"]) * N_FG)},
-                "roofline": roofline, "forms": forms, "parity_vs_oracle": parity, "cpu_baseline": cpu,
+                "roofline": roofline, "forms": forms, "smooth_kernel": vmf, "parity_vs_oracle": parity,
+                "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": int(reduce_over_ranks(tot["launches"], ws, "sum")), "clocks": clk}
         print(json.dumps(line), flush=True)
 

@@ -19,17 +19,20 @@
 // fixed-point accumulators shared with the FP32 form, and the same finalize
 // kernel normalises the seeds and tests convergence in FP64.
 //
-// Warp roles (608 threads, one CTA per SM): warp 0 issues TMA loads of pixel
-// tiles into an 11-stage ring; warp 1 owns TMEM (512 columns: two S, one Y and
-// three mask buffers) and issues GEMM1, running ahead of the mask warps as far
-// as the S buffers allow; warp 2 issues GEMM2 as each mask tile lands; warps
-// 3-18 build the mask, four warps per 32-lane TMEM quadrant, 32 pixels each,
-// and store it to TMEM, where GEMM2 reads it as its A operand. Seed operands
-// (A1) and S are double-buffered, masks triple-buffered (the mask warps would
-// otherwise wait for GEMM2's commit round trip), Y single (one item at a time;
-// the next item's first GEMM2 waits for the epilogue's read). All waits are bounded; a timeout
-// raises the CTA's abort flag, drains what is in flight, frees TMEM and
-// reports MS_ERR_TIMEOUT through the frame's status word.
+// Warp roles (608 threads, one CTA per SM): warps 0-15 build the mask, four
+// warps per 32-lane TMEM quadrant (warp w reaches lanes 32 * (w % 4) + 0..31),
+// 32 pixels each, and store it to TMEM, where GEMM2 reads it as its A operand;
+// warp 16 issues TMA loads of pixel tiles into an 11-stage ring; warp 17 owns
+// TMEM (512 columns: two S, one Y and three mask buffers) and issues GEMM1,
+// running ahead of the mask warps as far as the S buffers allow; warp 18
+// issues GEMM2 as each mask tile lands. The issuing warps run their loops with
+// all 32 lanes and let one elected lane issue each MMA and commit: a loop run
+// by lane 0 alone issues the MMAs about 1.5x slower. Seed operands (A1) and S
+// are double-buffered, masks triple-buffered (the mask warps would otherwise
+// wait for GEMM2's commit round trip), Y single (one item at a time; the next
+// item's first GEMM2 waits for the epilogue's read). All waits are bounded; a
+// timeout raises the CTA's abort flag, drains what is in flight, frees TMEM
+// and reports MS_ERR_TIMEOUT through the frame's status word.
 #include <cudaTypedefs.h>
 
 #include "ms_batch.cuh"
@@ -41,9 +44,14 @@ namespace {
 
 using namespace tc;
 
-constexpr int kMaskWarps = 16;
-constexpr int kMaskWarp0 = 3;         // warps 0-2: TMA, GEMM1, GEMM2
-constexpr int kTcThreads = (kMaskWarp0 + kMaskWarps) * 32;  // 608
+constexpr int kMaskWarps = 16;                 // warps 0..kMaskWarps-1 build the mask
+constexpr int kPxPerWarp = 512 / kMaskWarps;   // pixels of a tile per mask warp
+constexpr int kSub = kPxPerWarp / 32;          // 32-pixel TMEM loads per mask warp and tile
+constexpr int kWarpTma = kMaskWarps;           // then the TMA producer and the two MMA issuers
+constexpr int kWarpG1 = kMaskWarps + 1;
+constexpr int kWarpG2 = kMaskWarps + 2;
+constexpr int kTcThreads = (kMaskWarps + 3) * 32;
+static_assert(kMaskWarps % 4 == 0 && kPxPerWarp % 32 == 0, "mask warps cover the four TMEM quadrants evenly");
 constexpr int kStages = 11;            // pixel-tile ring
 constexpr int kTileBytes = 128 * 128;  // 128 rows x 128 bytes
 constexpr uint32_t kTmemCols = 512;
@@ -240,8 +248,8 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
         *abort = 0;
         fence_mbar_init();
     }
-    if (warp == 0 && lane == 0) tma_prefetch_desc(&pmap);
-    if (warp == 1) {
+    if (warp == kWarpTma && lane == 0) tma_prefetch_desc(&pmap);
+    if (warp == kWarpG1) {
         tmem_alloc(tmem_slot, kTmemCols);
         tmem_relinquish();
     }
@@ -251,97 +259,97 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
     const uint32_t tmem = *tmem_slot;
     const int items = map.total();
 
-    if (warp == 0) {
+    if (warp == kWarpTma) {
         // ------------------------------------------------ TMA producer
-        if (lane == 0) {
-            int g = 0;
-            for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x) {
-                const TcItem ii = map.item(item);
-                for (int pt = ii.pt0; pt < ii.pt1; ++pt, ++g) {
-                    const int s = g % kStages;
-                    if (g >= kStages && !mbar_wait(&empty[s], ((g / kStages) - 1) & 1, abort)) break;
+        // The three issuing warps run their loops with all 32 lanes (waits
+        // are warp-uniform) and one lane issues; see mma_bf16_warp.
+        int g = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+            const TcItem ii = map.item(item);
+            for (int pt = ii.pt0; pt < ii.pt1; ++pt, ++g) {
+                const int s = g % kStages;
+                if (g >= kStages && !(ok = warp_wait(&empty[s], ((g / kStages) - 1) & 1, abort))) break;
+                if (lane == 0) {
                     mbar_arrive_expect_tx(&full[s], kTileBytes);
                     tma_load_2d(Pst + s * kTileBytes, &pmap, 0, ii.pk_row0 + pt * 128, &full[s]);
                 }
+                __syncwarp();
             }
-            if (*abort)
-                for (int q = max(0, g - kStages); q < g; ++q) drain_wait(&full[q % kStages], (q / kStages) & 1);
         }
-    } else if (warp == 1) {
+        if (lane == 0 && *abort)
+            for (int q = max(0, g - kStages); q < g; ++q) drain_wait(&full[q % kStages], (q / kStages) & 1);
+    } else if (warp == kWarpG1) {
         // ------------------------------------------------ GEMM1 issuer
         // Runs ahead of the mask warps as far as the two S buffers allow.
-        if (lane == 0) {
-            // Descriptors are built once; moving an operand by b bytes adds
-            // b >> 4 to the descriptor's start-address field (no carry: shared
-            // addresses stay below 2^18).
-            const uint64_t dA1 = desc_sw128(smem_u32(A1), 16, 1024);   // seed operand, K-major
-            const uint64_t dP1 = desc_sw128(smem_u32(Pst), 16, 1024);  // pixel tile, K-major
-            constexpr uint32_t id1 = idesc_bf16(128, 128, 0, 0);
-            constexpr uint64_t kT = kTileBytes >> 4;
-            bool ok = true;
-            int g = 0, it = 0;
-            for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
-                const TcItem ii = map.item(item);
-                if (!(ok = mbar_wait(&a1_full[it & 1], (it >> 1) & 1, abort))) break;
-                const uint64_t a = dA1 + (uint64_t)(it & 1) * kT;
-                for (int pt = ii.pt0; pt < ii.pt1; ++pt, ++g) {
-                    const int s = g % kStages, b = g & 1;
-                    if (!(ok = mbar_wait(&full[s], (g / kStages) & 1, abort))) break;
-                    if (g >= 2 && !(ok = mbar_wait(&s_empty[b], ((g >> 1) - 1) & 1, abort))) break;
-                    tc_fence_after();
-                    const uint32_t tS = tmem + kColS + b * 128;
-                    const uint64_t pb = dP1 + (uint64_t)s * kT;
-                    mma_bf16(tS, a, pb, id1, 0);            // Xh . Ph
-                    mma_bf16(tS, a, pb + 2, id1, 1);        // Xh . Pm
-                    mma_bf16(tS, a + 2, pb, id1, 1);        // Xl . Ph
-                    mma_bf16(tS, a + 4, pb + 6, id1, 1);    // -c split . ones
-                    mma_commit(&s_full[b]);
-                }
-            }
-            if (*abort) {
-                mma_commit(&aux[0]);
-                drain_wait(&aux[0], 0);
+        // Descriptors are built once; moving an operand by b bytes adds b >> 4
+        // to the descriptor's start-address field (no carry: shared addresses
+        // stay below 2^18).
+        const uint64_t dA1 = desc_sw128(smem_u32(A1), 16, 1024);   // seed operand, K-major
+        const uint64_t dP1 = desc_sw128(smem_u32(Pst), 16, 1024);  // pixel tile, K-major
+        constexpr uint32_t id1 = idesc_bf16(128, 128, 0, 0);
+        constexpr uint64_t kT = kTileBytes >> 4;
+        bool ok = true;
+        int g = 0, it = 0;
+        for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
+            const TcItem ii = map.item(item);
+            if (!(ok = warp_wait(&a1_full[it & 1], (it >> 1) & 1, abort))) break;
+            const uint64_t a = dA1 + (uint64_t)(it & 1) * kT;
+            for (int pt = ii.pt0; pt < ii.pt1; ++pt, ++g) {
+                const int s = g % kStages, b = g & 1;
+                if (!(ok = warp_wait(&full[s], (g / kStages) & 1, abort))) break;
+                if (g >= 2 && !(ok = warp_wait(&s_empty[b], ((g >> 1) - 1) & 1, abort))) break;
+                tc_fence_after();
+                const uint32_t tS = tmem + kColS + b * 128;
+                const uint64_t pb = dP1 + (uint64_t)s * kT;
+                mma_bf16_warp(tS, a, pb, id1, 0);            // Xh . Ph
+                mma_bf16_warp(tS, a, pb + 2, id1, 1);        // Xh . Pm
+                mma_bf16_warp(tS, a + 2, pb, id1, 1);        // Xl . Ph
+                mma_bf16_warp(tS, a + 4, pb + 6, id1, 1);    // -c split . ones
+                mma_commit_warp(&s_full[b]);
             }
         }
-    } else if (warp == 2) {
+        if (__any_sync(0xffffffffu, *abort)) {
+            mma_commit_warp(&aux[0]);
+            drain_wait(&aux[0], 0);
+        }
+    } else if (warp == kWarpG2) {
         // ------------------------------------------------ GEMM2 issuer
         // Y += Mask . P as soon as a mask tile is in TMEM; the pixel stage is
         // released when these MMAs complete.
-        if (lane == 0) {
-            const uint64_t dP2 = desc_sw128(smem_u32(Pst), kTileBytes, 1024);  // pixel tile, MN-major
-            constexpr uint32_t id2 = idesc_bf16(128, 64, 0, 1);
-            constexpr uint64_t kT = kTileBytes >> 4;
-            bool ok = true;
-            int g = 0, it = 0;
-            for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
-                const TcItem ii = map.item(item);
-                for (int pt = ii.pt0; pt < ii.pt1; ++pt, ++g) {
-                    const int s = g % kStages, mb = g % kMBufs;
-                    const bool first = pt == ii.pt0;
-                    if (!(ok = mbar_wait(&m_full[mb], (g / kMBufs) & 1, abort))) break;
-                    if (!(ok = mbar_wait(&full[s], (g / kStages) & 1, abort))) break;
-                    if (first && it >= 1 && !(ok = mbar_wait(d_empty, (it - 1) & 1, abort))) break;
-                    tc_fence_after();
-                    const uint32_t tY = tmem + kColY;
-                    const uint32_t tM = tmem + kColM + mb * 64;
-                    const uint64_t pb = dP2 + (uint64_t)s * kT;
+        const uint64_t dP2 = desc_sw128(smem_u32(Pst), kTileBytes, 1024);  // pixel tile, MN-major
+        constexpr uint32_t id2 = idesc_bf16(128, 64, 0, 1);
+        constexpr uint64_t kT = kTileBytes >> 4;
+        bool ok = true;
+        int g = 0, it = 0;
+        for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
+            const TcItem ii = map.item(item);
+            for (int pt = ii.pt0; pt < ii.pt1; ++pt, ++g) {
+                const int s = g % kStages, mb = g % kMBufs;
+                const bool first = pt == ii.pt0;
+                if (!(ok = warp_wait(&m_full[mb], (g / kMBufs) & 1, abort))) break;
+                if (!(ok = warp_wait(&full[s], (g / kStages) & 1, abort))) break;
+                if (first && it >= 1 && !(ok = warp_wait(d_empty, (it - 1) & 1, abort))) break;
+                tc_fence_after();
+                const uint32_t tY = tmem + kColY;
+                const uint32_t tM = tmem + kColM + mb * 64;
+                const uint64_t pb = dP2 + (uint64_t)s * kT;
 #pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        mma_bf16_ts(tY, tM + 8 * k, pb + k * 128, id2, (first && k == 0) ? 0u : 1u);
-                    mma_commit(&m_empty[mb]);
-                    mma_commit(&empty[s]);
-                    if (pt == ii.pt1 - 1) mma_commit(d_full);
-                }
-            }
-            if (*abort) {
-                mma_commit(&aux[1]);
-                drain_wait(&aux[1], 0);
+                for (int k = 0; k < 8; ++k)
+                    mma_bf16_ts_warp(tY, tM + 8 * k, pb + k * 128, id2, (first && k == 0) ? 0u : 1u);
+                mma_commit_warp(&m_empty[mb]);
+                mma_commit_warp(&empty[s]);
+                if (pt == ii.pt1 - 1) mma_commit_warp(d_full);
             }
         }
+        if (__any_sync(0xffffffffu, *abort)) {
+            mma_commit_warp(&aux[1]);
+            drain_wait(&aux[1], 0);
+        }
     } else {
-        // ------------------------------------------------ mask warps (3..18)
+        // ------------------------------------------------ mask warps
         const int q = warp & 3;                   // TMEM lane quadrant (a warp reaches lanes 32 * (warp % 4) + 0..31)
-        const int h = (warp - kMaskWarp0) >> 2;   // which 32 pixels of a tile
+        const int h = warp >> 2;                  // which kPxPerWarp pixels of a tile
         const int r = q * 32 + lane;              // seed row
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         long long band_local = 0;
@@ -380,19 +388,24 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                 const int b = g & 1;
                 if (!(ok = warp_wait(&s_full[b], (g >> 1) & 1, abort))) break;
                 tc_fence_after();
-                uint32_t v[32];
-                tmem_ld32(tmem + kColS + b * 128 + lane_base + h * 32, v);
+                uint32_t v[kSub][32];
+#pragma unroll
+                for (int j = 0; j < kSub; ++j)
+                    tmem_ld32(tmem + kColS + b * 128 + lane_base + h * kPxPerWarp + j * 32, v[j]);
                 tmem_ld_wait();
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&s_empty[b]);
-                uint32_t w[16];
+                uint32_t w[kSub][16];
                 float mn = INFINITY;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    w[i] = ~sign_halves(v[2 * i], v[2 * i + 1]) & 0x3F803F80u;
-                    mn = fminf(mn, fminf(fabsf(__uint_as_float(v[2 * i])), fabsf(__uint_as_float(v[2 * i + 1]))));
-                }
+                for (int j = 0; j < kSub; ++j)
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        w[j][i] = ~sign_halves(v[j][2 * i], v[j][2 * i + 1]) & 0x3F803F80u;
+                        mn = fminf(mn, fminf(fabsf(__uint_as_float(v[j][2 * i])),
+                                             fabsf(__uint_as_float(v[j][2 * i + 1]))));
+                    }
                 if (__any_sync(0xffffffffu, mn < kBand)) {
                     // Re-decide near-boundary pairs with the FP32 form's dot
                     // product against the exact FP32 pixel rebuilt from the
@@ -401,39 +414,47 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                     const int s = g % kStages;
                     if (!(ok = warp_wait(&full[s], (g / kStages) & 1, abort))) break;
                     const uint8_t* stage = Pst + s * kTileBytes;
-                    uint32_t bandm = 0;
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) bandm |= (uint32_t)(fabsf(__uint_as_float(v[i])) < kBand) << i;
-                    uint32_t inm = 0, todo = bandm;
-                    while (todo) {
-                        const int i = __ffs(todo) - 1;
-                        todo &= todo - 1;
-                        const int row = h * 32 + i;
-                        if (pt * 128 + row < ii.n) {
-                            ++band_local;
-                            float pv[16];
-                            stage_pixel(stage, row, pv);
-                            if (dot_seq<16>(x, pv) >= c_f) inm |= 1u << i;
+                    for (int j = 0; j < kSub; ++j) {
+                        uint32_t bandm = 0;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) bandm |= (uint32_t)(fabsf(__uint_as_float(v[j][i])) < kBand) << i;
+                        uint32_t inm = 0, todo = bandm;
+                        while (todo) {
+                            const int i = __ffs(todo) - 1;
+                            todo &= todo - 1;
+                            const int row = h * kPxPerWarp + j * 32 + i;
+                            if (pt * 128 + row < ii.n) {
+                                ++band_local;
+                                float pv[16];
+                                stage_pixel(stage, row, pv);
+                                if (dot_seq<16>(x, pv) >= c_f) inm |= 1u << i;
+                            }
                         }
-                    }
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const uint32_t bm = (bandm >> (2 * j)) & 3u;
-                        const uint32_t im = (inm >> (2 * j)) & 3u;
-                        const uint32_t clear = ((bm & 1u) ? 0x3F80u : 0u) | ((bm & 2u) ? 0x3F800000u : 0u);
-                        const uint32_t set = ((im & 1u) ? 0x3F80u : 0u) | ((im & 2u) ? 0x3F800000u : 0u);
-                        w[j] = (w[j] & ~clear) | set;
+                        for (int k = 0; k < 16; ++k) {
+                            const uint32_t bm = (bandm >> (2 * k)) & 3u;
+                            const uint32_t im = (inm >> (2 * k)) & 3u;
+                            const uint32_t clear = ((bm & 1u) ? 0x3F80u : 0u) | ((bm & 2u) ? 0x3F800000u : 0u);
+                            const uint32_t set = ((im & 1u) ? 0x3F80u : 0u) | ((im & 2u) ? 0x3F800000u : 0u);
+                            w[j][k] = (w[j][k] & ~clear) | set;
+                        }
                     }
                 }
                 if (kDebug) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        dbg_S[(int64_t)r * dbg_stride + pt * 128 + h * 32 + i] = __uint_as_float(v[i]);
+                    for (int j = 0; j < kSub; ++j)
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            dbg_S[(int64_t)r * dbg_stride + pt * 128 + h * kPxPerWarp + j * 32 + i] =
+                                __uint_as_float(v[j][i]);
                 }
                 const int mb = g % kMBufs;
                 if (g >= kMBufs && !(ok = warp_wait(&m_empty[mb], ((g / kMBufs) - 1) & 1, abort))) break;
                 tc_fence_after();
-                tmem_st16(tmem + kColM + mb * 64 + lane_base + h * 16, w);
+#pragma unroll
+                for (int j = 0; j < kSub; ++j)
+                    tmem_st16(tmem + kColM + mb * 64 + lane_base + h * (kPxPerWarp / 2) + j * 16, w[j]);
                 tmem_st_wait();
                 tc_fence_before();
                 __syncwarp();
@@ -469,7 +490,7 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+    if (warp == kWarpG1) tmem_dealloc(tmem, kTmemCols);
     if (threadIdx.x == 0 && *abort) atomicOr(status, 2);
 }
 

@@ -399,7 +399,7 @@ k_b_seed(const BFrame* __restrict__ frames, BState* states, const float* __restr
 // is shared out in proportion to each frame's seed-by-pixel work (exact
 // integer totals, so the split is deterministic).
 __global__ void k_b_plan(const BFrame* __restrict__ frames, const BState* __restrict__ states, int B, BPlan plan,
-                         int target, int canon_target, int tc) {
+                         int target, int canon_target, int tc, int grid) {
     __shared__ unsigned long long s_work;
     __shared__ int s_carry_items, s_carry_seeds;
     if (threadIdx.x == 0) {
@@ -427,10 +427,10 @@ __global__ void k_b_plan(const BFrame* __restrict__ frames, const BState* __rest
                 tf = tf < 1 ? 1 : tf;
             }
             if (tc) {
+                // the canonical split fits the items to the grid exactly as a
+                // single-frame launch on that grid does
                 const int tiles = (na + 127) / 128;
-                int ch = (tf + tiles - 1) / tiles;
-                ch = ch < 1 ? 1 : (ch > fr.n_ptiles ? fr.n_ptiles : ch);
-                const int tpc = (fr.n_ptiles + ch - 1) / ch;
+                const int tpc = tc_tiles_per_chunk(tiles, fr.n_ptiles, tf, canon_target > 0 ? grid : 0);
                 plan.tpc[f] = tpc;
                 plan.chunks[f] = (fr.n_ptiles + tpc - 1) / tpc;
                 items = tiles * plan.chunks[f];
@@ -1008,7 +1008,7 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     // target_mult x grid items across the iterating frames by their work.
     const int grid_shift = b->tc ? b->tc_grid : b->f32_grid;
     k_b_plan<<<1, kIT, 0, s>>>(b->frames, b->states, B, b->plan, b->target_mult * grid_shift,
-                               b->split ? 0 : 2 * grid_shift, b->tc ? 1 : 0);
+                               b->split ? 0 : 2 * grid_shift, b->tc ? 1 : 0, grid_shift);
     LAUNCHED("k_b_plan");
     if (b->prof) {
         k_b_tick<<<1, 1, 0, s>>>(b->misc, b->plan.item_off + B, 0);

@@ -70,4 +70,39 @@ __device__ __forceinline__ int locate(const int32_t* off, int nf, int i) {
     return lo;
 }
 
+// Pixel tiles per chunk when a frame's seed tiles (128 seeds each) are cut
+// into tiles x chunks work items for the tensor-core shift. The plain rule
+// spreads `target` items over the seed tiles. With grid > 0 the items are
+// also fitted to the launch's CTAs, which each take items in turn: among the
+// chunk counts that fill 2..8 whole waves of the grid (at least two items per
+// CTA, so one item's pipeline fill overlaps the previous item's drain) and the
+// plain rule's,
+// the one with the smallest makespan waves x (tiles per item + 2 tiles of
+// per-item overhead) wins (ties: the earlier candidate). Integer arithmetic
+// only, so every caller with the same arguments cuts a frame the same way.
+__host__ __device__ inline int tc_tiles_per_chunk(int tiles, int n_ptiles, int target, int grid) {
+    if (tiles <= 0 || n_ptiles <= 0) return 1;
+    int ch = (target + tiles - 1) / tiles;
+    ch = ch < 1 ? 1 : (ch > n_ptiles ? n_ptiles : ch);
+    int best = (n_ptiles + ch - 1) / ch;
+    if (grid <= 0) return best;
+    auto cost = [&](int tpc) {
+        const long long items = (long long)tiles * ((n_ptiles + tpc - 1) / tpc);
+        return ((items + grid - 1) / grid) * (long long)(tpc + 2);
+    };
+    long long best_cost = cost(best);
+    for (int w = 2; w <= 8; ++w) {
+        int c = (int)((long long)w * grid / tiles);
+        if (c < 1) continue;
+        c = c > n_ptiles ? n_ptiles : c;
+        const int tpc = (n_ptiles + c - 1) / c;
+        const long long k = cost(tpc);
+        if (k < best_cost) {
+            best_cost = k;
+            best = tpc;
+        }
+    }
+    return best;
+}
+
 }  // namespace ms

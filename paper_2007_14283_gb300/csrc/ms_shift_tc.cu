@@ -73,7 +73,7 @@ struct TcSplit {
     int tiles, chunks, tpc;  // seed tiles, pixel chunks, pixel tiles per chunk
 };
 
-__device__ __forceinline__ TcSplit tc_split(int n_active, int n_ptiles, int target) {
+__device__ __forceinline__ TcSplit tc_split(int n_active, int n_ptiles, int target, int grid) {
     TcSplit s;
     s.tiles = (n_active + 127) / 128;
     if (s.tiles == 0 || n_ptiles == 0) {
@@ -81,9 +81,7 @@ __device__ __forceinline__ TcSplit tc_split(int n_active, int n_ptiles, int targ
         s.tpc = 1;
         return s;
     }
-    int ch = (target + s.tiles - 1) / s.tiles;
-    ch = ch < 1 ? 1 : (ch > n_ptiles ? n_ptiles : ch);
-    s.tpc = (n_ptiles + ch - 1) / ch;
+    s.tpc = tc_tiles_per_chunk(s.tiles, n_ptiles, target, grid);
     s.chunks = (n_ptiles + s.tpc - 1) / s.tpc;
     return s;
 }
@@ -155,7 +153,7 @@ struct TcSingleMap {
     __device__ __forceinline__ bool init() {
         if (dc->done) return false;
         n_active = dc->n_active;
-        sp = tc_split(n_active, n_ptiles, target);
+        sp = tc_split(n_active, n_ptiles, target, (int)gridDim.x);
         return true;
     }
     __device__ __forceinline__ int total() const { return sp.tiles * sp.chunks; }

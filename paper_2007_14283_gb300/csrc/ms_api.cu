@@ -122,7 +122,7 @@ ms_status validate(const ms_config* c) {
 constexpr size_t kAlign = 256;
 
 struct Layout {
-    size_t off[24];
+    size_t off[26];
     size_t total;
 
 };
@@ -156,9 +156,11 @@ Layout plan(int64_t np, int Dp, int target_items, bool bf16) {
         ((n + 1023) / 1024 + 1) * sizeof(int32_t),  // 20 block_tmp
         sizeof(DevCounters),              // 21 dc
         bf16 ? (n + 127) / 128 * 128 * 128 : 0,  // 22 Pk
+        bf16 ? (n + 127) / 128 * 128 * 128 : 0,  // 23 Mk
+        bf16 ? n * sizeof(int2) + 16 : 0,         // 24 label_fix + count
     };
     size_t t = 0;
-    for (int i = 0; i < 23; ++i) {
+    for (int i = 0; i < 25; ++i) {
         L.off[i] = t;
         t += align_up(sizes[i]);
     }
@@ -289,6 +291,8 @@ ms_status ms_create(const ms_config* cfg, const float* d_emb, const uint8_t* d_m
     ctx->block_tmp = (int32_t*)(b + L.off[20]);
     ctx->dc = (DevCounters*)(b + L.off[21]);
     ctx->Pk = cfg->precision == MS_BF16 ? (void*)(b + L.off[22]) : nullptr;
+    ctx->Mk = cfg->precision == MS_BF16 ? (void*)(b + L.off[23]) : nullptr;
+    ctx->label_fix = cfg->precision == MS_BF16 ? (int2*)(b + L.off[24]) : nullptr;
     ctx->round_log_cap = 64;
     ctx->round_log = new (std::nothrow) int64_t[ctx->round_log_cap * 4];
     if (!ctx->round_log) {

@@ -60,8 +60,11 @@ struct ms_batch {
     int32_t* conf;
     int32_t* block_tmp;       // [B, nblk_max]
     void* Pk;
+    void* Mk;                 // kept modes as BF16 split rows at the frames' Pk offsets (labelling)
     int32_t** label_ptrs;     // device array of B label buffers
     CUtensorMap pmap;
+    CUtensorMap mmap;
+    ms::LabelTcScratch lsc;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     int64_t body_launches;    // kernels per pass of the loop body
@@ -261,25 +264,7 @@ __global__ void k_b_pack(const BFrame* __restrict__ frames, const float* __restr
     const BFrame& fr = frames[blockIdx.y];
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= fr.n_ptiles * 128) return;
-    uint32_t w[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) w[k] = 0u;
-    if (r < fr.n) {
-        const float* p = P32 + (fr.pix0 + r) * 16;
-#pragma unroll
-        for (int k = 0; k < 16; k += 2) {
-            const float h0 = bf16_round(p[k]), h1 = bf16_round(p[k + 1]);
-            const float m0 = bf16_round(p[k] - h0), m1 = bf16_round(p[k + 1] - h1);
-            w[k / 2] = pack_bf16(h0, h1);
-            w[8 + k / 2] = pack_bf16(m0, m1);
-            w[16 + k / 2] = pack_bf16((p[k] - h0) - m0, (p[k + 1] - h1) - m1);
-        }
-    }
-    w[24] = pack_bf16(1.f, 1.f);
-    w[25] = pack_bf16(1.f, 0.f);
-    uint4* row = Pk + (int64_t)(fr.pk_row0 + r) * 8;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) row[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+    tc::pack_split_row(r < fr.n ? P32 + (fr.pix0 + r) * 16 : nullptr, Pk + (int64_t)(fr.pk_row0 + r) * 8);
 }
 
 __global__ void k_b_labels_clear(const BFrame* __restrict__ frames, int32_t* const* __restrict__ labels) {
@@ -1110,6 +1095,10 @@ ms_status enqueue_setup(ms_batch* b, cudaStream_t s) {
 
 template <int Dp>
 ms_status enqueue_label(ms_batch* b, cudaStream_t s) {
+    if (b->tc)  // BF16 form (d <= 16): the tensor-core kernel, same labels (exact FP64 argmax)
+        return launch_label_tc_batch(b->pmap, b->mmap, b->Mk, b->frames, b->states, b->B, (int)b->max_pk_rows,
+                                     b->modes, b->P32, b->pix, b->d, b->label_ptrs, b->lsc, b->tc_grid, b->misc + 1,
+                                     s);
     k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, b->B, kSelAllPixels, kPT, 0, b->blk_off);
     MS_LAUNCH("k_b_blocks");
     k_b_label<Dp><<<b->grid, kPT, 0, s>>>(b->frames, b->states, b->B, b->blk_off, b->d, b->P32, b->pix, b->modes,
@@ -1161,7 +1150,7 @@ ms_status build_graph(ms_batch* b) {
     if (st2 != MS_OK) return st2;
     MS_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
     b->body_launches = nl;
-    b->fixed_launches = (b->tc ? 5 : 4) + 2;
+    b->fixed_launches = b->tc ? 5 + 4 : 4 + 2;  // set-up, then labelling
     return MS_OK;
 }
 
@@ -1264,7 +1253,8 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
         sizeof(BFrame) * B, sizeof(BState) * B, sizeof(int32_t) * ((B + 1) * 4 + (B + 2) * 2), 64,
         n * Dp * 4, n * 4, n, n * Dp * 4, n * 4, n * 4, n, n * 4, n * 4, n * 4,
         n * (Dp + 1) * 8, n * Dp * 4, n * 4, n * 4, n * 4, n, n * 4, n * kMergeCap * 4,
-        (size_t)B * b->nblk_max * 4 + 4, b->tc ? (size_t)b->total_pk_rows * 128 : 0, sizeof(int32_t*) * B};
+        (size_t)B * b->nblk_max * 4 + 4, b->tc ? (size_t)b->total_pk_rows * 128 : 0, sizeof(int32_t*) * B,
+        b->tc ? (size_t)b->total_pk_rows * 128 : 0, b->tc ? n * sizeof(int2) : 0, sizeof(int32_t) * (B + 1) + 16};
     const int NS = (int)(sizeof(sizes) / sizeof(sizes[0]));
     size_t offs[32], tot = 0;
     for (int i = 0; i < NS; ++i) {
@@ -1309,6 +1299,10 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
     b->block_tmp = (int32_t*)(w + offs[22]);
     b->Pk = b->tc ? (void*)(w + offs[23]) : nullptr;
     b->label_ptrs = (int32_t**)(w + offs[24]);
+    b->Mk = b->tc ? (void*)(w + offs[25]) : nullptr;
+    b->lsc.fix = b->tc ? (int2*)(w + offs[26]) : nullptr;
+    b->lsc.off = (int32_t*)(w + offs[27]);
+    b->lsc.fix_count = b->lsc.off + (B + 1);
     ms_status s = cuda_check(cudaMallocHost((void**)&b->h_states, sizeof(BState) * B), "cudaMallocHost");
     if (s == MS_OK) s = cuda_check(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "cudaStreamCreate");
     if (s == MS_OK)
@@ -1321,6 +1315,8 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
     if (s == MS_OK) s = cuda_check(cudaStreamSynchronize(b->stream), "sync");
     if (s == MS_OK && b->tc) s = tc_batch_setup();
     if (s == MS_OK && b->tc) s = encode_pk_map(b->Pk, (int)b->total_pk_rows, &b->pmap);
+    if (s == MS_OK && b->tc) s = encode_pk_map(b->Mk, (int)b->total_pk_rows, &b->mmap);
+    if (s == MS_OK && b->tc) s = label_tc_setup();
     if (s == MS_OK) s = rebuild_graph(b);
     if (s != MS_OK) {
         free_batch(b);

@@ -70,6 +70,24 @@ __device__ __forceinline__ int locate(const int32_t* off, int nf, int i) {
     return lo;
 }
 
+// Scratch of the tensor-core labelling: the near-tie queue (capacity: the
+// foreground pixels) and, in batch form, the per-frame item offsets (B + 1).
+struct LabelTcScratch {
+    int2* fix;
+    int* fix_count;
+    int32_t* off;
+};
+
+int label_tc_smem_bytes();
+ms_status label_tc_setup();
+ms_status launch_label_tc_single(const CUtensorMap& pmap, void* Mk, int64_t n_pad, const float* modes, int K, int n,
+                                 const float* P32, const int32_t* pix, const float* emb, int d, int32_t* labels,
+                                 LabelTcScratch sc, int grid, int* status, cudaStream_t st);
+ms_status launch_label_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, void* Mk, const BFrame* frames,
+                                const BState* states, int B, int max_pk_rows, const float* modes, const float* P32,
+                                const int32_t* pix, int d, int32_t* const* labels, LabelTcScratch sc, int grid,
+                                int* status, cudaStream_t st);
+
 // Pixel tiles per chunk when a frame's seed tiles (128 seeds each) are cut
 // into tiles x chunks work items for the tensor-core shift. The plain rule
 // spreads `target` items over the seed tiles. With grid > 0 the items are

@@ -136,6 +136,8 @@ struct ms_ctx {
     int64_t n_pad;       // n rounded up to 128 (0 when n = 0)
     CUtensorMap pmap;    // TMA map of Pk: boxes of 128 rows x 128 bytes, 128-byte swizzle
     int tc_grid;         // persistent grid of the tensor-core shift kernel
+    void* Mk;            // [n_pad, 64] bf16 split rows of the kept modes (labelling)
+    int2* label_fix;     // [n] near-tie queue of the tensor-core labelling, then its count
     // measurement
     bool prof;
     cudaEvent_t ev[64];  // start/end pairs around shift launches of one batch

@@ -6,6 +6,7 @@
 // the winner is re-decided in FP64 among the modes whose FP32 score is within
 // 2*kEpsF32 of the best, from the raw embedding: the FP64 argmax always lies in
 // that set, so the label is the exact FP64 argmax over the modes.
+#include "ms_batch.cuh"
 #include "ms_device.cuh"
 
 namespace ms {
@@ -72,6 +73,15 @@ k_label(const float* __restrict__ P32, const float* __restrict__ emb, int d,
 ms_status launch_label(ms_ctx* ctx, int32_t* d_labels) {
     MS_CUDA(cudaMemsetAsync(d_labels, 0xff, sizeof(int32_t) * (size_t)ctx->n_pixels, ctx->stream));
     if (ctx->n == 0) return MS_OK;
+    if (ctx->Mk) {
+        // BF16 form: the tensor-core kernel, same labels (exact FP64 argmax)
+        LabelTcScratch sc{ctx->label_fix, (int*)(ctx->label_fix + ctx->n), nullptr};
+        const ms_status s = launch_label_tc_single(ctx->pmap, ctx->Mk, ctx->n_pad, ctx->modes, ctx->n_kept,
+                                                   (int)ctx->n, ctx->P32, ctx->pix, ctx->emb, ctx->d, d_labels, sc,
+                                                   ctx->tc_grid, &ctx->dc->status, ctx->stream);
+        ctx->launches += ctx->n_kept > 1 ? 3 : 2;
+        return s;
+    }
     const unsigned g = (unsigned)((ctx->n + kLT - 1) / kLT);
     if (ctx->Dp == 16)
         k_label<16><<<g, kLT, 0, ctx->stream>>>(ctx->P32, ctx->emb, ctx->d, ctx->pix, (int)ctx->n,

@@ -1,0 +1,466 @@
+// Labelling, BF16 tensor-core form (Algorithm 2, lines 10-12): every
+// foreground vector takes the mode of highest cosine, lowest index on ties.
+//
+// The pixel-by-mode score matrix is a GEMM with K = d = 16. A work item is one
+// tile of 128 pixels (the GEMM's M rows) against every 128-mode tile of its
+// frame (N columns); the scores live only in TMEM:
+//     S = Ph.Mh + Ph.Mm + Pm.Mh          (3 tcgen05 MMAs, FP32 accumulate)
+// with p = Ph + Pm + Pl and m = Mh + Mm + Ml the exact BF16 splits of the FP32
+// vectors. The dropped terms are at most 3 * 2^-18 for unit vectors and the
+// tensor cores' FP32 accumulation of 48 exact products adds at most 48 * 2^-23,
+// so |S - p.m| <= kEpsTc. Sixteen warps read S from TMEM, one pixel per lane
+// and 32 mode columns per warp, and keep the best and second-best score of
+// each pixel. A pixel whose best leads its second by more than 2 * kEpsTc has
+// the exact FP64 argmax as its winner; the others (near-ties) are queued and
+// re-decided by k_label_fix exactly as the FP32 form decides them: FP32 scores
+// over all modes, then FP64 among those within 2 * kEpsF32 of the best.
+//
+// Warp roles (576 threads, one CTA per SM): warps 0-15 read S (warp w reaches
+// TMEM lanes 32 * (w % 4) + 0..31); warp 16 issues TMA loads (the item's pixel
+// tile, double-buffered, and mode tiles into an 8-stage ring); warp 17 owns the
+// 512 TMEM columns (four S buffers of 128) and issues the MMAs from a converged
+// warp, one elected lane issuing. Waits are bounded as in the shift kernel.
+#include <cudaTypedefs.h>
+
+#include "ms_batch.cuh"
+#include "ms_device.cuh"
+#include "ms_tc.cuh"
+
+namespace ms {
+namespace {
+
+using namespace tc;
+
+constexpr int kLEpi = 16;                   // score-reading warps
+constexpr int kLWarpTma = kLEpi;
+constexpr int kLWarpMma = kLEpi + 1;
+constexpr int kLThreads = (kLEpi + 2) * 32;  // 576
+constexpr int kLStages = 8;                 // mode-tile ring
+constexpr int kLSBufs = 4;                  // S buffers, 128 TMEM columns each
+constexpr int kLTile = 128 * 128;           // bytes of a 128-row operand tile
+constexpr uint32_t kLTmemCols = 512;
+constexpr float kEpsTc = 2.5e-5f;
+
+constexpr int kLOffA = 0;                                // 2 pixel tiles
+constexpr int kLOffB = 2 * kLTile;                       // kLStages mode tiles
+constexpr int kLOffX = kLOffB + kLStages * kLTile;       // exchange: [4][128] x (b1, i1, b2)
+constexpr int kLOffBar = kLOffX + 4 * 128 * 12;
+constexpr int kLNumBars = 2 * 2 + 2 * kLStages + 2 * kLSBufs + 2;
+constexpr int kLSmemBytes = kLOffBar + kLNumBars * 8 + 16 + 1024;
+static_assert(kLSmemBytes <= 227 * 1024, "shared memory budget");
+
+// What an item covers.
+struct LbItem {
+    int frame;
+    int pk_row0;   // Pk / Mk row of the frame's pixel 0 and mode 0 (multiple of 128)
+    int pt;        // pixel tile
+    int n;         // the frame's foreground count
+    int K;         // the frame's kept modes
+};
+
+struct LbSingle {
+    int n, K;
+    __device__ __forceinline__ bool init() { return n > 0; }
+    __device__ __forceinline__ int total() const { return (n + 127) / 128; }
+    __device__ __forceinline__ LbItem item(int i) const { return LbItem{0, 0, i, n, K}; }
+};
+
+struct LbBatch {
+    const BFrame* frames;
+    const BState* states;
+    const int32_t* off;   // pixel-tile offsets over frames (B + 1)
+    int B;
+    int total_;
+    __device__ __forceinline__ bool init() {
+        total_ = off[B];
+        return total_ > 0;
+    }
+    __device__ __forceinline__ int total() const { return total_; }
+    __device__ __forceinline__ LbItem item(int i) const {
+        const int f = locate(off, B, i);
+        const BFrame& fr = frames[f];
+        return LbItem{f, fr.pk_row0, i - off[f], fr.n, states[f].dc.n_kept};
+    }
+};
+
+__device__ __forceinline__ bool lwarp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort));
+}
+
+__device__ __forceinline__ void ldrain(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return;
+}
+
+// Output of one pixel: where its label goes and, for a near-tie, the queue.
+// Batch form: per-frame label pointers and pixel offsets from the frames;
+// single form: labels1 and offset 0.
+struct LbOut {
+    int32_t* const* labels;    // per frame, or nullptr
+    int32_t* labels1;
+    const BFrame* frames;      // pixel offsets (pix0), or nullptr
+    const int32_t* pix;        // foreground index -> pixel index, all frames
+    int2* fix;                 // near-ties (frame, foreground index)
+    int* fix_count;
+};
+
+template <class Map>
+__global__ void __launch_bounds__(kLThreads, 1)
+k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap mmap, Map map, LbOut out,
+           int* status) {
+    if (!map.init()) return;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* Ab = smem + kLOffA;
+    uint8_t* Bst = smem + kLOffB;
+    float* xb1 = (float*)(smem + kLOffX);          // [4][128]
+    int* xi1 = (int*)(xb1 + 4 * 128);              // [4][128]
+    float* xb2 = (float*)(xi1 + 4 * 128);          // [4][128]
+    uint64_t* bars = (uint64_t*)(smem + kLOffBar);
+    uint64_t* a_full = bars;                       // [2]
+    uint64_t* a_empty = a_full + 2;                // [2]
+    uint64_t* b_full = a_empty + 2;                // [kLStages]
+    uint64_t* b_empty = b_full + kLStages;         // [kLStages]
+    uint64_t* s_full = b_empty + kLStages;         // [kLSBufs]
+    uint64_t* s_empty = s_full + kLSBufs;          // [kLSBufs]
+    uint64_t* aux = s_empty + kLSBufs;             // [2] drain
+    uint32_t* tmem_slot = (uint32_t*)(bars + kLNumBars);
+    volatile int* abort = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&a_full[i], 1);
+            mbar_init(&a_empty[i], 1);
+        }
+        for (int s = 0; s < kLStages; ++s) {
+            mbar_init(&b_full[s], 1);
+            mbar_init(&b_empty[s], 1);
+        }
+        for (int b = 0; b < kLSBufs; ++b) {
+            mbar_init(&s_full[b], 1);
+            mbar_init(&s_empty[b], kLEpi);
+        }
+        mbar_init(&aux[0], 1);
+        mbar_init(&aux[1], 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == kLWarpTma && lane == 0) {
+        tma_prefetch_desc(&pmap);
+        tma_prefetch_desc(&mmap);
+    }
+    if (warp == kLWarpMma) {
+        tmem_alloc(tmem_slot, kLTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int items = map.total();
+
+    if (warp == kLWarpTma) {
+        // ------------------------------------------------ TMA producer
+        int g = 0, ia = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+            const LbItem ii = map.item(item);
+            const int nmt = (ii.K + 127) / 128;
+            if (nmt == 0) continue;
+            const int ab = ia & 1;
+            if (ia >= 2 && !(ok = lwarp_wait(&a_empty[ab], ((ia >> 1) - 1) & 1, abort))) break;
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&a_full[ab], kLTile);
+                tma_load_2d(Ab + ab * kLTile, &pmap, 0, ii.pk_row0 + ii.pt * 128, &a_full[ab]);
+            }
+            __syncwarp();
+            ++ia;
+            for (int mt = 0; mt < nmt; ++mt, ++g) {
+                const int s = g % kLStages;
+                if (g >= kLStages && !(ok = lwarp_wait(&b_empty[s], ((g / kLStages) - 1) & 1, abort))) break;
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(&b_full[s], kLTile);
+                    tma_load_2d(Bst + s * kLTile, &mmap, 0, ii.pk_row0 + mt * 128, &b_full[s]);
+                }
+                __syncwarp();
+            }
+        }
+        if (lane == 0 && *abort) {
+            for (int q = max(0, g - kLStages); q < g; ++q) ldrain(&b_full[q % kLStages], (q / kLStages) & 1);
+            for (int q = max(0, ia - 2); q < ia; ++q) ldrain(&a_full[q & 1], (q >> 1) & 1);
+        }
+    } else if (warp == kLWarpMma) {
+        // ------------------------------------------------ MMA issuer
+        const uint64_t dA = desc_sw128(smem_u32(Ab), 16, 1024);
+        const uint64_t dB = desc_sw128(smem_u32(Bst), 16, 1024);
+        constexpr uint32_t id = idesc_bf16(128, 128, 0, 0);
+        constexpr uint64_t kT = kLTile >> 4;
+        int g = 0, ia = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+            const LbItem ii = map.item(item);
+            const int nmt = (ii.K + 127) / 128;
+            if (nmt == 0) continue;
+            const int ab = ia & 1;
+            if (!(ok = lwarp_wait(&a_full[ab], (ia >> 1) & 1, abort))) break;
+            const uint64_t a = dA + (uint64_t)ab * kT;
+            for (int mt = 0; mt < nmt; ++mt, ++g) {
+                const int s = g % kLStages, b = g % kLSBufs;
+                if (!(ok = lwarp_wait(&b_full[s], (g / kLStages) & 1, abort))) break;
+                if (g >= kLSBufs && !(ok = lwarp_wait(&s_empty[b], ((g / kLSBufs) - 1) & 1, abort))) break;
+                tc_fence_after();
+                const uint32_t tS = tmem + b * 128;
+                const uint64_t bb = dB + (uint64_t)s * kT;
+                mma_bf16_warp(tS, a, bb, id, 0);          // Ph . Mh
+                mma_bf16_warp(tS, a, bb + 2, id, 1);      // Ph . Mm
+                mma_bf16_warp(tS, a + 2, bb, id, 1);      // Pm . Mh
+                mma_commit_warp(&s_full[b]);
+                mma_commit_warp(&b_empty[s]);
+            }
+            if (!ok) break;
+            mma_commit_warp(&a_empty[ab]);
+            ++ia;
+        }
+        if (__any_sync(0xffffffffu, *abort)) {
+            mma_commit_warp(&aux[0]);
+            ldrain(&aux[0], 0);
+        }
+    } else {
+        // ------------------------------------------------ score readers
+        const int q = warp & 3;                  // TMEM lane quadrant
+        const int h = warp >> 2;                 // which 32 columns of a mode tile
+        const int r = q * 32 + lane;             // pixel row of the tile
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        int g = 0;
+        for (int item = blockIdx.x; item < items; item += gridDim.x) {
+            const LbItem ii = map.item(item);
+            const int nmt = (ii.K + 127) / 128;
+            bool ok = true;
+            float b1 = -INFINITY, b2 = -INFINITY;
+            int i1 = -1;
+            for (int mt = 0; mt < nmt; ++mt, ++g) {
+                const int b = g % kLSBufs;
+                if (!(ok = lwarp_wait(&s_full[b], (g / kLSBufs) & 1, abort))) break;
+                tc_fence_after();
+                uint32_t v[32];
+                tmem_ld32(tmem + b * 128 + lane_base + h * 32, v);
+                tmem_ld_wait();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&s_empty[b]);
+                const int col0 = mt * 128 + h * 32;
+                if (col0 + 32 > ii.K) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (col0 + j >= ii.K) v[j] = 0xFF800000u;  // -inf: past the last mode
+                }
+                float m = __uint_as_float(v[0]);
+#pragma unroll
+                for (int j = 1; j < 32; ++j) m = fmaxf(m, __uint_as_float(v[j]));
+                // A column can change the best two only if it beats the
+                // second best; in increasing column order a tie keeps the
+                // lower index as the best.
+                if (__any_sync(0xffffffffu, m > b2)) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float sc = __uint_as_float(v[j]);
+                        if (sc > b1) {
+                            b2 = b1;
+                            b1 = sc;
+                            i1 = col0 + j;
+                        } else if (sc > b2) {
+                            b2 = sc;
+                        }
+                    }
+                }
+            }
+            // Merge the four column slices of each pixel. The 16 score warps
+            // meet at a named barrier that also ORs their failure flags, so
+            // after a timeout they leave together and none waits there alone.
+            xb1[h * 128 + r] = b1;
+            xi1[h * 128 + r] = i1;
+            xb2[h * 128 + r] = b2;
+            uint32_t any_bad;
+            asm volatile(
+                "{\n\t.reg .pred p, q;\n\t"
+                "setp.ne.u32 p, %1, 0;\n\t"
+                "bar.red.or.pred q, 1, %2, p;\n\t"
+                "selp.u32 %0, 1, 0, q;\n\t}"
+                : "=r"(any_bad)
+                : "r"(ok ? 0u : 1u), "n"(kLEpi * 32)
+                : "memory");
+            if (any_bad) break;
+            if (h == 0) {
+                float B1 = xb1[r], B2 = xb2[r];
+                int I1 = xi1[r];
+#pragma unroll
+                for (int k = 1; k < 4; ++k) {
+                    const float c1 = xb1[k * 128 + r], c2 = xb2[k * 128 + r];
+                    const int ci = xi1[k * 128 + r];
+                    if (c1 > B1 || (c1 == B1 && ci >= 0 && (I1 < 0 || ci < I1))) {
+                        B2 = fmaxf(B1, fmaxf(B2, c2));
+                        B1 = c1;
+                        I1 = ci;
+                    } else {
+                        B2 = fmaxf(B2, fmaxf(c1, c2));
+                    }
+                }
+                const int i = ii.pt * 128 + r;
+                if (i < ii.n) {
+                    const int64_t base = out.frames ? out.frames[ii.frame].pix0 : 0;
+                    int32_t* lab = out.labels ? out.labels[ii.frame] : out.labels1;
+                    lab[out.pix[base + i]] = I1;
+                    if (ii.K > 1 && !(B1 - B2 > 2.f * kEpsTc)) {
+                        const int slot = atomicAdd(out.fix_count, 1);
+                        out.fix[slot] = make_int2(ii.frame, i);
+                    }
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"n"(kLEpi * 32) : "memory");
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kLWarpMma) tmem_dealloc(tmem, kLTmemCols);
+    if (threadIdx.x == 0 && *abort) atomicOr(status, 2);
+}
+
+// Near-ties: one warp per queued pixel re-decides its label as the FP32 form
+// does. FP32 scores over all modes (lanes stride the modes), the best of
+// them, then the FP64 cosine of the raw embedding for every mode within
+// 2 * kEpsF32 of that best; the largest wins, the lowest index on ties.
+__global__ void k_label_fix(const int2* __restrict__ fix, const int* __restrict__ fix_count,
+                            const float* __restrict__ P32, const float* __restrict__ modes,
+                            const BFrame* __restrict__ frames, const BState* __restrict__ states,
+                            const int32_t* __restrict__ pix, const float* __restrict__ emb1, int K1, int d,
+                            int32_t* const* __restrict__ labels, int32_t* __restrict__ labels1) {
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int cnt = *fix_count;
+    for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < cnt; e += gridDim.x * wpb) {
+        const int2 fi = fix[e];
+        const int f = fi.x, i = fi.y;
+        const int64_t base = frames ? frames[f].pix0 : 0;
+        const int K = states ? states[f].dc.n_kept : K1;
+        const float* emb = frames ? frames[f].emb : emb1;
+        int32_t* lab = labels ? labels[f] : labels1;
+        const float* p = P32 + (base + i) * 16;
+        const float* M = modes + base * 16;
+        float pv[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) pv[k] = p[k];
+        float b1 = -INFINITY;
+        for (int j = lane; j < K; j += 32) b1 = fmaxf(b1, dot_seq<16>(pv, M + (int64_t)j * 16));
+        for (int o = 16; o > 0; o >>= 1) b1 = fmaxf(b1, __shfl_xor_sync(0xffffffffu, b1, o));
+        const float* em = emb + (int64_t)pix[base + i] * d;
+        double bc = -INFINITY;
+        int best = K;
+        for (int j = lane; j < K; j += 32) {
+            const float* m = M + (int64_t)j * 16;
+            if (dot_seq<16>(pv, m) < b1 - 2.f * kEpsF32) continue;
+            const double cs = cos64(em, m, d);
+            if (cs > bc) {
+                bc = cs;
+                best = j;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, bc, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, best, o);
+            if (ob > bc || (ob == bc && oi < best)) {
+                bc = ob;
+                best = oi;
+            }
+        }
+        if (lane == 0 && best < K) lab[pix[base + i]] = best;
+    }
+}
+
+// Modes as BF16 split rows at the frame's Pk row offsets (padding rows hold
+// the ones only; their columns are masked out by the score readers).
+__global__ void k_pack_modes_single(const float* __restrict__ modes, int K, int K_pad, uint4* __restrict__ Mk) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= K_pad) return;
+    pack_split_row(r < K ? modes + (int64_t)r * 16 : nullptr, Mk + (int64_t)r * 8);
+}
+
+__global__ void k_pack_modes_batch(const BFrame* __restrict__ frames, const BState* __restrict__ states,
+                                   const float* __restrict__ modes, uint4* __restrict__ Mk) {
+    const BFrame& fr = frames[blockIdx.y];
+    const int K = states[blockIdx.y].dc.n_kept;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (K + 127) / 128 * 128) return;
+    pack_split_row(r < K ? modes + (fr.pix0 + r) * 16 : nullptr, Mk + (int64_t)(fr.pk_row0 + r) * 8);
+}
+
+// Per-frame offsets of the label items (128-pixel tiles); clears the queue.
+__global__ void k_label_items(const BFrame* __restrict__ frames, int B, int32_t* __restrict__ off,
+                              int* __restrict__ fix_count) {
+    if (threadIdx.x != 0) return;
+    int t = 0;
+    for (int f = 0; f < B; ++f) {
+        off[f] = t;
+        t += (frames[f].n + 127) / 128;
+    }
+    off[B] = t;
+    *fix_count = 0;
+}
+
+}  // namespace
+
+int label_tc_smem_bytes() { return kLSmemBytes; }
+
+ms_status label_tc_setup() {
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbSingle>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLSmemBytes));
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLSmemBytes));
+    return MS_OK;
+}
+
+ms_status launch_label_tc_single(const CUtensorMap& pmap, void* Mk, int64_t n_pad, const float* modes, int K, int n,
+                                 const float* P32, const int32_t* pix, const float* emb, int d, int32_t* labels,
+                                 LabelTcScratch sc, int grid, int* status, cudaStream_t st) {
+    if (n == 0) return MS_OK;
+    MS_CUDA(cudaMemsetAsync(sc.fix_count, 0, sizeof(int), st));
+    if (K > 0) {
+        const int K_pad = (K + 127) / 128 * 128;
+        k_pack_modes_single<<<(K_pad + 255) / 256, 256, 0, st>>>(modes, K, K_pad, (uint4*)Mk);
+        MS_LAUNCH("k_pack_modes_single");
+    }
+    CUtensorMap mmap;
+    ms_status s = encode_pk_map(Mk, (int)n_pad, &mmap);
+    if (s != MS_OK) return s;
+    LbSingle map{n, K};
+    LbOut out{nullptr, labels, nullptr, pix, sc.fix, sc.fix_count};
+    k_label_tc<LbSingle><<<grid, kLThreads, kLSmemBytes, st>>>(pmap, mmap, map, out, status);
+    MS_LAUNCH("k_label_tc");
+    if (K > 1) {
+        k_label_fix<<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, P32, modes, nullptr, nullptr, pix, emb, K, d,
+                                          nullptr, labels);
+        MS_LAUNCH("k_label_fix");
+    }
+    return MS_OK;
+}
+
+ms_status launch_label_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, void* Mk, const BFrame* frames,
+                                const BState* states, int B, int max_pk_rows, const float* modes, const float* P32,
+                                const int32_t* pix, int d, int32_t* const* labels, LabelTcScratch sc, int grid,
+                                int* status, cudaStream_t st) {
+    const dim3 gp((unsigned)((max_pk_rows + 255) / 256), (unsigned)B);
+    k_pack_modes_batch<<<gp, 256, 0, st>>>(frames, states, modes, (uint4*)Mk);
+    MS_LAUNCH("k_pack_modes_batch");
+    k_label_items<<<1, 32, 0, st>>>(frames, B, sc.off, sc.fix_count);
+    MS_LAUNCH("k_label_items");
+    LbBatch map{frames, states, sc.off, B, 0};
+    LbOut out{labels, nullptr, frames, pix, sc.fix, sc.fix_count};
+    k_label_tc<LbBatch><<<grid, kLThreads, kLSmemBytes, st>>>(pmap, mmap, map, out, status);
+    MS_LAUNCH("k_label_tc(batch)");
+    k_label_fix<<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, P32, modes, frames, states, pix, nullptr, 0, d, labels,
+                                      nullptr);
+    MS_LAUNCH("k_label_fix(batch)");
+    return MS_OK;
+}
+
+}  // namespace ms

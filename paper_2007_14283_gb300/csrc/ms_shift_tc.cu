@@ -498,25 +498,7 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
 __global__ void k_pack_bf16(const float* __restrict__ P32, int n, int n_pad, uint4* __restrict__ Pk) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_pad) return;
-    uint32_t w[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) w[k] = 0u;
-    if (i < n) {
-#pragma unroll
-        for (int k = 0; k < 16; k += 2) {
-            const float p0 = P32[(int64_t)i * 16 + k], p1 = P32[(int64_t)i * 16 + k + 1];
-            const float h0 = bf16_round(p0), h1 = bf16_round(p1);
-            const float m0 = bf16_round(p0 - h0), m1 = bf16_round(p1 - h1);
-            w[k / 2] = pack_bf16(h0, h1);
-            w[8 + k / 2] = pack_bf16(m0, m1);
-            w[16 + k / 2] = pack_bf16((p0 - h0) - m0, (p1 - h1) - m1);
-        }
-    }
-    w[24] = pack_bf16(1.f, 1.f);
-    w[25] = pack_bf16(1.f, 0.f);
-    uint4* row = Pk + (int64_t)i * 8;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) row[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+    pack_split_row(i < n ? P32 + (int64_t)i * 16 : nullptr, Pk + (int64_t)i * 8);
 }
 
 ms_status encode_pmap(void* Pk, int n_pad, CUtensorMap* map) {
@@ -555,6 +537,7 @@ ms_status tc_prepare(ms_ctx* ctx) {
     MS_CUDA(cudaFuncSetAttribute(k_shift_tc<true, TcSingleMap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSmemBytes));
     ctx->tc_grid = ctx->num_sms;  // one CTA per SM: it owns all 512 TMEM columns
+    if (ms_status ls = label_tc_setup(); ls != MS_OK) return ls;
     return encode_pmap(ctx->Pk, (int)ctx->n_pad, &ctx->pmap);
 }
 

@@ -214,5 +214,30 @@ __device__ __forceinline__ float bf16_round(float x) {
     return __uint_as_float(r << 16);
 }
 
+// One 128-byte row of a BF16 split operand for a unit vector v (16 FP32
+// components, or nullptr for a padding row): [vh | vm | vl | 1 1 1 0..0], where
+// vh = RN(v), vm = RN(v - vh), vl = (v - vh) - vm, so v = vh + vm + vl exactly
+// (|v_k| >= 2^-100 or 0). The ones give a -c column against a split constant.
+__device__ __forceinline__ void pack_split_row(const float* v, uint4* row) {
+    uint32_t w[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) w[k] = 0u;
+    if (v) {
+#pragma unroll
+        for (int k = 0; k < 16; k += 2) {
+            const float p0 = v[k], p1 = v[k + 1];
+            const float h0 = bf16_round(p0), h1 = bf16_round(p1);
+            const float m0 = bf16_round(p0 - h0), m1 = bf16_round(p1 - h1);
+            w[k / 2] = pack_bf16(h0, h1);
+            w[8 + k / 2] = pack_bf16(m0, m1);
+            w[16 + k / 2] = pack_bf16((p0 - h0) - m0, (p1 - h1) - m1);
+        }
+    }
+    w[24] = pack_bf16(1.f, 1.f);
+    w[25] = pack_bf16(1.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) row[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+}
+
 }  // namespace tc
 }  // namespace ms

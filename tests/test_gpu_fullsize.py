@@ -17,7 +17,9 @@ near tol: they agree within 0.01% (seed-iterations), two seeds per round plus
 0.1% (candidates, dropped; their sum is exact) and one iteration per round. Sampled outputs are then
 checked one by one in FP64: labels are the FP64 argmax over the GPU's modes
 (pixels whose top-two margin exceeds 1e-5), every foreground pixel is covered
-(seeded or within c of a mode) and modes are fixed points of the FP64 update.
+(seeded or within c of a mode) and modes are fixed points of the FP64 update;
+then every pixel's label is checked against the FP64 argmax over the GPU's
+modes (top-two margin above 1e-12).
 
 C4 (64 frames of uneven size, 2k-260k foreground pixels, one graph): each
 frame of the batch equals a single-frame run of that frame bit for bit, and
@@ -101,6 +103,26 @@ def _sampled_checks(f, labels, modes, seed_pixels, c=0.9, n_samples=3000, seed=0
     assert errs.max() <= 1e-3 and (errs <= 1e-6).mean() >= 0.9, errs
 
 
+def _full_label_check(f, labels, modes, margin=1e-12):
+    """Every foreground pixel's label is the FP64 argmax of its cosine over the
+    GPU's modes (lowest index on ties), except where the top two lie within
+    `margin` (FP64 rounding decides those). Covers the labelling's near-tie
+    re-decision, which the sampled check rarely reaches."""
+    fg = np.flatnonzero(f.mask) if f.mask is not None else np.arange(f.emb.shape[0])
+    P = f.emb[fg].astype(np.float64)
+    P /= np.linalg.norm(P, axis=1, keepdims=True)
+    M = modes.astype(np.float64)
+    M /= np.linalg.norm(M, axis=1, keepdims=True)
+    lab = labels[fg]
+    for a in range(0, len(fg), 16384):
+        S = P[a:a + 16384] @ M.T
+        want = np.argmax(S, axis=1)
+        top = np.partition(S, -2, axis=1)[:, -2:] if S.shape[1] > 1 else np.concatenate([S, S - 1], axis=1)
+        clear = (top[:, 1] - top[:, 0]) > margin if S.shape[1] > 1 else np.ones(len(S), bool)
+        assert np.array_equal(want[clear], lab[a:a + 16384][clear]), a
+    assert np.all(labels[np.setdiff1d(np.arange(labels.size), fg)] == -1)
+
+
 def _label_agreement(a, b, modes_a, modes_b):
     """Share of foreground pixels with equal labels: index by index when both
     mode lists agree in order, else a greedy overlap matching (a lower bound of
@@ -132,6 +154,7 @@ def test_c2_full_frame_counters_equal_oracle(ms_lib, bf16):
     res = ms_lib.cluster(e, m, precision=prec)
     _counters_match_oracle(res.stats, ref)
     _sampled_checks(f, res.labels.cpu().numpy(), res.modes.cpu().numpy(), res.stats["seed_log"])
+    _full_label_check(f, res.labels.cpu().numpy(), res.modes.cpu().numpy())
 
 
 def test_c2_frames_batched_as_benchmarked(ms_lib):

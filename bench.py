@@ -410,9 +410,14 @@ def roofline_of(form, tot, step_ms, clk, n_sm):
 def vmf_leg(n_sm, clk):
     """Smooth-kernel form on the differentiable configuration: N = 65536 pixels,
     M = 1024 seeds, d = 16, kappa = 20, T = 10. Times ms_vmf_forward and
-    ms_vmf_backward (CUDA events, median of 5 after 2 warm-ups). Bound: one exp
-    per seed-pixel pair and step on the special-function units; the backward
-    re-runs the forward and evaluates each weight once more per step."""
+    ms_vmf_backward (CUDA events, median of 5 after 2 warm-ups).
+
+    Bound: FP32 FMA on the CUDA cores. Per seed-pixel pair and step the
+    forward does the 16-term dot product and the 16-term weighted sum (4d = 64
+    flops) and one exp; the adjoint re-runs the forward (64), then pass A's two
+    dot products and weighted sum (96) and pass B's two dot products and two
+    weighted sums (128): 288 flops and two exps. The exps (one special-function
+    result per pair, 16 per SM per clock) bind well below the FMAs."""
     import torch
 
     import paper_2007_14283_gb300 as ms
@@ -441,14 +446,16 @@ def vmf_leg(n_sm, clk):
     bwd = timed_ms(lambda: ms.ms_vmf_backward(P, X0, kappa, T, G))
     pairs = 65536 * 1024 * T
     sm_mhz = clk.get("sm_mhz") or 2070.0
-    mufu_peak = n_sm * 16 * sm_mhz * 1e6  # exp results per second: 16 per SM per clock
+    fma_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 TFLOP/s: 128 FMA lanes per SM
+    f_tf = 64 * pairs / (fwd * 1e-3) / 1e12
+    b_tf = 288 * pairs / (bwd * 1e-3) / 1e12
     return {"config": "N=65536 pixels, M=1024 seeds, d=16, kappa=20, T=10 (synthetic vMF cells)",
             "forward_ms": fwd, "backward_ms": bwd,
-            "forward_exp_per_s": pairs / (fwd * 1e-3), "backward_exp_per_s": 2 * pairs / (bwd * 1e-3),
-            "mufu_peak_exp_per_s": mufu_peak,
-            "forward_frac": pairs / (fwd * 1e-3) / mufu_peak,
-            "backward_frac": 2 * pairs / (bwd * 1e-3) / mufu_peak,
-            "peak_source": f"{n_sm} SMs x 16 exp/clock/SM x {sm_mhz:.0f} MHz (assumed SFU rate)"}
+            "bound": "fp32 fma", "unit": "TFLOP/s",
+            "forward_achieved": f_tf, "backward_achieved": b_tf, "peak": fma_peak,
+            "forward_frac": f_tf / fma_peak, "backward_frac": b_tf / fma_peak,
+            "algorithmic": "64 flops per seed-pixel pair and step (forward); 288 (adjoint, with the re-run forward)",
+            "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz (nominal CUDA-core rate)"}
 
 
 def e2e_leg(args, runner, ws):

@@ -18,31 +18,37 @@
 // The backward call re-runs the forward to rebuild x_0..x_T and |y_t| (a few
 // hundred KB) and recomputes every w_mi tile on the fly; no M x N matrix is
 // ever stored. Reductions go through per-chunk partial sums added in a fixed
-// order, so results are deterministic. d = 16.
+// order, so results are deterministic for a given GPU (the chunks fill one wave
+// of resident blocks). The weights are evaluated as 2^(kappa log2(e) (s - 1))
+// with exp2f. d = 16.
 #include "ms_internal.cuh"
 
 namespace ms {
 namespace {
 
-constexpr int kVT = 128;          // threads per block
-constexpr int kVSeeds = 256;      // seeds per work item (2 per thread)
 constexpr int kVPixTile = 128;    // pixels per shared-memory stage
 constexpr int kVD = 16;
+// Forward: 128 threads x 4 seeds = 512 seeds per work item. Adjoint pass A:
+// 128 threads x 2 seeds = 256 seeds per item (three 16-vectors per seed).
+// Adjoint pass B: 128 threads x 2 pixels.
+constexpr int kFT = 128, kFS = 4, kFSeeds = kFT * kFS;
+constexpr int kAT = 128, kAS = 2, kASeeds = kAT * kAS;
+constexpr int kBT = 128, kBP = 2;
 
 struct VSplit {
-    int tiles, chunks, chunk_len;
+    int tiles, chunks, chunk_len, seeds;  // seed tiles of `seeds`, pixel chunks of chunk_len
 };
 
-inline VSplit vsplit(int M, int64_t N, int target) {
+// Seed tiles x pixel chunks filling one wave of `slots` resident blocks
+// (chunks of any length: the stage loop handles a partial last stage).
+inline VSplit vsplit(int M, int64_t N, int slots, int seeds) {
     VSplit s;
-    s.tiles = (M + kVSeeds - 1) / kVSeeds;
-    const int max_chunks = (int)((N + kVPixTile - 1) / kVPixTile);
-    int ch = (target + s.tiles - 1) / s.tiles;
-    ch = ch < 1 ? 1 : (ch > max_chunks ? max_chunks : ch);
-    int per = (int)((N + ch - 1) / ch);
-    per = (per + kVPixTile - 1) / kVPixTile * kVPixTile;
-    s.chunk_len = per;
-    s.chunks = (int)((N + per - 1) / per);
+    s.seeds = seeds;
+    s.tiles = (M + seeds - 1) / seeds;
+    int ch = slots / s.tiles;
+    ch = ch < 1 ? 1 : (int64_t)ch > N ? (int)N : ch;
+    s.chunk_len = (int)((N + ch - 1) / ch);
+    s.chunks = (int)((N + s.chunk_len - 1) / s.chunk_len);
     return s;
 }
 
@@ -55,50 +61,57 @@ __device__ __forceinline__ void ld16(const float* src, float (&v)[16]) {
 }
 
 // Forward partial sums: for seed tile t and pixel chunk ch,
-// partial[item][k][r] = sum over the chunk of w p_k for seed t*256 + r.
-__global__ void __launch_bounds__(kVT)
+// partial[item][k][r] = sum over the chunk of w p_k for seed t*512 + r.
+// Thread j holds seeds j, j+128, j+256, j+384 of the tile; every pixel of a
+// stage is read once from shared memory for all four.
+__global__ void __launch_bounds__(kFT)
 k_vmf_fwd_partial(const float* __restrict__ P, int64_t N, const float* __restrict__ X, int M, float kappa,
                   VSplit sp, float* __restrict__ partial) {
+    const float kl2 = kappa * 1.4426950408889634f;  // exp(kappa u) = 2^(kappa log2(e) u)
     __shared__ __align__(16) float tile[kVPixTile * kVD];
     const int item = blockIdx.x;
     const int t = item / sp.chunks, ch = item - t * sp.chunks;
-    const int m0 = t * kVSeeds + threadIdx.x, m1 = m0 + kVT;
-    float x0[16], x1[16], y0[16], y1[16];
-    if (m0 < M) ld16(X + (int64_t)m0 * kVD, x0); else for (int k = 0; k < 16; ++k) x0[k] = 0.f;
-    if (m1 < M) ld16(X + (int64_t)m1 * kVD, x1); else for (int k = 0; k < 16; ++k) x1[k] = 0.f;
+    float x[kFS][16], y[kFS][16];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) y0[k] = y1[k] = 0.f;
+    for (int q = 0; q < kFS; ++q) {
+        const int m = t * kFSeeds + q * kFT + threadIdx.x;
+        if (m < M) ld16(X + (int64_t)m * kVD, x[q]);
+        else
+#pragma unroll
+            for (int k = 0; k < 16; ++k) x[q][k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) y[q][k] = 0.f;
+    }
     const int64_t p_begin = (int64_t)ch * sp.chunk_len;
     const int64_t p_end = min(N, p_begin + sp.chunk_len);
     for (int64_t pb = p_begin; pb < p_end; pb += kVPixTile) {
         const int cnt = (int)min((int64_t)kVPixTile, p_end - pb);
         __syncthreads();
-        for (int q = threadIdx.x; q < cnt * 4; q += kVT)
+        for (int q = threadIdx.x; q < cnt * 4; q += kFT)
             reinterpret_cast<float4*>(tile)[q] = reinterpret_cast<const float4*>(P + pb * kVD)[q];
         __syncthreads();
         for (int j = 0; j < cnt; ++j) {
             float p[16];
             ld16(tile + j * kVD, p);
-            float s0 = 0.f, s1 = 0.f;
+            float w[kFS];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                s0 = fmaf(x0[k], p[k], s0);
-                s1 = fmaf(x1[k], p[k], s1);
-            }
-            const float w0 = expf(kappa * (s0 - 1.f)), w1 = expf(kappa * (s1 - 1.f));
+            for (int q = 0; q < kFS; ++q) {
+                float sc = 0.f;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                y0[k] = fmaf(w0, p[k], y0[k]);
-                y1[k] = fmaf(w1, p[k], y1[k]);
+                for (int k = 0; k < 16; ++k) sc = fmaf(x[q][k], p[k], sc);
+                w[q] = exp2f(kl2 * (sc - 1.f));
             }
+#pragma unroll
+            for (int q = 0; q < kFS; ++q)
+#pragma unroll
+                for (int k = 0; k < 16; ++k) y[q][k] = fmaf(w[q], p[k], y[q][k]);
         }
     }
-    float* out = partial + (size_t)item * kVD * kVSeeds;
+    float* out = partial + (size_t)item * kVD * kFSeeds;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        out[k * kVSeeds + threadIdx.x] = y0[k];
-        out[k * kVSeeds + kVT + threadIdx.x] = y1[k];
-    }
+    for (int q = 0; q < kFS; ++q)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) out[k * kFSeeds + q * kFT + threadIdx.x] = y[q][k];
 }
 
 // One warp per seed: sum the chunk partials in a fixed order (lane-strided,
@@ -106,13 +119,13 @@ k_vmf_fwd_partial(const float* __restrict__ P, int64_t N, const float* __restric
 // Adjoint mode writes g = dL/dx (the sum itself) and the next gy from it.
 __device__ __forceinline__ void warp_sum16(const float* __restrict__ partial, VSplit sp, int m, float (&s)[16]) {
     const int lane = threadIdx.x & 31;
-    const int t = m / kVSeeds, r = m - t * kVSeeds;
+    const int t = m / sp.seeds, r = m - t * sp.seeds;
 #pragma unroll
     for (int k = 0; k < 16; ++k) s[k] = 0.f;
     for (int ch = lane; ch < sp.chunks; ch += 32) {
-        const float* in = partial + (size_t)(t * sp.chunks + ch) * kVD * kVSeeds + r;
+        const float* in = partial + (size_t)(t * sp.chunks + ch) * kVD * sp.seeds + r;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) s[k] += in[k * kVSeeds];
+        for (int k = 0; k < 16; ++k) s[k] += in[k * sp.seeds];
     }
 #pragma unroll
     for (int k = 0; k < 16; ++k)
@@ -152,55 +165,62 @@ __global__ void k_vmf_gy(const float* __restrict__ G, const float* __restrict__ 
     for (int k = 0; k < 16; ++k) GY[(int64_t)m * kVD + k] = (g[k] - x[k] * xg) * inv;
 }
 
-// Pass A: partial[item][k][r] = sum over the chunk of ds_mi p_ik.
-__global__ void __launch_bounds__(kVT)
+// Pass A: partial[item][k][r] = sum over the chunk of ds_mi p_ik, for seed
+// t*256 + r (thread j holds seeds j and j+128).
+__global__ void __launch_bounds__(kAT)
 k_vmf_bwd_seeds(const float* __restrict__ P, int64_t N, const float* __restrict__ X, const float* __restrict__ GY,
                 int M, float kappa, VSplit sp, float* __restrict__ partial) {
+    const float kl2 = kappa * 1.4426950408889634f;  // exp(kappa u) = 2^(kappa log2(e) u)
     __shared__ __align__(16) float tile[kVPixTile * kVD];
     const int item = blockIdx.x;
     const int t = item / sp.chunks, ch = item - t * sp.chunks;
-    const int m0 = t * kVSeeds + threadIdx.x, m1 = m0 + kVT;
-    float x0[16], x1[16], g0[16], g1[16], d0[16], d1[16];
-    if (m0 < M) { ld16(X + (int64_t)m0 * kVD, x0); ld16(GY + (int64_t)m0 * kVD, g0); }
-    else for (int k = 0; k < 16; ++k) x0[k] = g0[k] = 0.f;
-    if (m1 < M) { ld16(X + (int64_t)m1 * kVD, x1); ld16(GY + (int64_t)m1 * kVD, g1); }
-    else for (int k = 0; k < 16; ++k) x1[k] = g1[k] = 0.f;
+    float x[kAS][16], g[kAS][16], dd[kAS][16];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) d0[k] = d1[k] = 0.f;
+    for (int q = 0; q < kAS; ++q) {
+        const int m = t * kASeeds + q * kAT + threadIdx.x;
+        if (m < M) {
+            ld16(X + (int64_t)m * kVD, x[q]);
+            ld16(GY + (int64_t)m * kVD, g[q]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) x[q][k] = g[q][k] = 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) dd[q][k] = 0.f;
+    }
     const int64_t p_begin = (int64_t)ch * sp.chunk_len;
     const int64_t p_end = min(N, p_begin + sp.chunk_len);
     for (int64_t pb = p_begin; pb < p_end; pb += kVPixTile) {
         const int cnt = (int)min((int64_t)kVPixTile, p_end - pb);
         __syncthreads();
-        for (int q = threadIdx.x; q < cnt * 4; q += kVT)
+        for (int q = threadIdx.x; q < cnt * 4; q += kAT)
             reinterpret_cast<float4*>(tile)[q] = reinterpret_cast<const float4*>(P + pb * kVD)[q];
         __syncthreads();
         for (int j = 0; j < cnt; ++j) {
             float p[16];
             ld16(tile + j * kVD, p);
-            float s0 = 0.f, s1 = 0.f, a0 = 0.f, a1 = 0.f;
+            float e[kAS];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                s0 = fmaf(x0[k], p[k], s0);
-                s1 = fmaf(x1[k], p[k], s1);
-                a0 = fmaf(g0[k], p[k], a0);
-                a1 = fmaf(g1[k], p[k], a1);
-            }
-            const float e0 = kappa * expf(kappa * (s0 - 1.f)) * a0;
-            const float e1 = kappa * expf(kappa * (s1 - 1.f)) * a1;
+            for (int q = 0; q < kAS; ++q) {
+                float sc = 0.f, a = 0.f;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                d0[k] = fmaf(e0, p[k], d0[k]);
-                d1[k] = fmaf(e1, p[k], d1[k]);
+                for (int k = 0; k < 16; ++k) {
+                    sc = fmaf(x[q][k], p[k], sc);
+                    a = fmaf(g[q][k], p[k], a);
+                }
+                e[q] = kappa * exp2f(kl2 * (sc - 1.f)) * a;
             }
+#pragma unroll
+            for (int q = 0; q < kAS; ++q)
+#pragma unroll
+                for (int k = 0; k < 16; ++k) dd[q][k] = fmaf(e[q], p[k], dd[q][k]);
         }
     }
-    float* out = partial + (size_t)item * kVD * kVSeeds;
+    float* out = partial + (size_t)item * kVD * kASeeds;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        out[k * kVSeeds + threadIdx.x] = d0[k];
-        out[k * kVSeeds + kVT + threadIdx.x] = d1[k];
-    }
+    for (int q = 0; q < kAS; ++q)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) out[k * kASeeds + q * kAT + threadIdx.x] = dd[q][k];
 }
 
 __global__ void k_vmf_bwd_reduce(const float* __restrict__ partial, VSplit sp, int M, float* __restrict__ G) {
@@ -213,21 +233,33 @@ __global__ void k_vmf_bwd_reduce(const float* __restrict__ partial, VSplit sp, i
         for (int k = 0; k < 16; ++k) G[(int64_t)m * kVD + k] = s[k];
 }
 
-// Pass B: one thread per pixel, all seeds from shared memory.
-__global__ void __launch_bounds__(kVT)
+// Pass B: two pixels per thread (i and i + 128 of the block's 256), all
+// seeds from shared memory; each seed's x and gy are read once for both.
+__global__ void __launch_bounds__(kBT)
 k_vmf_bwd_pixels(const float* __restrict__ P, int64_t N, const float* __restrict__ X, const float* __restrict__ GY,
                  int M, float kappa, float* __restrict__ dP) {
+    const float kl2 = kappa * 1.4426950408889634f;  // exp(kappa u) = 2^(kappa log2(e) u)
     __shared__ __align__(16) float sx[64 * kVD];
     __shared__ __align__(16) float sg[64 * kVD];
-    const int64_t i = (int64_t)blockIdx.x * kVT + threadIdx.x;
-    const bool act = i < N;
-    float p[16], dp[16];
-    if (act) { ld16(P + i * kVD, p); ld16(dP + i * kVD, dp); }
-    else for (int k = 0; k < 16; ++k) p[k] = dp[k] = 0.f;
+    float p[kBP][16], dp[kBP][16];
+    int64_t idx[kBP];
+    bool act[kBP];
+#pragma unroll
+    for (int u = 0; u < kBP; ++u) {
+        idx[u] = (int64_t)blockIdx.x * (kBT * kBP) + u * kBT + threadIdx.x;
+        act[u] = idx[u] < N;
+        if (act[u]) {
+            ld16(P + idx[u] * kVD, p[u]);
+            ld16(dP + idx[u] * kVD, dp[u]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) p[u][k] = dp[u][k] = 0.f;
+        }
+    }
     for (int base = 0; base < M; base += 64) {
         const int cnt = min(64, M - base);
         __syncthreads();
-        for (int q = threadIdx.x; q < cnt * 4; q += kVT) {
+        for (int q = threadIdx.x; q < cnt * 4; q += kBT) {
             reinterpret_cast<float4*>(sx)[q] = reinterpret_cast<const float4*>(X + (int64_t)base * kVD)[q];
             reinterpret_cast<float4*>(sg)[q] = reinterpret_cast<const float4*>(GY + (int64_t)base * kVD)[q];
         }
@@ -236,21 +268,26 @@ k_vmf_bwd_pixels(const float* __restrict__ P, int64_t N, const float* __restrict
             float x[16], g[16];
             ld16(sx + j * kVD, x);
             ld16(sg + j * kVD, g);
-            float s = 0.f, a = 0.f;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                s = fmaf(x[k], p[k], s);
-                a = fmaf(g[k], p[k], a);
+            for (int u = 0; u < kBP; ++u) {
+                float sc = 0.f, a = 0.f;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    sc = fmaf(x[k], p[u][k], sc);
+                    a = fmaf(g[k], p[u][k], a);
+                }
+                const float w = exp2f(kl2 * (sc - 1.f));
+                const float ds = kappa * w * a;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) dp[u][k] = fmaf(w, g[k], fmaf(ds, x[k], dp[u][k]));
             }
-            const float w = expf(kappa * (s - 1.f));
-            const float ds = kappa * w * a;
-#pragma unroll
-            for (int k = 0; k < 16; ++k) dp[k] = fmaf(w, g[k], fmaf(ds, x[k], dp[k]));
         }
     }
-    if (act)
 #pragma unroll
-        for (int k = 0; k < 16; ++k) dP[i * kVD + k] = dp[k];
+    for (int u = 0; u < kBP; ++u)
+        if (act[u])
+#pragma unroll
+            for (int k = 0; k < 16; ++k) dP[idx[u] * kVD + k] = dp[u][k];
 }
 
 struct VmfWork {
@@ -259,15 +296,18 @@ struct VmfWork {
     float* ynorm;   // [T, M]
     float* gy;      // [M, 16]
     float* g;       // [M, 16]
-    VSplit sp;
+    VSplit sp;      // forward items (512-seed tiles)
+    VSplit spa;     // adjoint pass A items (256-seed tiles)
 };
 
-int vmf_target(int* sms_out) {
-    int dev = 0, sms = 1;
+// Resident blocks of a kernel over the whole GPU (blocks per SM x SMs).
+template <class K>
+int vmf_slots(K kernel, int threads) {
+    int dev = 0, sms = 1, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    *sms_out = sms;
-    return 4 * sms;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0) != cudaSuccess || per < 1) per = 1;
+    return per * sms;
 }
 
 ms_status vmf_validate(const float* P, int64_t N, const float* X0, int32_t M, int32_t dim, double kappa, int32_t T) {
@@ -279,11 +319,11 @@ ms_status vmf_validate(const float* P, int64_t N, const float* X0, int32_t M, in
 }
 
 ms_status vmf_alloc(VmfWork* w, int64_t N, int32_t M, int32_t T, cudaStream_t st) {
-    int sms = 1;
-    const int target = vmf_target(&sms);
-    w->sp = vsplit(M, N, target);
-    const size_t items = (size_t)w->sp.tiles * w->sp.chunks;
-    const size_t bytes = items * kVD * kVSeeds * sizeof(float) + (size_t)(T + 1) * M * kVD * sizeof(float) +
+    w->sp = vsplit(M, N, vmf_slots(k_vmf_fwd_partial, kFT), kFSeeds);
+    w->spa = vsplit(M, N, vmf_slots(k_vmf_bwd_seeds, kAT), kASeeds);
+    const size_t pf = (size_t)w->sp.tiles * w->sp.chunks * kFSeeds, pa = (size_t)w->spa.tiles * w->spa.chunks * kASeeds;
+    const size_t pmax = pf > pa ? pf : pa;
+    const size_t bytes = pmax * kVD * sizeof(float) + (size_t)(T + 1) * M * kVD * sizeof(float) +
                          (size_t)(T > 0 ? T : 1) * M * sizeof(float) + 2 * (size_t)M * kVD * sizeof(float) + 4 * 256;
     char* b = nullptr;
     MS_CUDA(cudaMallocAsync((void**)&b, bytes, st));
@@ -292,7 +332,7 @@ ms_status vmf_alloc(VmfWork* w, int64_t N, int32_t M, int32_t T, cudaStream_t st
         b += (n + 255) / 256 * 256;
         return (float*)p;
     };
-    w->partial = take(items * kVD * kVSeeds * sizeof(float));
+    w->partial = take(pmax * kVD * sizeof(float));
     w->iters = take((size_t)(T + 1) * M * kVD * sizeof(float));
     w->ynorm = take((size_t)(T > 0 ? T : 1) * M * sizeof(float));
     w->gy = take((size_t)M * kVD * sizeof(float));
@@ -309,7 +349,7 @@ ms_status vmf_forward_steps(const float* P, int64_t N, const float* X0, int32_t 
     for (int t = 0; t < T; ++t) {
         const float* Xt = w->iters + (size_t)t * M * kVD;
         float* Xn = w->iters + (size_t)(t + 1) * M * kVD;
-        k_vmf_fwd_partial<<<items, kVT, 0, st>>>(P, N, Xt, M, kappa, w->sp, w->partial);
+        k_vmf_fwd_partial<<<items, kFT, 0, st>>>(P, N, Xt, M, kappa, w->sp, w->partial);
         MS_LAUNCH("k_vmf_fwd_partial");
         k_vmf_fwd_reduce<<<rblocks, 256, 0, st>>>(w->partial, w->sp, M, Xn, w->ynorm + (size_t)t * M);
         MS_LAUNCH("k_vmf_fwd_reduce");
@@ -357,18 +397,19 @@ extern "C" ms_status ms_vmf_backward(const float* d_P, int64_t N, const float* d
     if (s == MS_OK)
         s = cuda_check(cudaMemcpyAsync(w.g, d_GT, sizeof(float) * (size_t)M * kVD, cudaMemcpyDeviceToDevice, st),
                        "copy g_T");
-    const unsigned items = (unsigned)(w.sp.tiles * w.sp.chunks);
+    const unsigned items = (unsigned)(w.spa.tiles * w.spa.chunks);
     const unsigned rblocks = (unsigned)((M + 7) / 8);
     for (int t = T - 1; t >= 0 && s == MS_OK; --t) {
         const float* Xt = w.iters + (size_t)t * M * kVD;
         const float* Xn = w.iters + (size_t)(t + 1) * M * kVD;
         k_vmf_gy<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(w.g, Xn, w.ynorm + (size_t)t * M, M, w.gy);
         if ((s = cuda_check(cudaGetLastError(), "k_vmf_gy")) != MS_OK) break;
-        k_vmf_bwd_pixels<<<(unsigned)((N + kVT - 1) / kVT), kVT, 0, st>>>(d_P, N, Xt, w.gy, M, kf, d_dP);
+        k_vmf_bwd_pixels<<<(unsigned)((N + kBT * kBP - 1) / (kBT * kBP)), kBT, 0, st>>>(d_P, N, Xt, w.gy, M, kf,
+                                                                                    d_dP);
         if ((s = cuda_check(cudaGetLastError(), "k_vmf_bwd_pixels")) != MS_OK) break;
-        k_vmf_bwd_seeds<<<items, kVT, 0, st>>>(d_P, N, Xt, w.gy, M, kf, w.sp, w.partial);
+        k_vmf_bwd_seeds<<<items, kAT, 0, st>>>(d_P, N, Xt, w.gy, M, kf, w.spa, w.partial);
         if ((s = cuda_check(cudaGetLastError(), "k_vmf_bwd_seeds")) != MS_OK) break;
-        k_vmf_bwd_reduce<<<rblocks, 256, 0, st>>>(w.partial, w.sp, M, w.g);
+        k_vmf_bwd_reduce<<<rblocks, 256, 0, st>>>(w.partial, w.spa, M, w.g);
         s = cuda_check(cudaGetLastError(), "k_vmf_bwd_reduce");
     }
     if (s == MS_OK)

@@ -697,10 +697,14 @@ template <int Dp>
 __global__ void __launch_bounds__(kMT)
 k_b_merge_pairs(const BFrame* __restrict__ frames, const BState* __restrict__ states, int B,
                 const int32_t* __restrict__ off, const float* __restrict__ X, const int32_t* __restrict__ cand,
-                const int32_t* __restrict__ cand_rank, const uint8_t* __restrict__ cand_state, float thr_f,
+                const int32_t* __restrict__ rank_cand, const uint8_t* __restrict__ cand_state, float thr_f,
                 double thr, int32_t* __restrict__ conf_deg, int32_t* __restrict__ conf) {
+    // Candidates are visited in rank order: thread t of a block takes rank
+    // r0 + t and compares it with every higher-priority candidate (rank < its
+    // own) in the block's slice of ranks, so neighbouring lanes stop at
+    // neighbouring ranks and only the k(k-1)/2 ordered pairs are tested.
     __shared__ __align__(16) float tile[kVT * Dp];
-    __shared__ int32_t s_rank[kVT];
+    __shared__ int32_t s_idx[kVT];
     __shared__ uint8_t s_state[kVT];
     const int S = off[B + 1];
     for (int bb = blockIdx.x; bb < off[B]; bb += gridDim.x) {
@@ -708,10 +712,12 @@ k_b_merge_pairs(const BFrame* __restrict__ frames, const BState* __restrict__ st
         const int lb = bb - off[f], sl = lb % S;
         const int64_t base = frames[f].pix0;
         const int k = states[f].dc.n_cand;
-        const int a = (lb / S) * kMT + threadIdx.x;
-        const int lo = (int)((int64_t)sl * k / S), hi = (int)((int64_t)(sl + 1) * k / S);
-        const bool act = a < k && cand_state[base + a] == kUndecided;
-        const int ra = a < k ? cand_rank[base + a] : 0;
+        const int r0 = (lb / S) * kMT;
+        const int r = r0 + threadIdx.x;
+        const int a = r < k ? rank_cand[base + r] : -1;
+        const bool act = a >= 0 && cand_state[base + a] == kUndecided;
+        const int lo = (int)((int64_t)sl * k / S);
+        const int hi = min((int)((int64_t)(sl + 1) * k / S), r0 + kMT - 1);
         float x[Dp];
         if (act) ldv<Dp>(x, X + (int64_t)cand[base + a] * Dp);
         for (int t0 = lo; t0 < hi; t0 += kVT) {
@@ -719,21 +725,24 @@ k_b_merge_pairs(const BFrame* __restrict__ frames, const BState* __restrict__ st
             __syncthreads();
             for (int q = threadIdx.x; q < cnt * Dp; q += kMT) {
                 const int j = q / Dp, kk = q - j * Dp;
-                tile[q] = X[(int64_t)cand[base + t0 + j] * Dp + kk];
+                tile[q] = X[(int64_t)cand[base + rank_cand[base + t0 + j]] * Dp + kk];
             }
             for (int j = threadIdx.x; j < cnt; j += kMT) {
-                s_rank[j] = cand_rank[base + t0 + j];
-                s_state[j] = cand_state[base + t0 + j];
+                const int cj = rank_cand[base + t0 + j];
+                s_idx[j] = cj;
+                s_state[j] = cand_state[base + cj];
             }
             __syncthreads();
-            if (act)
-                for (int j = 0; j < cnt; ++j) {
-                    if (s_rank[j] >= ra || s_state[j] == kRemoved) continue;
+            if (act) {
+                const int jend = min(cnt, r - t0);
+                for (int j = 0; j < jend; ++j) {
+                    if (s_state[j] == kRemoved) continue;
                     if (cos_at_least<Dp>(x, tile + j * Dp, thr_f, thr)) {
                         const int slot = atomicAdd(&conf_deg[base + a], 1);
-                        if (slot < kMergeCap) conf[(base + a) * kMergeCap + slot] = t0 + j;
+                        if (slot < kMergeCap) conf[(base + a) * kMergeCap + slot] = s_idx[j];
                     }
                 }
+            }
         }
         __syncthreads();
     }
@@ -845,12 +854,26 @@ k_b_merge_append(const BFrame* __restrict__ frames, BState* states, const float*
 }
 
 // Coverage for the frames whose round ended: FP32 decides, FP64 inside the band.
+// A block takes kPT * cov_per(Dp) consecutive pixels (1024 for d <= 16),
+// compacts the uncovered ones into a shared list (warp ballots and a prefix
+// over the block's warp-passes) and gives each thread up to cov_per of them,
+// so every tile of new modes read from memory is tested against all the
+// block's uncovered pixels at once.
+__host__ __device__ constexpr int cov_per(int Dp) { return Dp <= 16 ? 4 : 2; }
+
 template <int Dp>
 __global__ void __launch_bounds__(kPT)
 k_b_cover(const BFrame* __restrict__ frames, BState* states, int B, const int32_t* __restrict__ off, int d,
           const float* __restrict__ P32, const int32_t* __restrict__ pix, uint8_t* __restrict__ covered,
           const float* __restrict__ modes, float c_f, double c) {
     __shared__ __align__(16) float tile[kVT * Dp];
+    constexpr int kCovPer = cov_per(Dp);
+    constexpr int kNW = kPT / 32 * kCovPer;  // warp-passes of a block
+    static_assert(kNW <= 32, "one warp scans the warp-pass counts");
+    __shared__ int32_t s_list[kPT * kCovPer];
+    __shared__ int32_t s_pos[kNW];
+    __shared__ int s_nact;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int bb = blockIdx.x; bb < off[B]; bb += gridDim.x) {
         const int f = locate(off, B, bb);
         const int lb = bb - off[f];
@@ -858,33 +881,77 @@ k_b_cover(const BFrame* __restrict__ frames, BState* states, int B, const int32_
         BState& st = states[f];
         const int64_t base = fr.pix0;
         const int k0 = st.k0, k1 = st.dc.n_kept;
-        const int i = lb * kPT + threadIdx.x;
-        const bool act = i < fr.n && covered[base + i] == 0;
-        float p[Dp];
-        if (act) ldv<Dp>(p, P32 + (base + i) * Dp);
-        bool cov = false, band = false;
+        const int i0 = lb * kPT * kCovPer;
+        unsigned bal[kCovPer];
+#pragma unroll
+        for (int u = 0; u < kCovPer; ++u) {
+            const int i = i0 + u * kPT + threadIdx.x;
+            bal[u] = __ballot_sync(0xffffffffu, i < fr.n && covered[base + i] == 0);
+            if (lane == 0) s_pos[u * (kPT / 32) + warp] = __popc(bal[u]);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const int v = lane < kNW ? s_pos[lane] : 0;
+            int incl = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane < kNW) s_pos[lane] = incl - v;
+            if (lane == 31) s_nact = incl;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kCovPer; ++u)
+            if ((bal[u] >> lane) & 1u)
+                s_list[s_pos[u * (kPT / 32) + warp] + __popc(bal[u] & ((1u << lane) - 1u))] =
+                    i0 + u * kPT + threadIdx.x;
+        __syncthreads();
+        const int nact = s_nact;
+        if (nact == 0) continue;
+        int idx[kCovPer];
+        float p[kCovPer][Dp];
+        bool cov[kCovPer], band[kCovPer];
+#pragma unroll
+        for (int u = 0; u < kCovPer; ++u) {
+            const int e = threadIdx.x + u * kPT;
+            idx[u] = e < nact ? s_list[e] : -1;
+            if (idx[u] >= 0) ldv<Dp>(p[u], P32 + (base + idx[u]) * Dp);
+            cov[u] = band[u] = false;
+        }
         for (int t0 = k0; t0 < k1; t0 += kVT) {
             const int cnt = min(kVT, k1 - t0);
             __syncthreads();
             for (int q = threadIdx.x; q < cnt * Dp; q += kPT) tile[q] = modes[(base + t0) * Dp + q];
             __syncthreads();
-            if (act && !cov)
-                for (int j = 0; j < cnt; ++j) {
-                    const float s = dot_seq<Dp>(p, tile + j * Dp);
-                    if (s >= c_f + kEpsF32) { cov = true; break; }
-                    if (s >= c_f - kEpsF32) band = true;
-                }
+#pragma unroll
+            for (int u = 0; u < kCovPer; ++u)
+                if (idx[u] >= 0 && !cov[u])
+                    for (int j = 0; j < cnt; ++j) {
+                        const float sc = dot_seq<Dp>(p[u], tile + j * Dp);
+                        if (sc >= c_f + kEpsF32) { cov[u] = true; break; }
+                        if (sc >= c_f - kEpsF32) band[u] = true;
+                    }
         }
-        if (act && !cov && band) {
-            const float* e = fr.emb + (int64_t)pix[base + i] * d;
-            for (int j = k0; j < k1 && !cov; ++j) {
-                const float* m = modes + (base + j) * Dp;
-                if (dot_seq<Dp>(p, m) >= c_f - kEpsF32 && cos64(e, m, d) >= c) cov = true;
+        int newly = 0;
+#pragma unroll
+        for (int u = 0; u < kCovPer; ++u) {
+            if (idx[u] >= 0 && !cov[u] && band[u]) {
+                const float* e = fr.emb + (int64_t)pix[base + idx[u]] * d;
+                for (int j = k0; j < k1 && !cov[u]; ++j) {
+                    const float* m = modes + (base + j) * Dp;
+                    if (dot_seq<Dp>(p[u], m) >= c_f - kEpsF32 && cos64(e, m, d) >= c) cov[u] = true;
+                }
+            }
+            if (idx[u] >= 0 && cov[u]) {
+                covered[base + idx[u]] = 1;
+                ++newly;
             }
         }
-        if (act && cov) covered[base + i] = 1;
-        const int newly = __syncthreads_count(act && cov);
-        if (threadIdx.x == 0 && newly) atomicSub(&st.dc.n_uncovered, newly);
+        // each warp's count of newly covered pixels
+        for (int o = 16; o > 0; o >>= 1) newly += __shfl_xor_sync(0xffffffffu, newly, o);
+        if (lane == 0 && newly) atomicSub(&st.dc.n_uncovered, newly);
+        __syncthreads();
     }
 }
 
@@ -1037,7 +1104,7 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     k_b_merge_old<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_split, b->X, b->cand, b->modes, mf,
                                         b->cfg.merge_cos, b->cand_state);
     LAUNCHED("k_b_merge_old");
-    k_b_merge_pairs<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_split, b->X, b->cand, b->cand_rank,
+    k_b_merge_pairs<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_split, b->X, b->cand, b->rank_cand,
                                           b->cand_state, mf, b->cfg.merge_cos, b->conf_deg, b->conf);
     LAUNCHED("k_b_merge_pairs");
     for (int sw = 0; sw < 8; ++sw) {
@@ -1051,7 +1118,7 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     k_b_merge_append<Dp><<<B, kIT, 0, s>>>(b->frames, b->states, b->X, b->cand, b->rank_cand, b->cand_state,
                                            b->modes);
     LAUNCHED("k_b_merge_append");
-    k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, B, kSelDonePixels, kPT, 0, b->blk_off);
+    k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, B, kSelDonePixels, kPT * cov_per(Dp), 0, b->blk_off);
     LAUNCHED("k_b_blocks");
     k_b_cover<Dp><<<G, kPT, 0, s>>>(b->frames, b->states, B, b->blk_off, b->d, b->P32, b->pix, b->covered, b->modes,
                                     (float)b->cfg.bandwidth_cos, b->cfg.bandwidth_cos);

@@ -1164,7 +1164,7 @@ template <int Dp>
 ms_status enqueue_label(ms_batch* b, cudaStream_t s) {
     if (b->tc)  // BF16 form (d <= 16): the tensor-core kernel, same labels (exact FP64 argmax)
         return launch_label_tc_batch(b->pmap, b->mmap, b->Mk, b->frames, b->states, b->B, (int)b->max_pk_rows,
-                                     b->modes, b->P32, b->pix, b->d, b->label_ptrs, b->lsc, b->tc_grid, b->misc + 1,
+                                     b->modes, b->P32, b->pix, b->d, b->label_ptrs, b->lsc, b->num_sms, b->misc + 1,
                                      s);
     k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, b->B, kSelAllPixels, kPT, 0, b->blk_off);
     MS_LAUNCH("k_b_blocks");

@@ -78,7 +78,7 @@ ms_status launch_label(ms_ctx* ctx, int32_t* d_labels) {
         LabelTcScratch sc{ctx->label_fix, (int*)(ctx->label_fix + ctx->n), nullptr};
         const ms_status s = launch_label_tc_single(ctx->pmap, ctx->Mk, ctx->n_pad, ctx->modes, ctx->n_kept,
                                                    (int)ctx->n, ctx->P32, ctx->pix, ctx->emb, ctx->d, d_labels, sc,
-                                                   ctx->tc_grid, &ctx->dc->status, ctx->stream);
+                                                   ctx->num_sms, &ctx->dc->status, ctx->stream);
         ctx->launches += ctx->n_kept > 1 ? 3 : 2;
         return s;
     }

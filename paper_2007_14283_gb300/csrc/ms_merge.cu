@@ -114,34 +114,42 @@ k_merge_old(const float* __restrict__ X, const int32_t* __restrict__ cand, int k
 template <int Dp>
 __global__ void __launch_bounds__(kMT)
 k_merge_pairs(const float* __restrict__ X, const int32_t* __restrict__ cand, int k,
-              const int32_t* __restrict__ cand_rank, const uint8_t* __restrict__ cand_state,
+              const int32_t* __restrict__ rank_cand, const uint8_t* __restrict__ cand_state,
               float thr_f, double thr, int32_t* __restrict__ conf_deg, int32_t* __restrict__ conf) {
+    // Candidates in rank order: thread t of block x takes rank x*kMT + t and
+    // compares it with the higher-priority candidates (lower ranks) of the
+    // block's slice, so neighbouring lanes stop at neighbouring ranks and only
+    // the k(k-1)/2 ordered pairs are tested.
     __shared__ __align__(16) float tile[kVT * Dp];
-    __shared__ int32_t s_rank[kVT];
+    __shared__ int32_t s_idx[kVT];
     __shared__ uint8_t s_state[kVT];
-    const int a = blockIdx.x * kMT + threadIdx.x;
-    const bool act = a < k && cand_state[a] == kUndecided;
-    const int ra = a < k ? cand_rank[a] : 0;
+    const int r0 = blockIdx.x * kMT;
+    const int r = r0 + threadIdx.x;
+    const int a = r < k ? rank_cand[r] : -1;
+    const bool act = a >= 0 && cand_state[a] == kUndecided;
     float x[Dp];
     if (act) load_vec<Dp>(x, X + (int64_t)cand[a] * Dp);
-    const int lo = (int)((int64_t)blockIdx.y * k / gridDim.y), hi = (int)((int64_t)(blockIdx.y + 1) * k / gridDim.y);
+    const int lo = (int)((int64_t)blockIdx.y * k / gridDim.y);
+    const int hi = min((int)((int64_t)(blockIdx.y + 1) * k / gridDim.y), r0 + kMT - 1);
     for (int base = lo; base < hi; base += kVT) {
         const int cnt = min(kVT, hi - base);
         for (int q = threadIdx.x; q < cnt * Dp; q += kMT) {
             const int j = q / Dp, kk = q - j * Dp;
-            tile[q] = X[(int64_t)cand[base + j] * Dp + kk];
+            tile[q] = X[(int64_t)cand[rank_cand[base + j]] * Dp + kk];
         }
         for (int j = threadIdx.x; j < cnt; j += kMT) {
-            s_rank[j] = cand_rank[base + j];
-            s_state[j] = cand_state[base + j];
+            const int cj = rank_cand[base + j];
+            s_idx[j] = cj;
+            s_state[j] = cand_state[cj];
         }
         __syncthreads();
         if (act) {
-            for (int j = 0; j < cnt; ++j) {
-                if (s_rank[j] >= ra || s_state[j] == kRemoved) continue;
+            const int jend = min(cnt, r - base);
+            for (int j = 0; j < jend; ++j) {
+                if (s_state[j] == kRemoved) continue;
                 if (cos_at_least<Dp>(x, tile + j * Dp, thr_f, thr)) {
                     const int slot = atomicAdd(&conf_deg[a], 1);
-                    if (slot < kMergeCap) conf[(int64_t)a * kMergeCap + slot] = base + j;
+                    if (slot < kMergeCap) conf[(int64_t)a * kMergeCap + slot] = s_idx[j];
                 }
             }
         }
@@ -263,43 +271,96 @@ k_merge_append(const float* __restrict__ X, const int32_t* __restrict__ cand,
 // Coverage (OSOP stop rule): an uncovered pixel is covered once some new mode
 // has cos >= c. FP32 decides pairs outside the band; inside it the cosine is
 // recomputed in FP64 from the raw embedding.
+// A block takes 256 * cover_per(Dp) consecutive pixels (1024 for d <= 16),
+// compacts the uncovered ones into a shared list (warp ballots and a prefix
+// over the block's warp-passes) and gives each thread up to cover_per of
+// them, so every tile of new modes is read once for all of them.
+__host__ __device__ constexpr int cover_per(int Dp) { return Dp <= 16 ? 4 : 2; }
+
 template <int Dp>
 __global__ void __launch_bounds__(256)
 k_cover(const float* __restrict__ P32, const float* __restrict__ emb, int d,
         const int32_t* __restrict__ pix, int n, uint8_t* __restrict__ covered,
         const float* __restrict__ modes, int k0, int k1, float c_f, double c, DevCounters* dc) {
+    constexpr int kPer = cover_per(Dp);
+    constexpr int kNW = 256 / 32 * kPer;  // warp-passes of the block
+    static_assert(kNW <= 32, "one warp scans the warp-pass counts");
     __shared__ __align__(16) float tile[kVT * Dp];
-    const int i = blockIdx.x * 256 + threadIdx.x;
-    const bool act = i < n && covered[i] == 0;
-    float p[Dp];
-    if (act) load_vec<Dp>(p, P32 + (int64_t)i * Dp);
-    bool cov = false, band = false;
+    __shared__ int32_t s_list[256 * kPer];
+    __shared__ int32_t s_pos[kNW];
+    __shared__ int s_nact;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i0 = blockIdx.x * 256 * kPer;
+    unsigned bal[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int i = i0 + u * 256 + threadIdx.x;
+        bal[u] = __ballot_sync(0xffffffffu, i < n && covered[i] == 0);
+        if (lane == 0) s_pos[u * 8 + warp] = __popc(bal[u]);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int v = lane < kNW ? s_pos[lane] : 0;
+        int incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane < kNW) s_pos[lane] = incl - v;
+        if (lane == 31) s_nact = incl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kPer; ++u)
+        if ((bal[u] >> lane) & 1u)
+            s_list[s_pos[u * 8 + warp] + __popc(bal[u] & ((1u << lane) - 1u))] = i0 + u * 256 + threadIdx.x;
+    __syncthreads();
+    const int nact = s_nact;
+    if (nact == 0) return;
+    int idx[kPer];
+    float p[kPer][Dp];
+    bool cov[kPer], band[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int e = threadIdx.x + u * 256;
+        idx[u] = e < nact ? s_list[e] : -1;
+        if (idx[u] >= 0) load_vec<Dp>(p[u], P32 + (int64_t)idx[u] * Dp);
+        cov[u] = band[u] = false;
+    }
     for (int base = k0; base < k1; base += kVT) {
         const int cnt = min(kVT, k1 - base);
+        __syncthreads();
         for (int q = threadIdx.x; q < cnt * Dp; q += 256) tile[q] = modes[(int64_t)base * Dp + q];
         __syncthreads();
-        if (act && !cov) {
-            for (int j = 0; j < cnt; ++j) {
-                const float s = dot_seq<Dp>(p, tile + j * Dp);
-                if (s >= c_f + kEpsF32) {
-                    cov = true;
-                    break;
+#pragma unroll
+        for (int u = 0; u < kPer; ++u)
+            if (idx[u] >= 0 && !cov[u])
+                for (int j = 0; j < cnt; ++j) {
+                    const float sc = dot_seq<Dp>(p[u], tile + j * Dp);
+                    if (sc >= c_f + kEpsF32) {
+                        cov[u] = true;
+                        break;
+                    }
+                    if (sc >= c_f - kEpsF32) band[u] = true;
                 }
-                if (s >= c_f - kEpsF32) band = true;
+    }
+    int newly = 0;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        if (idx[u] >= 0 && !cov[u] && band[u]) {
+            const float* e = emb + (int64_t)pix[idx[u]] * d;
+            for (int j = k0; j < k1 && !cov[u]; ++j) {
+                const float* m = modes + (int64_t)j * Dp;
+                if (dot_seq<Dp>(p[u], m) >= c_f - kEpsF32 && cos64(e, m, d) >= c) cov[u] = true;
             }
         }
-        __syncthreads();
-    }
-    if (act && !cov && band) {
-        const float* e = emb + (int64_t)pix[i] * d;
-        for (int j = k0; j < k1 && !cov; ++j) {
-            const float* m = modes + (int64_t)j * Dp;
-            if (dot_seq<Dp>(p, m) >= c_f - kEpsF32 && cos64(e, m, d) >= c) cov = true;
+        if (idx[u] >= 0 && cov[u]) {
+            covered[idx[u]] = 1;
+            ++newly;
         }
     }
-    if (act && cov) covered[i] = 1;
-    const int newly = __syncthreads_count(act && cov);
-    if (threadIdx.x == 0 && newly) atomicSub(&dc->n_uncovered, newly);
+    for (int o = 16; o > 0; o >>= 1) newly += __shfl_xor_sync(0xffffffffu, newly, o);
+    if (lane == 0 && newly) atomicSub(&dc->n_uncovered, newly);
 }
 
 // Slices of an O(outer x inner) loop so that the grid fills about four waves
@@ -331,7 +392,7 @@ ms_status merge_prepare_t(ms_ctx* ctx, int32_t k) {
         MS_LAUNCH("k_merge_old");
     }
     k_merge_pairs<Dp><<<dim3(gm, inner_slices((int)gm, k, ctx->num_sms)), kMT, 0, ctx->stream>>>(
-        ctx->X, ctx->cand, k, ctx->cand_rank, ctx->cand_state, thr_f, thr, ctx->conf_deg, ctx->conf);
+        ctx->X, ctx->cand, k, ctx->rank_cand, ctx->cand_state, thr_f, thr, ctx->conf_deg, ctx->conf);
     MS_LAUNCH("k_merge_pairs");
     ctx->launches += 4;
     return MS_OK;
@@ -408,7 +469,7 @@ ms_status launch_merge_append(ms_ctx* ctx, int32_t k) {
 ms_status launch_cover(ms_ctx* ctx, int32_t k0, int32_t k1) {
     if (k1 <= k0 || ctx->n == 0) return MS_OK;
     const float c_f = (float)ctx->cfg.bandwidth_cos;
-    const unsigned g = (unsigned)((ctx->n + 255) / 256);
+    const unsigned g = (unsigned)((ctx->n + 256 * cover_per(ctx->Dp) - 1) / (256 * cover_per(ctx->Dp)));
     if (ctx->Dp == 16)
         k_cover<16><<<g, 256, 0, ctx->stream>>>(ctx->P32, ctx->emb, ctx->d, ctx->pix, (int)ctx->n,
                                                 ctx->covered, ctx->modes, k0, k1, c_f,

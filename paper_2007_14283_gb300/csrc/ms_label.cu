@@ -1,11 +1,13 @@
 // Labelling (Algorithm 2, lines 10-12): every foreground vector takes the
 // mode of highest cosine, lowest index on ties; background stays -1.
 //
-// A thread owns one pixel and scans the modes from shared memory in FP32,
-// keeping the best and second-best scores. When the two are within 2*kEpsF32
-// the winner is re-decided in FP64 among the modes whose FP32 score is within
-// 2*kEpsF32 of the best, from the raw embedding: the FP64 argmax always lies in
-// that set, so the label is the exact FP64 argmax over the modes.
+// FP32 form (the BF16 form labels on the tensor cores, ms_label_tc.cu, with
+// the same result): a thread owns one pixel and scans the modes from shared
+// memory in FP32, keeping the best and second-best scores. When the two are
+// within 2*kEpsF32 the winner is re-decided in FP64 among the modes whose FP32
+// score is within 2*kEpsF32 of the best, from the raw embedding: the FP64
+// argmax always lies in that set, so the label is the exact FP64 argmax over
+// the modes.
 #include "ms_batch.cuh"
 #include "ms_device.cuh"
 

@@ -78,7 +78,6 @@ struct LabelTcScratch {
     int32_t* off;
 };
 
-int label_tc_smem_bytes();
 ms_status label_tc_setup();
 ms_status launch_label_tc_single(const CUtensorMap& pmap, void* Mk, int64_t n_pad, const float* modes, int K, int n,
                                  const float* P32, const int32_t* pix, const float* emb, int d, int32_t* labels,

@@ -411,8 +411,6 @@ __global__ void k_label_items(const BFrame* __restrict__ frames, int B, int32_t*
 
 }  // namespace
 
-int label_tc_smem_bytes() { return kLSmemBytes; }
-
 ms_status label_tc_setup() {
     MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbSingle>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLSmemBytes));
     MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLSmemBytes));

@@ -86,7 +86,10 @@ typedef struct ms_config {
     int32_t batch_split;  /* ms_batch_* only: 0 = each frame split into work items as on its own
                              (results bit-identical to ms_run on that frame); 1 = the batch's
                              work items shared out by each frame's seed x pixel work */
-    int32_t reserved[6];  /* zero */
+    int32_t batch_max_passes; /* ms_batch_* only: guard on passes of the graph's loop body (every
+                                 iterating frame advances one iteration per pass); a batch still
+                                 unfinished after it stops with MS_ERR_TIMEOUT. 0 = 200000 */
+    int32_t reserved[5];  /* zero */
 } ms_config;
 
 /* Per-context counters, filled by ms_stats_get. */
@@ -114,6 +117,12 @@ MS_API void ms_config_default(ms_config* cfg);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 MS_API const char* ms_last_error(void);
+
+/* Testing hook for the allocation-failure path (no counterpart in the paper):
+ * the next `count` workspace allocations of this process (ms_create,
+ * ms_batch_create) fail with MS_ERR_OOM as if cudaMalloc had failed, without
+ * calling it; nothing is left allocated. count <= 0 clears it. */
+MS_API void ms_inject_alloc_failure(int32_t count);
 
 /* Device bytes ms_create would allocate for n_pixels pixels with cfg. */
 MS_API ms_status ms_workspace_bytes(const ms_config* cfg, int64_t n_pixels, int64_t* bytes_out);
@@ -251,7 +260,10 @@ MS_API ms_status ms_tc_selftest(const float* d_X, const float* d_P, int32_t n_pi
  * that first call before capturing a stream. All calls on a device share the
  * array, which keeps the last call's contents (each call clears what must
  * start at zero): calls whose work overlaps on the GPU, e.g. on two streams,
- * race. Work is enqueued on `stream`; the call does not synchronise. */
+ * race. Work is enqueued on `stream`; the call does not synchronise, so a
+ * pixel of zero or non-finite norm cannot be rejected up front: the call then
+ * returns MS_OK and every row of d_acc_out reads sums 0 and count -1 (check
+ * the counts after synchronising). Each call clears that error state. */
 MS_API ms_status ms_window_sums_static(const float* d_X, int32_t m, const float* d_P, int32_t n, double c,
                                        int64_t* d_acc_out, void* stream);
 

@@ -41,7 +41,8 @@ class ms_config(ctypes.Structure):
         ("H", ctypes.c_double), ("P_target", ctypes.c_double), ("alpha", ctypes.c_double),
         ("merge_cos", ctypes.c_double), ("seed", ctypes.c_uint64), ("frame_id", ctypes.c_uint64),
         ("precision", ctypes.c_int32), ("max_rounds", ctypes.c_int32), ("eps_band", ctypes.c_double),
-        ("all_seeds", ctypes.c_int32), ("batch_split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6),
+        ("all_seeds", ctypes.c_int32), ("batch_split", ctypes.c_int32), ("batch_max_passes", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 
@@ -97,6 +98,7 @@ _SIGNATURES = {
     "ms_batch_autotune": (_i32, [_vp, _i32, ctypes.POINTER(ms_tune_result), _i32, _pi32]),
     "ms_batch_modes": (_i32, [_vp, _i32, _vp, _i32, _pi32]),
     "ms_batch_destroy": (None, [_vp]),
+    "ms_inject_alloc_failure": (None, [_i32]),
 }
 
 
@@ -146,6 +148,11 @@ def ms_config_default(**overrides) -> ms_config:
             raise KeyError(k)
         setattr(cfg, k, v)
     return cfg
+
+
+def ms_inject_alloc_failure(count: int) -> None:
+    """Testing hook: the next `count` workspace allocations fail with MS_ERR_OOM."""
+    load().ms_inject_alloc_failure(int(count))
 
 
 def ms_last_error() -> str:

@@ -5,6 +5,7 @@
 // drawn from the foreground only); N doubles while N < L*N_min and shrinks by
 // N_min when N > H*N_min. The GPU does all per-pixel and per-seed work; the
 // host reads back a few counters per call.
+#include <atomic>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -24,6 +25,19 @@ ms_status set_error(ms_status code, const char* fmt, ...) {
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
     return code;
+}
+
+static std::atomic<int32_t> g_fail_allocs{0};
+
+cudaError_t workspace_malloc(void** p, size_t bytes) {
+    int32_t left = g_fail_allocs.load();
+    while (left > 0 && !g_fail_allocs.compare_exchange_weak(left, left - 1)) {
+    }
+    if (left > 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
 }
 
 ms_status cuda_check(cudaError_t e, const char* what) {
@@ -116,6 +130,7 @@ ms_status validate(const ms_config* c) {
     if (c->precision == MS_BF16 && c->dim > 16)
         return set_error(MS_ERR_INVALID_ARG, "the BF16 tensor-core form supports dim <= 16");
     if (c->max_rounds < 1) return set_error(MS_ERR_INVALID_ARG, "max_rounds must be >= 1");
+    if (c->batch_max_passes < 0) return set_error(MS_ERR_INVALID_ARG, "batch_max_passes must be >= 0");
     return MS_OK;
 }
 
@@ -196,6 +211,8 @@ void free_ctx(ms_ctx* ctx) {
 
 using namespace ms;
 
+extern "C" void ms_inject_alloc_failure(int32_t count) { g_fail_allocs.store(count > 0 ? count : 0); }
+
 extern "C" {
 
 void ms_config_default(ms_config* c) {
@@ -257,7 +274,7 @@ ms_status ms_create(const ms_config* cfg, const float* d_emb, const uint8_t* d_m
     ctx->target_items = 2 * ctx->shift_grid;
     const Layout L = plan(n_pixels, ctx->Dp, ctx->target_items, cfg->precision == MS_BF16);
     ctx->ws_bytes = L.total;
-    cudaError_t e = cudaMalloc(&ctx->ws, L.total);
+    cudaError_t e = workspace_malloc(&ctx->ws, L.total);
     if (e != cudaSuccess) {
         free_ctx(ctx);
         return cuda_check(e, "cudaMalloc(workspace)");

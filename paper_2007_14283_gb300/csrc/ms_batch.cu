@@ -87,7 +87,7 @@ constexpr int kIT = 1024;   // ingest / selection threads
 constexpr int kMT = 128;    // merge threads
 constexpr int kVT = 64;     // vectors per shared tile
 constexpr int kPT = 256;    // pixel threads (cover, label)
-constexpr int kMaxPasses = 200000;  // loop guard: far above any real run (rounds x iterations)
+constexpr int kDefaultMaxPasses = 200000;  // loop guard: far above any real run (rounds x iterations)
 
 enum BlockSel { kSelDoneSeeds = 0, kSelDoneCands = 1, kSelDonePixels = 2, kSelAllPixels = 3 };
 
@@ -981,12 +981,13 @@ __global__ void k_b_tick(int* misc, const int32_t* __restrict__ item_total, int 
     }
 }
 
-__global__ void k_b_cond(const BState* __restrict__ states, int B, int* misc, cudaGraphConditionalHandle h) {
+__global__ void k_b_cond(const BState* __restrict__ states, int B, int* misc, int max_passes,
+                         cudaGraphConditionalHandle h) {
     if (threadIdx.x != 0) return;
     int live = 0;
     for (int f = 0; f < B; ++f) live += states[f].phase != kFinished;
     const int passes = ++misc[0];
-    if (passes >= kMaxPasses && live) misc[1] |= 2;
+    if (passes >= max_passes && live) misc[1] |= 2;
     if (misc[1] != 0) live = 0;  // bad input or a bounded wait gave up: stop, the host reports it
     cudaGraphSetConditional(h, live ? 1u : 0u);
 }
@@ -1127,7 +1128,8 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
                                                  b->cfg.all_seeds);
     LAUNCHED("k_b_schedule");
     if (with_cond) {
-        k_b_cond<<<1, 32, 0, s>>>(b->states, B, b->misc, h);
+        k_b_cond<<<1, 32, 0, s>>>(b->states, B, b->misc,
+                                  b->cfg.batch_max_passes > 0 ? b->cfg.batch_max_passes : kDefaultMaxPasses, h);
         LAUNCHED("k_b_cond");
     }
 #undef LAUNCHED
@@ -1328,7 +1330,7 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
         offs[i] = tot;
         tot += (sizes[i] + 255) / 256 * 256;
     }
-    cudaError_t e = cudaMalloc(&b->ws, tot);
+    cudaError_t e = workspace_malloc(&b->ws, tot);
     if (e != cudaSuccess) {
         free_batch(b);
         return cuda_check(e, "cudaMalloc(batch workspace)");

@@ -149,6 +149,9 @@ namespace ms {
 // Error plumbing (ms_api.cu).
 ms_status set_error(ms_status code, const char* fmt, ...);
 ms_status cuda_check(cudaError_t e, const char* what);
+// cudaMalloc of a context's or batch's workspace, failing first when a test
+// asked for it through ms_inject_alloc_failure (ms_api.cu).
+cudaError_t workspace_malloc(void** p, size_t bytes);
 #define MS_CUDA(call)                                                 \
     do {                                                              \
         ms_status _s = ::ms::cuda_check((call), #call);               \

@@ -8,6 +8,7 @@
 // pixels, fixed-point accumulators, active list, counters) in one file-scope
 // device array of fixed size. Every GPU that loads the library holds that
 // array until the process exits; all calls on a device share it.
+#include <cstddef>
 #include <mutex>
 
 #include "ms_internal.cuh"
@@ -75,10 +76,16 @@ __global__ void k_static_prepare(const float* __restrict__ P, int n, int m, unsi
     }
 }
 
+// Copy the accumulators out. When the prepare step met a pixel of zero or
+// non-finite norm, every row instead reads sums 0 and count -1, so a caller
+// that cannot synchronise inside the call still sees the error in its output.
 __global__ void k_static_copy_out(int m, const unsigned char* scratch, int64_t* __restrict__ out) {
     const unsigned long long* acc = reinterpret_cast<const unsigned long long*>(scratch + kOffAcc);
+    const DevCounters* dc = reinterpret_cast<const DevCounters*>(scratch + kOffCounters);
+    const bool bad = dc->status != 0;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m * (kStaticDim + 1)) out[i] = (int64_t)acc[i];
+    if (i < m * (kStaticDim + 1))
+        out[i] = bad ? ((i % (kStaticDim + 1)) == kStaticDim ? -1 : 0) : (int64_t)acc[i];
 }
 
 }  // namespace
@@ -101,6 +108,8 @@ extern "C" ms_status ms_window_sums_static(const float* d_X, int32_t m, const fl
     if (s != MS_OK) return s;
     unsigned char* scratch = static_cast<unsigned char*>(base);
     cudaStream_t st = (cudaStream_t)stream;
+    // the error flag starts clear on every call (the array keeps the last call's contents)
+    MS_CUDA(cudaMemsetAsync(scratch + kOffCounters + offsetof(DevCounters, status), 0, sizeof(int32_t), st));
     const int threads = 256;
     const int items = n > m ? n : m;
     k_static_prepare<<<(items + threads - 1) / threads, threads, 0, st>>>(d_P, n, m, scratch);

@@ -3,8 +3,15 @@ benchmark times.
 
 C2 (one 512x512 frame, 131072 foreground pixels): the oracle needs about a
 minute per frame, so its counters for synth.frame_c2(seed=0) are stored in
-tests/golden/c2_oracle_stats.json (written by a committed script that calls
-only oracle/ and synth/). Every integer counter of the GPU run -- rounds, kept
+tests/golden/c2_oracle_stats.json and its kept modes, label map and seed log
+in tests/golden/c2_oracle_result.npz (both written by committed scripts that
+call only oracle/ and synth/). The GPU's modes must equal the oracle's in
+count and keep order, each within 1 - cos <= 1e-5; its labels must equal the
+oracle's on every pixel whose oracle top-two margin clears both 1e-5 and
+twice the modes' largest direction error, and on at least 99.9% of all
+pixels; the seed log must be the oracle's. This holds for the FP32 form, the
+BF16 form and the BF16-batched graph with the work split its autotuner picks
+(the benchmark's launch configuration), and for the C3 stack. Every integer counter of the GPU run -- rounds, kept
 modes, seeds, seed-iterations, candidates, dropped seeds, iterations -- must
 equal the oracle's where the method fixes it: rounds, kept modes and seeds
 (which follow from the modes through coverage) exactly -- seeds within 0.01%
@@ -93,14 +100,19 @@ def _sampled_checks(f, labels, modes, seed_pixels, c=0.9, n_samples=3000, seed=0
     seeded = np.zeros(len(fg), dtype=bool)
     seeded[seed_pixels] = True
     assert np.all((top[:, -1] >= c - 1e-6) | seeded[idx])
-    # modes are fixed points of the FP64 update over their FP64 window (a pixel
-    # within FP32 rounding of the boundary can fall on the other side in FP64)
-    errs = []
-    for j in rng.choice(len(M), size=min(32, len(M)), replace=False):
-        y = P[P @ M[j] >= c].sum(0)
+    # modes are fixed points of the FP64 update over their FP64 window, to the
+    # modes' 1e-5 bar; excused only is a mode whose window has a pixel within
+    # FP32 rounding of the boundary (such a pixel can fall on either side)
+    errs, excused = [], 0
+    for j in rng.choice(len(M), size=min(64, len(M)), replace=False):
+        s = P @ M[j]
+        if np.any(np.abs(s - c) < 2e-6):
+            excused += 1
+            continue
+        y = P[s >= c].sum(0)
         errs.append(1.0 - float(y @ M[j]) / np.linalg.norm(y))
     errs = np.array(errs)
-    assert errs.max() <= 1e-3 and (errs <= 1e-6).mean() >= 0.9, errs
+    assert excused <= 8 and errs.max() <= 1e-5, (excused, errs.max())
 
 
 def _full_label_check(f, labels, modes, margin=1e-12):
@@ -121,6 +133,62 @@ def _full_label_check(f, labels, modes, margin=1e-12):
         clear = (top[:, 1] - top[:, 0]) > margin if S.shape[1] > 1 else np.ones(len(S), bool)
         assert np.array_equal(want[clear], lab[a:a + 16384][clear]), a
     assert np.all(labels[np.setdiff1d(np.arange(labels.size), fg)] == -1)
+
+
+def _oracle_result(name):
+    path = os.path.join(GOLDEN, f"{name}_oracle_result.npz")
+    if not os.path.exists(path):
+        pytest.skip(f"{name}_oracle_result.npz not present")
+    return dict(np.load(path))
+
+
+def _fg_unit(f):
+    fg = np.flatnonzero(f.mask) if f.mask is not None else np.arange(f.emb.shape[0])
+    P = f.emb[fg].astype(np.float64)
+    return fg, P / np.linalg.norm(P, axis=1, keepdims=True)
+
+
+def _top_two_margin(P, M):
+    """Per pixel, FP64 top-1 minus top-2 cosine over the modes M."""
+    Mn = M / np.linalg.norm(M, axis=1, keepdims=True)
+    out = np.empty(P.shape[0])
+    for a in range(0, P.shape[0], 16384):
+        S = P[a:a + 16384] @ Mn.T
+        top = np.partition(S, -2, axis=1)[:, -2:] if S.shape[1] > 1 else np.concatenate([S - 2, S], axis=1)
+        out[a:a + 16384] = top[:, 1] - top[:, 0]
+    return out
+
+
+def _equal_to_oracle(f, ref, labels, modes, seed_log=None, exact_seeds=True):
+    """Element-by-element parity with the oracle's stored result (Algorithm 2,
+    lines 10-12: every vector labelled by its nearest kept mode)."""
+    from parity_util import same_order_errors
+    K = ref["modes"].shape[0]
+    assert modes.shape[0] == K, (modes.shape[0], K)
+    err = same_order_errors(modes, ref["modes"])
+    assert err.max() <= 1e-5, err.max()
+    # a direction error delta moves any cosine by at most delta, and 1 - cos = delta^2 / 2
+    delta = float(np.sqrt(2.0 * max(err.max(), 0.0)))
+    fg, P = _fg_unit(f)
+    bg = np.setdiff1d(np.arange(labels.size), fg)
+    assert np.all(labels[bg] == -1) and np.all(ref["labels"][bg] == -1)
+    want, got = ref["labels"][fg], labels[fg]
+    if 2 * delta <= ref["safe_margin"]:
+        safe = np.unpackbits(ref["margin_gt"])[: ref["labels"].size].astype(bool)[fg]
+    else:
+        safe = _top_two_margin(P, ref["modes"]) > 2 * delta
+    assert safe.mean() > 0.99, safe.mean()
+    bad = np.flatnonzero(safe & (want != got))
+    assert bad.size == 0, (bad.size, bad[:10])
+    assert (want == got).mean() >= 0.999, (want == got).mean()
+    if seed_log is not None:
+        if exact_seeds:
+            assert np.array_equal(np.asarray(seed_log), ref["seed_log"])
+        else:
+            n = min(len(seed_log), len(ref["seed_log"]))
+            assert abs(len(seed_log) - len(ref["seed_log"])) <= max(2, len(ref["seed_log"]) // 10000)
+            assert (np.asarray(seed_log)[:n] == ref["seed_log"][:n]).mean() >= 0.999
+    return err.max()
 
 
 def _label_agreement(a, b, modes_a, modes_b):
@@ -220,3 +288,46 @@ def test_c3_tracking_stack_counters_equal_oracle(ms_lib):
     res = ms_lib.cluster(e, m, precision=ms_lib.MS_BF16)
     _counters_match_oracle(res.stats, ref)
     _sampled_checks(f, res.labels.cpu().numpy(), res.modes.cpu().numpy(), res.stats["seed_log"])
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_c2_full_frame_modes_and_labels_equal_oracle(ms_lib, bf16):
+    ref = _oracle_result("c2")
+    st = _golden("c2_oracle_stats.json")
+    f = synth.frame_c2(seed=0)
+    e, m = _dev(f)
+    res = ms_lib.cluster(e, m, precision=ms_lib.MS_BF16 if bf16 else ms_lib.MS_FP32)
+    _equal_to_oracle(f, ref, res.labels.cpu().numpy(), res.modes.cpu().numpy(), res.stats["seed_log"],
+                     exact_seeds=st["min_cover_margin"] > 1e-6)
+    assert np.array_equal(res.stats["round_log"], ref["round_log"])
+
+
+def test_c2_batched_autotuned_modes_and_labels_equal_oracle(ms_lib):
+    """The benchmark's launch configuration (BF16, C2 frames in one graph, the
+    work split the autotuner keeps), frame 0 against the oracle."""
+    import torch
+    ref = _oracle_result("c2")
+    fs = [synth.frame_c2(seed=i) for i in range(4)]
+    embs = [torch.from_numpy(f.emb).cuda() for f in fs]
+    masks = [torch.from_numpy(f.mask).cuda() for f in fs]
+    c = ms_lib.ms_config_default(dim=16, precision=ms_lib.MS_BF16)
+    b = ms_lib.ms_batch_create(c, embs, masks)
+    try:
+        ms_lib.ms_batch_autotune(b, reps=1)
+        _equal_to_oracle(fs[0], ref, b.labels[0].cpu().numpy(), ms_lib.ms_batch_modes(b, 0))
+        st = ms_lib.ms_batch_stats(b, 0)
+        assert st["n_modes"] == ref["modes"].shape[0] and st["rounds"] == ref["round_log"].shape[0]
+    finally:
+        b.close()
+
+
+def test_c3_stack_modes_and_labels_equal_oracle(ms_lib):
+    ref = _oracle_result("c3")
+    st = _golden("c3_oracle_stats.json")
+    f = synth.stack_c3(seed=0)
+    e, m = _dev(f)
+    res = ms_lib.cluster(e, m, precision=ms_lib.MS_BF16)
+    # the oracle saw a pixel within tol of the coverage boundary, so the seed
+    # log may differ by a seed where the FP32 modes cover it and FP64's do not
+    _equal_to_oracle(f, ref, res.labels.cpu().numpy(), res.modes.cpu().numpy(), res.stats["seed_log"],
+                     exact_seeds=st["min_cover_margin"] > 1e-6)

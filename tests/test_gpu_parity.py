@@ -1,7 +1,8 @@
 """GPU parity: the CUDA library against the FP64 oracle through the C ABI.
 
-Tolerances (stated here, derived in the design doc):
-  * modes: 1 - cos(gpu, oracle) <= 1e-5 (FP32 state, FP64 convergence norm)
+Tolerances:
+  * modes: 1 - cos(gpu, oracle) <= 1e-5 (the GPU keeps seeds in FP32 and
+    tests convergence in FP64; a direction error delta costs delta^2 / 2)
   * labels: >= 99.9% identical after optimal cluster matching; bit-identical
     integer maps when both sides kept the same modes in the same order, on
     every pixel whose oracle top-1/top-2 margin exceeds 1e-5

@@ -5,11 +5,16 @@ device, no cudaMalloc while a stream is captured, a plugin handed only its
 input and output buffers) use this entry point; its scratch is a fixed static
 device array. It must agree with ms_tc_selftest, the existing entry point that
 returns the same per-seed window sums and window sizes, on two calls in a row
-(the second with other inputs and sizes, so stale scratch would show).
+(the second with other inputs and sizes, so stale scratch would show), and
+its window sizes and sum directions must equal the FP64 oracle's window
+(Eq. 11) and update (Eq. 8) for every seed whose window has no pixel within
+1e-5 of the bandwidth. A pixel of zero norm must show in the output (count
+-1 on every row) without leaving the shared scratch in an error state.
 """
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -54,3 +59,41 @@ def test_static_window_sums_reject_sizes_beyond_the_scratch(ms_lib):
     with pytest.raises(ms_lib.MsError) as e:
         ms_lib.ms_window_sums_static(X[:4], P, out[:4])
     assert e.value.status == ms_lib.MS_ERR_INVALID_ARG
+
+
+def test_static_window_sums_match_the_oracle(ms_lib):
+    import torch
+    X, P = _inputs(3, 1000)
+    out = torch.empty((128, 17), dtype=torch.int64, device="cuda")
+    ms_lib.ms_window_sums_static(torch.from_numpy(X).cuda(), torch.from_numpy(P).cuda(), out, 0.9)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    Pn, pn, _ = oracle.normalize(P)
+    checked = 0
+    for r in range(128):
+        xn, cnt, margin = oracle.shift_step(Pn, pn, X[r].astype(np.float64), 0.9)
+        if margin <= 1e-5:
+            continue
+        checked += 1
+        assert got[r, 16] == cnt, r
+        y = got[r, :16].astype(np.float64)
+        assert 1.0 - float(y @ xn) / np.linalg.norm(y) <= 1e-6, r
+    assert checked >= 100
+
+
+def test_static_window_sums_flag_a_zero_norm_pixel_then_recover(ms_lib):
+    import torch
+    X, P = _inputs(4, 400)
+    Xd = torch.from_numpy(X).cuda()
+    bad = P.copy()
+    bad[123] = 0.0
+    out = torch.zeros((128, 17), dtype=torch.int64, device="cuda")
+    ms_lib.ms_window_sums_static(Xd, torch.from_numpy(bad).cuda(), out, 0.9)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert np.all(got[:, 16] == -1) and np.all(got[:, :16] == 0)
+    Pd = torch.from_numpy(P).cuda()
+    ms_lib.ms_window_sums_static(Xd, Pd, out, 0.9)
+    torch.cuda.synchronize()
+    _, ref = ms_lib.ms_tc_selftest(Xd, Pd, 0.9)
+    assert np.array_equal(out.cpu().numpy()[:, 16], ref[:, 16])

@@ -12,7 +12,10 @@
 //          dot product as the FP32 form, against the pixel's exact FP32 value
 //          rebuilt from its BF16 parts in the shared-memory tile, so every
 //          decision equals the FP32 form's, whose dot product is within 1e-6
-//          of x.p.
+//          of x.p. Whether a warp holds such a pair comes with the TMEM load
+//          of S' (tcgen05.ld.red min.abs: each lane's smallest |S'|), so the
+//          mask costs a byte permute and a logic op per two pixels and nothing
+//          else.
 //   GEMM2  Y += Mask . [Ph | Pm | Pl | 1]    (8 tcgen05 MMAs, mask exact in BF16;
 //          the ones column yields the window size)
 // The seed-by-pixel matrix lives only in TMEM and registers. After the item's last tile the Y sums are added to the per-seed
@@ -351,7 +354,7 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
         const int r = q * 32 + lane;              // seed row
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         long long band_local = 0;
-        int g = 0, it = 0;
+        int g = 0, it = 0, mb = 0, mph = 0;       // mask buffer and its phase, without divisions
         float x[16];
         for (int item = blockIdx.x; item < items; item += gridDim.x, ++it) {
             if (__any_sync(0xffffffffu, *abort)) break;
@@ -387,23 +390,22 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                 if (!(ok = warp_wait(&s_full[b], (g >> 1) & 1, abort))) break;
                 tc_fence_after();
                 uint32_t v[kSub][32];
+                float mnj[kSub];
 #pragma unroll
                 for (int j = 0; j < kSub; ++j)
-                    tmem_ld32(tmem + kColS + b * 128 + lane_base + h * kPxPerWarp + j * 32, v[j]);
+                    tmem_ld32_minabs(tmem + kColS + b * 128 + lane_base + h * kPxPerWarp + j * 32, v[j], &mnj[j]);
                 tmem_ld_wait();
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&s_empty[b]);
                 uint32_t w[kSub][16];
-                float mn = INFINITY;
+                float mn = mnj[0];
+#pragma unroll
+                for (int j = 1; j < kSub; ++j) mn = fminf(mn, mnj[j]);
 #pragma unroll
                 for (int j = 0; j < kSub; ++j)
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        w[j][i] = ~sign_halves(v[j][2 * i], v[j][2 * i + 1]) & 0x3F803F80u;
-                        mn = fminf(mn, fminf(fabsf(__uint_as_float(v[j][2 * i])),
-                                             fabsf(__uint_as_float(v[j][2 * i + 1]))));
-                    }
+                    for (int i = 0; i < 16; ++i) w[j][i] = ~sign_halves(v[j][2 * i], v[j][2 * i + 1]) & 0x3F803F80u;
                 if (__any_sync(0xffffffffu, mn < kBand)) {
                     // Re-decide near-boundary pairs with the FP32 form's dot
                     // product against the exact FP32 pixel rebuilt from the
@@ -447,8 +449,7 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                             dbg_S[(int64_t)r * dbg_stride + pt * 128 + h * kPxPerWarp + j * 32 + i] =
                                 __uint_as_float(v[j][i]);
                 }
-                const int mb = g % kMBufs;
-                if (g >= kMBufs && !(ok = warp_wait(&m_empty[mb], ((g / kMBufs) - 1) & 1, abort))) break;
+                if (g >= kMBufs && !(ok = warp_wait(&m_empty[mb], mph ^ 1, abort))) break;
                 tc_fence_after();
 #pragma unroll
                 for (int j = 0; j < kSub; ++j)
@@ -457,6 +458,10 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&m_full[mb]);
+                if (++mb == kMBufs) {
+                    mb = 0;
+                    mph ^= 1;
+                }
             }
             if (!ok) break;
             if (h == 0) {
@@ -493,12 +498,14 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
 }
 
 // Pixels as BF16 splits for the tensor cores: row i = [Ph | Pm | Pl | 1 1 1 0..0]
-// (64 values, 128 bytes) with p = Ph + Pm + Pl; padding rows n..n_pad-1 hold
-// only the ones, so they score S' = -c and never enter a window.
-__global__ void k_pack_bf16(const float* __restrict__ P32, int n, int n_pad, uint4* __restrict__ Pk) {
+// (64 values, 128 bytes) with p = Ph + Pm + Pl; rows from the foreground count
+// n (read on the device) up to `rows` hold only the ones, so they score
+// S' = -c and never enter a window.
+__global__ void k_pack_bf16(const float* __restrict__ P32, const DevCounters* __restrict__ dc, int rows,
+                            uint4* __restrict__ Pk) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_pad) return;
-    pack_split_row(i < n ? P32 + (int64_t)i * 16 : nullptr, Pk + (int64_t)i * 8);
+    if (i >= rows) return;
+    pack_split_row(i < dc->n_fg ? P32 + (int64_t)i * 16 : nullptr, Pk + (int64_t)i * 8);
 }
 
 ms_status encode_pmap(void* Pk, int n_pad, CUtensorMap* map) {
@@ -526,12 +533,16 @@ ms_status encode_pmap(void* Pk, int n_pad, CUtensorMap* map) {
 
 int tc_smem_bytes() { return kSmemBytes; }
 
-ms_status tc_prepare(ms_ctx* ctx) {
-    if (ctx->n_pad == 0) return MS_OK;
-    k_pack_bf16<<<(unsigned)((ctx->n_pad + 255) / 256), 256, 0, ctx->stream>>>(ctx->P32, (int)ctx->n,
-                                                                              (int)ctx->n_pad, (uint4*)ctx->Pk);
+ms_status tc_pack_async(ms_ctx* ctx) {
+    const int rows = (int)((ctx->n_pixels + 127) / 128 * 128);
+    if (rows == 0) return MS_OK;
+    k_pack_bf16<<<(unsigned)((rows + 255) / 256), 256, 0, ctx->stream>>>(ctx->P32, ctx->dc, rows, (uint4*)ctx->Pk);
     MS_LAUNCH("k_pack_bf16");
     ctx->launches += 1;
+    return MS_OK;
+}
+
+ms_status tc_finish(ms_ctx* ctx) {
     MS_CUDA(cudaFuncSetAttribute(k_shift_tc<false, TcSingleMap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSmemBytes));
     MS_CUDA(cudaFuncSetAttribute(k_shift_tc<true, TcSingleMap>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -38,14 +38,14 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
-// Non-blocking test of a phase's completion. Waiters poll it: a suspending
-// try_wait measured slower to notice completed phases in the pipelined
-// kernels, whose waits are short.
+// Test of a phase's completion that may suspend the warp for a while (the
+// hardware's time limit) instead of returning at once: waiters spend fewer
+// issue slots polling, which the warps sharing their sub-partition use.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)
@@ -116,6 +116,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
           "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
           "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+// tmem_ld32 that also reduces: *min_abs = min over the 32 loaded columns of
+// |value| (per thread, i.e. per TMEM lane), computed by the load itself.
+__device__ __forceinline__ void tmem_ld32_minabs(uint32_t taddr, uint32_t (&r)[32], float* min_abs) {
+    asm volatile(
+        "tcgen05.ld.red.sync.aligned.32x32b.x32.min.abs.f32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+        "%32, [%33];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+          "=r"(r[30]), "=r"(r[31]), "=f"(*min_abs)
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -217,7 +231,8 @@ __device__ __forceinline__ float bf16_round(float x) {
 // One 128-byte row of a BF16 split operand for a unit vector v (16 FP32
 // components, or nullptr for a padding row): [vh | vm | vl | 1 1 1 0..0], where
 // vh = RN(v), vm = RN(v - vh), vl = (v - vh) - vm, so v = vh + vm + vl exactly
-// (|v_k| >= 2^-100 or 0). The ones give a -c column against a split constant.
+// (|v_k| >= 2^-100 or 0). The ones give a -c column against a split constant
+// and the shift's window size in its second GEMM.
 __device__ __forceinline__ void pack_split_row(const float* v, uint4* row) {
     uint32_t w[32];
 #pragma unroll

@@ -60,14 +60,23 @@ def parse():
     ap.add_argument("--cpu", choices=["full", "sample", "none"], default="full",
                     help="oracle baseline: one full frame (also gives the label match), a seed sample, or none")
     ap.add_argument("--cpu-seeds", type=int, default=8192, help="seeds in the oracle's sampled run")
+    ap.add_argument("--cpu-runs", type=int, default=3,
+                    help="--cpu full: also the median of this many sampled runs and a one-core run (0: none)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-vmf", action="store_true", help="skip the smooth-kernel (vMF) forward/adjoint leg")
+    ap.add_argument("--video-frames", type=int, default=16,
+                    help="frames of the video-form leg (drifting 512x512 sequence; 0 skips it)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched forms: skip the work-split autotuner (keep the canonical split)")
     ap.add_argument("--eager", action="store_true",
                     help="batched forms: issue the graph's kernels as plain launches (for profilers)")
     ap.add_argument("--shift-only", type=int, default=0, metavar="SEEDS",
                     help="time one shift iteration of SEEDS seeds on frame 0 (fp32 or bf16 form) and exit")
+    ap.add_argument("--suite", action="store_true",
+                    help="the paper's simulation suite (Table 1 sizes, Appendix A overlap, Tables 3-4) and exit")
+    ap.add_argument("--volume", action="store_true", help="one 3D volume (128x256x256 voxels) and exit")
+    ap.add_argument("--vmf-only", action="store_true",
+                    help="time only the smooth-kernel forward and adjoint (differentiable configuration) and exit")
     return ap.parse_args()
 
 
@@ -211,6 +220,19 @@ def oracle_sample(frame, n_seeds):
     t0 = time.perf_counter()
     r = oracle.shift_round(P, pn, X0, gamma=0.9)
     return time.perf_counter() - t0, r["seed_iters"]
+
+
+def oracle_sample_single_core(n_seeds):
+    """The same bounded sample timed on one host core: a child process with
+    OMP_NUM_THREADS=1 (the oracle's OpenMP team size is fixed when it loads).
+    Returns (seconds, seed-iterations)."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "f = bench.c2_frames(0, 1)[0]; dt, si = bench.oracle_sample(f, %d); "
+            "print(json.dumps([dt, si]))" % (ROOT, n_seeds))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    dt, si = json.loads(out.stdout.strip().splitlines()[-1])
+    return dt, si
 
 
 def label_match(gpu_labels, ref_labels, gpu_modes, ref_modes):
@@ -458,6 +480,185 @@ def vmf_leg(n_sm, clk):
             "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz (nominal CUDA-core rate)"}
 
 
+def video_leg(n_frames=16):
+    """Video form on a drifting 512x512 sequence (the C2 frame recipe; cell means
+    drift 0.02 rad per frame): BF16, the seed count N carried from frame to
+    frame and the next frame bound on a second stream (ms_video_run), against
+    the same frames clustered independently (ms_create + ms_run, N restarting at
+    N_initial). Frames/s from CUDA events on the stream, after one warm-up pass."""
+    import torch
+
+    import paper_2007_14283_gb300 as ms
+    import synth
+    fs = synth.video_sequence(seed=11, T=n_frames)
+    embs = [torch.from_numpy(f.emb).cuda() for f in fs]
+    masks = [torch.from_numpy(f.mask).cuda() for f in fs]
+    labels = [torch.empty(f.emb.shape[0], dtype=torch.int32, device="cuda") for f in fs]
+    cfg = ms.ms_config_default(dim=DIM, precision=ms.MS_BF16)
+    stream = torch.cuda.current_stream()
+
+    def timed_s(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, out
+
+    def video():
+        with ms.ms_video_create(cfg, max(f.emb.shape[0] for f in fs)) as v:
+            _, n_start, n_modes = ms.ms_video_run(v, embs, masks, labels)
+        return n_start, n_modes
+
+    def independent():
+        for t, (e, m, lab) in enumerate(zip(embs, masks, labels)):
+            c = ms.ms_config_default(dim=DIM, precision=ms.MS_BF16, frame_id=t)
+            ctx = ms.ms_create(c, e, m)
+            try:
+                ms.ms_run(ctx, lab)
+            finally:
+                ctx.close()
+    tv, (n_start, n_modes) = timed_s(video)
+    ti, _ = timed_s(independent)
+    return {"config": f"{n_frames} consecutive 512x512 frames (131072 foreground px, 60 cells drifting 0.02 rad "
+                      "per frame), BF16 single-frame form",
+            "video_frames_per_s": n_frames / tv, "independent_frames_per_s": n_frames / ti,
+            "n_start": n_start, "modes_per_frame": sum(n_modes) / max(1, len(n_modes)),
+            "api": "ms_video_run (N carried, next frame bound on a second stream) vs ms_create + ms_run per frame"}
+
+
+PAPER_TABLE1_OURS_S = {1000: 1.624, 2000: 1.618, 5000: 1.664, 10000: 1.698, 20000: 1.747, 50000: 1.892,
+                       100000: 2.107, 200000: 2.692}  # Table 1, "Ours" (half a Tesla K80), context only
+
+
+def _cluster_timed(ms, emb, mask, reps=3, **cfg):
+    """Median seconds of ms_create + ms_run on device-resident inputs (CUDA
+    events, after one warm-up), with the last run's labels, modes and counters."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ts, res = [], None
+    for r in range(reps + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = ms.cluster(emb, mask, **cfg)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r:
+            ts.append(e0.elapsed_time(e1) / 1e3)
+    return statistics.median(ts), res
+
+
+def run_suite(args):
+    """The paper's simulation suite on synthetic inputs (Sec. 4.2 Table 1,
+    Appendix A, Sec. 4.3 Tables 3-4), one JSON line.
+
+    table1: n = 1K..200K points, 18-d, 10 orthogonal/opposite blob clusters,
+      sigma = 0.01, h = 0.1 (c = 0.9): GPU seconds per frame (FP32 form; d = 18)
+      and workspace MB beside the paper's own "Ours" row, the oracle's seconds on
+      the host cores up to 20K points, and label agreement with the truth.
+    appendix_a: 1000 x 1000 x 18 frames of 8 discs (diameter 250) at growing
+      overlap, P = 0.95, L = 2, H = 8: modes found, label agreement with the
+      truth, rounds, seeds, seconds.
+    tables_3_4: a drifting 512 x 512 sequence through the video form (N carried
+      across frames) with N_initial in {64, 128, 256} and H in {4, 8, 16}:
+      seconds per frame."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2007_14283_gb300 as ms
+    import synth
+    from tests.parity_util import matched_agreement
+    ms.load()
+    torch.cuda.set_device(0)
+    out = {"suite": True}
+    rows = []
+    for n in (1000, 2000, 5000, 10000, 20000, 50000, 100000, 200000):
+        emb, truth = synth.orthogonal_blobs(seed=n, n=n, d=18, K=10, sigma=0.01)
+        e = torch.from_numpy(emb).cuda()
+        t, res = _cluster_timed(ms, e, None, precision=ms.MS_FP32)
+        lab = res.labels.cpu().numpy()
+        row = {"n": n, "gpu_s": t, "gpu_workspace_mb": res.stats["workspace_bytes"] / 2 ** 20,
+               "modes": res.stats["n_modes"], "label_agreement_truth": matched_agreement(truth, lab),
+               "paper_ours_s": PAPER_TABLE1_OURS_S[n]}
+        if n <= 20000:
+            t0 = time.perf_counter()
+            ref = oracle.run(emb)
+            row["oracle_s"] = time.perf_counter() - t0
+            row["labels_equal_oracle"] = bool(np.array_equal(ref.labels, lab))
+        rows.append(row)
+    out["table1"] = {"rows": rows, "cores": host_threads(),
+                     "data": "synth.orthogonal_blobs: 18-d, 10 clusters at +/- e_j, sigma 0.01"}
+    arows = []
+    for ov in (0.0, 0.1, 0.2, 0.3):
+        f = synth.overlap_discs(seed=1, overlap=ov)
+        e, m = torch.from_numpy(f.emb).cuda(), torch.from_numpy(f.mask).cuda()
+        t, res = _cluster_timed(ms, e, m, reps=1, precision=ms.MS_FP32, P_target=0.95)
+        fg = f.mask.astype(bool)
+        arows.append({"overlap": ov, "fg_fraction": f.info["fg_fraction"], "modes": res.stats["n_modes"],
+                      "label_agreement_truth": matched_agreement(f.truth[fg], res.labels.cpu().numpy()[fg]),
+                      "rounds": res.stats["rounds"], "seeds": res.stats["seeds"], "gpu_s": t})
+    out["appendix_a"] = {"rows": arows, "config": "1000x1000x18, 8 discs of diameter 250, no noise, P = 0.95"}
+    fs = synth.video_sequence(seed=21, T=8)
+    embs = [torch.from_numpy(f.emb).cuda() for f in fs]
+    masks = [torch.from_numpy(f.mask).cuda() for f in fs]
+    ab = []
+    for key, vals in (("n_initial", (64, 128, 256)), ("H", (4.0, 8.0, 16.0))):
+        for val in vals:
+            cfg = ms.ms_config_default(dim=DIM, precision=ms.MS_BF16, **{key: val})
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with ms.ms_video_create(cfg, max(f.emb.shape[0] for f in fs)) as v:
+                _, n_start, n_modes = ms.ms_video_run(v, embs, masks)
+            torch.cuda.synchronize()
+            ab.append({key: val, "s_per_frame": (time.perf_counter() - t0) / len(fs), "n_start": n_start,
+                       "modes_per_frame": sum(n_modes) / len(n_modes)})
+    out["tables_3_4"] = {"rows": ab, "config": "8 consecutive 512x512 frames (C2 recipe, 0.02 rad drift), "
+                                               "video form, BF16"}
+    print(json.dumps(out), flush=True)
+
+
+def run_volume(args):
+    """3D volume (the paper's stated 2D limitation, Sec. 5.3): 128 x 256 x 256
+    voxels, half foreground (4.19M vectors), 400 ellipsoidal vMF cells, BF16
+    single-frame form. Seconds per volume (CUDA events) and sampled checks:
+    labels are the FP64 argmax over the GPU's modes, every sampled voxel is
+    covered, modes are fixed points."""
+    import numpy as np
+    import torch
+
+    import paper_2007_14283_gb300 as ms
+    import synth
+    ms.load()
+    torch.cuda.set_device(0)
+    f = synth.volume(seed=0)
+    e, m = torch.from_numpy(f.emb).cuda(), torch.from_numpy(f.mask).cuda()
+    t, res = _cluster_timed(ms, e, m, reps=1, precision=ms.MS_BF16)
+    st = res.stats
+    fg = np.flatnonzero(f.mask)
+    rng = np.random.default_rng(0)
+    idx = rng.choice(fg, size=2000, replace=False)
+    P = f.emb[idx].astype(np.float64)
+    P /= np.linalg.norm(P, axis=1, keepdims=True)
+    M = res.modes.cpu().numpy().astype(np.float64)
+    M /= np.linalg.norm(M, axis=1, keepdims=True)
+    S = P @ M.T
+    lab = res.labels.cpu().numpy()[idx]
+    top = np.sort(S, axis=1)
+    safe = top[:, -1] - top[:, -2] > 1e-5
+    out = {"volume": True, "shape": list(f.info["shape"]), "voxels": int(f.emb.shape[0]), "n_fg": int(fg.size),
+           "gpu_s": t, "seconds_per_mvoxel_fg": t / (fg.size / 1e6), "modes": st["n_modes"],
+           "rounds": st["rounds"], "seeds": st["seeds"], "seed_iters": st["seed_iters"],
+           "workspace_gb": st["workspace_bytes"] / 2 ** 30,
+           "sampled_labels_equal_fp64_argmax": float((np.argmax(S, axis=1)[safe] == lab[safe]).mean()),
+           "sampled_covered": float((top[:, -1] >= 0.9 - 1e-6).mean())}
+    print(json.dumps(out), flush=True)
+
+
 def e2e_leg(args, runner, ws):
     """Frames/s through the host-buffer entry points (pinned buffers in, labels out)."""
     import torch
@@ -534,6 +735,9 @@ def run_ours(args, rank, ws, local):
     vmf = None
     if rank == 0 and not args.no_vmf:
         vmf = vmf_leg(n_sm, clk)
+    video = None
+    if rank == 0 and args.video_frames > 0:
+        video = video_leg(args.video_frames)
     cpu, parity = None, None
     if rank == 0 and args.cpu != "none":
         import oracle
@@ -545,6 +749,22 @@ def run_ours(args, rank, ws, local):
             cpu = {"value": 1.0 / dt, "unit": "frames/s", "cores": host_threads(), "kind": "oracle",
                    "sample": f"one full frame (frame 0 of the step): every OSOP round, merge, coverage and "
                              f"labelling in FP64, {dt:.1f} s"}
+            per_frame = c2_seed_iters_per_frame()
+            if per_frame and args.cpu_runs > 0:
+                # the bounded seed sample, median of cpu_runs runs on every core and one run on one core
+                rates = []
+                for _ in range(args.cpu_runs):
+                    sdt, ssi = oracle_sample(f0, args.cpu_seeds // 4)
+                    rates.append(1.0 / (sdt / ssi * per_frame))
+                sdt1, ssi1 = oracle_sample_single_core(args.cpu_seeds // 8)
+                cpu["sample_median"] = {
+                    "value": statistics.median(rates), "runs": len(rates), "cores": host_threads(),
+                    "sample": f"{args.cpu_seeds // 4} seeds shifted to the gamma stop, scaled by the oracle's "
+                              f"{int(per_frame)} seed-iterations per frame; merge/cover/label not included"}
+                cpu["single_core"] = {
+                    "value": 1.0 / (sdt1 / ssi1 * per_frame), "cores": 1,
+                    "sample": f"{args.cpu_seeds // 8} seeds ({ssi1} seed-iterations, {sdt1:.1f} s) on one core, "
+                              f"scaled likewise"}
             match, how, err, bg_ok = label_match(main.labels[0].cpu().numpy(), ref.labels, main.modes(0),
                                                  ref.modes)
             parity = {"frame": 0, "label_match": match, "method": how, "mode_err_max": err,
@@ -576,7 +796,8 @@ def run_ours(args, rank, ws, local):
                            "autotune": main.tuning,
                            "fp32_rechecked_pair_fraction": tot.get("band_pairs", 0) /
                            max(1.0, float(tot["seed_iters"]) * N_FG)},
-                "roofline": roofline, "forms": forms, "smooth_kernel": vmf, "parity_vs_oracle": parity,
+                "roofline": roofline, "forms": forms, "smooth_kernel": vmf, "video": video,
+                "parity_vs_oracle": parity,
                 "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": int(reduce_over_ranks(tot["launches"], ws, "sum")), "clocks": clk}
         print(json.dumps(line), flush=True)
@@ -620,6 +841,21 @@ def main():
     args = parse()
     if args.shift_only > 0:
         run_shift_only(args)
+        return
+    if args.suite:
+        run_suite(args)
+        return
+    if args.volume:
+        run_volume(args)
+        return
+    if args.vmf_only:
+        import torch
+
+        import paper_2007_14283_gb300 as ms
+        ms.load()
+        torch.cuda.set_device(0)
+        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+        print(json.dumps({"vmf_only": True, **vmf_leg(n_sm, {})}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args, int(os.environ.get("RANK", "0")))

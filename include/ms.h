@@ -184,8 +184,12 @@ MS_API ms_status ms_profile(ms_ctx* ctx, int32_t enable);
 /* Counters of the context so far. */
 MS_API ms_status ms_stats_get(const ms_ctx* ctx, ms_stats* out);
 
-/* OSOP state carried across frames of a video (Sec. 4.3, Table 3): the seed
- * count N the schedule will use for the next batch. */
+/* OSOP state carried across frames of a video (Sec. 3.2.4; Sec. 4.3, Table 3):
+ * the seed count N that a next frame starts from. It follows the same Eq. 19-21
+ * updates as the frame's own schedule, from the frame's starting N, but is
+ * never clamped to the frame's uncovered pixel count (that clamp only bounds
+ * each draw inside the frame). ms_set_state sets the frame's starting N; it
+ * returns MS_ERR_STATE once the frame's first round has run. */
 MS_API ms_status ms_get_state(const ms_ctx* ctx, int64_t* n_next_out);
 MS_API ms_status ms_set_state(ms_ctx* ctx, int64_t n_next);
 
@@ -266,6 +270,41 @@ MS_API ms_status ms_tc_selftest(const float* d_X, const float* d_P, int32_t n_pi
  * the counts after synchronising). Each call clears that error state. */
 MS_API ms_status ms_window_sums_static(const float* d_X, int32_t m, const float* d_P, int32_t n, double c,
                                        int64_t* d_acc_out, void* stream);
+
+/* Video form (Sec. 3.2.4; Sec. 4.3 and Table 3): the frames of one sequence
+ * clustered in order, each as its own vector set (Algorithm 2), with the seed
+ * count N carried from each frame into the next (the ms_get_state value; the
+ * first frame of the video starts at cfg->n_initial). Frame t of the video
+ * (counting over every ms_video_run call) uses the seed order of frame_id =
+ * cfg->frame_id + t, so its results equal ms_create + ms_set_state(carried N)
+ * + ms_run on that frame with that frame_id.
+ *
+ * ms_video_create allocates two workspaces for frames of up to max_pixels
+ * pixels (0 <= max_pixels < 2^24) and a second, internal stream; cfg as for
+ * ms_create (MS_FLAT, all_seeds = 0). Work runs on `stream` (NULL = legacy
+ * default stream).
+ * ms_video_run clusters T more frames: d_embs[t] device float32
+ * [n_pixels[t], dim], d_masks (NULL, or entries NULL = all foreground) device
+ * uint8 [n_pixels[t]], d_labels[t] device int32 [n_pixels[t]] receives the
+ * labels (-1 background). All borrowed for the duration of the call; the host
+ * arrays are read during the call only. While frame t runs its rounds on
+ * `stream`, frame t+1 is compacted, normalised and (MS_BF16) split on the
+ * internal stream into the other workspace. h_n_start (nullable, host int64
+ * [T]) receives the N each frame started from, h_n_modes (nullable, host int32
+ * [T]) its mode count. Returns after the last frame's rounds; its labels are
+ * written when `stream` reaches them. Errors as ms_create/ms_run for the
+ * failing frame; frames before it are complete.
+ * ms_video_state gives the N the next frame will start from and the frames
+ * clustered so far; ms_video_stats the counters of the last (which = 0) or the
+ * previous (which = 1) frame. ms_video_destroy synchronises and frees. */
+typedef struct ms_video ms_video;
+MS_API ms_status ms_video_create(const ms_config* cfg, int64_t max_pixels, void* stream, ms_video** out);
+MS_API ms_status ms_video_run(ms_video* v, int32_t T, const float* const* d_embs, const uint8_t* const* d_masks,
+                              const int64_t* n_pixels, int32_t* const* d_labels, int64_t* h_n_start,
+                              int32_t* h_n_modes);
+MS_API ms_status ms_video_state(const ms_video* v, int64_t* n_carry_out, int64_t* frames_out);
+MS_API ms_status ms_video_stats(const ms_video* v, int32_t which, ms_stats* out);
+MS_API void ms_video_destroy(ms_video* v);
 
 /* Batched form: B frames (e.g. the frames of a time-lapse sequence, each its
  * own vector set S of Algorithm 2) clustered by one CUDA graph. Every frame

@@ -80,7 +80,7 @@ class OrStats(ctypes.Structure):
         ("pad_", ctypes.c_int32), ("seeds", ctypes.c_int64), ("seed_iters", ctypes.c_int64),
         ("candidates", ctypes.c_int64), ("dropped", ctypes.c_int64),
         ("min_window_margin", ctypes.c_double), ("min_cover_margin", ctypes.c_double),
-        ("min_merge_margin", ctypes.c_double),
+        ("min_merge_margin", ctypes.c_double), ("n_carry", ctypes.c_int64),
     ]
 
 

@@ -99,6 +99,12 @@ _SIGNATURES = {
     "ms_batch_modes": (_i32, [_vp, _i32, _vp, _i32, _pi32]),
     "ms_batch_destroy": (None, [_vp]),
     "ms_inject_alloc_failure": (None, [_i32]),
+    "ms_video_create": (_i32, [ctypes.POINTER(ms_config), _i64, _vp, ctypes.POINTER(_vp)]),
+    "ms_video_run": (_i32, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _pi64, ctypes.POINTER(_vp),
+                            _pi64, _pi32]),
+    "ms_video_state": (_i32, [_vp, _pi64, _pi64]),
+    "ms_video_stats": (_i32, [_vp, _i32, ctypes.POINTER(ms_stats)]),
+    "ms_video_destroy": (None, [_vp]),
 }
 
 
@@ -353,6 +359,67 @@ class Batch:
         if getattr(self, "handle", None):
             load().ms_batch_destroy(self.handle)
             self.handle = None
+
+
+class Video:
+    """Owns an ms_video (two workspaces and a side stream)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ms_video_destroy(self.handle)
+            self.handle = None
+
+
+def ms_video_create(cfg: ms_config, max_pixels: int, stream=None) -> Video:
+    h = ctypes.c_void_p()
+    _check(load().ms_video_create(ctypes.byref(cfg), int(max_pixels), _stream_handle(stream), ctypes.byref(h)))
+    return Video(h)
+
+
+def ms_video_destroy(v: Video):
+    v.close()
+
+
+def ms_video_run(v: Video, embs, masks=None, labels=None):
+    """Cluster the next frames of the video. embs: list of CUDA float32
+    [n_t, dim]; masks: None or a list (entries may be None) of CUDA uint8
+    [n_t]; labels: None (allocated here) or a list of CUDA int32 [n_t].
+    Returns (labels, n_start per frame, mode count per frame)."""
+    import torch
+    T = len(embs)
+    arr = _vp * max(T, 1)
+    e = arr(*[_dptr(t, torch.float32, "emb") for t in embs])
+    m = None if masks is None else arr(*[_dptr(t, torch.uint8, "mask") if t is not None else None for t in masks])
+    if labels is None:
+        labels = [torch.empty(t.shape[0], dtype=torch.int32, device=t.device) for t in embs]
+    lab = arr(*[_dptr(t, torch.int32, "labels") for t in labels])
+    n = (ctypes.c_int64 * max(T, 1))(*[int(t.shape[0]) for t in embs])
+    n_start = (ctypes.c_int64 * max(T, 1))()
+    n_modes = (ctypes.c_int32 * max(T, 1))()
+    _check(load().ms_video_run(v.handle, T, e, m, n, lab, n_start, n_modes))
+    return labels, [int(x) for x in n_start[:T]], [int(x) for x in n_modes[:T]]
+
+
+def ms_video_state(v: Video):
+    """(N the next frame starts from, frames clustered so far)."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().ms_video_state(v.handle, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def ms_video_stats(v: Video, which: int = 0) -> dict:
+    st = ms_stats()
+    _check(load().ms_video_stats(v.handle, int(which), ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in ms_stats._fields_ if not f.startswith("reserved")}
 
 
 def ms_batch_create(cfg: ms_config, embs, masks=None, stream=None) -> Batch:

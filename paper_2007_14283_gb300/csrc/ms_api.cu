@@ -6,6 +6,7 @@
 // N_min when N > H*N_min. The GPU does all per-pixel and per-seed work; the
 // host reads back a few counters per call.
 #include <atomic>
+#include <stdint.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -251,28 +252,24 @@ ms_status ms_workspace_bytes(const ms_config* cfg, int64_t n_pixels, int64_t* by
     return MS_OK;
 }
 
-ms_status ms_create(const ms_config* cfg, const float* d_emb, const uint8_t* d_mask, int64_t n_pixels,
-                    void* stream, ms_ctx** out) {
-    g_err[0] = 0;
-    if (!out) return set_error(MS_ERR_INVALID_ARG, "out is NULL");
+}  // extern "C"
+
+namespace ms {
+
+// Workspace for frames of up to max_pixels pixels; no frame bound yet.
+ms_status ctx_alloc(const ms_config* cfg, int64_t max_pixels, cudaStream_t stream, ms_ctx** out) {
     *out = nullptr;
-    ms_status s = validate(cfg);
-    if (s != MS_OK) return s;
-    if (n_pixels < 0 || n_pixels >= (1LL << 24)) return set_error(MS_ERR_INVALID_ARG, "n_pixels must be in [0, 2^24)");
-    if (n_pixels > 0 && !d_emb) return set_error(MS_ERR_INVALID_ARG, "d_emb is NULL");
     ms_ctx* ctx = new (std::nothrow) ms_ctx();
     if (!ctx) return set_error(MS_ERR_OOM, "host allocation failed");
     ctx->cfg = *cfg;
     ctx->d = cfg->dim;
     ctx->Dp = padded_dim(cfg->dim);
-    ctx->stream = (cudaStream_t)stream;
-    ctx->emb = d_emb;
-    ctx->mask = d_mask;
-    ctx->n_pixels = n_pixels;
+    ctx->stream = stream;
+    ctx->max_pixels = max_pixels;
     ctx->num_sms = device_sms();
     ctx->shift_grid = ctx->num_sms * shift_blocks_per_sm();
     ctx->target_items = 2 * ctx->shift_grid;
-    const Layout L = plan(n_pixels, ctx->Dp, ctx->target_items, cfg->precision == MS_BF16);
+    const Layout L = plan(max_pixels, ctx->Dp, ctx->target_items, cfg->precision == MS_BF16);
     ctx->ws_bytes = L.total;
     cudaError_t e = workspace_malloc(&ctx->ws, L.total);
     if (e != cudaSuccess) {
@@ -316,38 +313,83 @@ ms_status ms_create(const ms_config* cfg, const float* d_emb, const uint8_t* d_m
         free_ctx(ctx);
         return set_error(MS_ERR_OOM, "host allocation failed");
     }
-    s = cuda_check(cudaMemsetAsync(ctx->covered, 0, (size_t)(n_pixels > 0 ? n_pixels : 1), ctx->stream), "memset");
-    if (s == MS_OK) s = cuda_check(cudaMemsetAsync(ctx->dc, 0, sizeof(DevCounters), ctx->stream), "memset");
-    if (s == MS_OK)
-        s = cuda_check(cudaMemsetAsync(ctx->acc, 0, sizeof(unsigned long long) * (size_t)(ctx->Dp + 1) *
-                                                        (size_t)(n_pixels > 0 ? n_pixels : 1), ctx->stream),
-                       "memset");
-    if (s == MS_OK) s = launch_ingest(ctx);
-    if (s == MS_OK) s = readback(ctx);
+    *out = ctx;
+    return MS_OK;
+}
+
+// Enqueue on `st` everything that binds a frame to the workspace and needs no
+// host decision: clearing, foreground compaction and normalisation, and the
+// BF16 split rows (sized on the device from the foreground count).
+ms_status ctx_bind_async(ms_ctx* ctx, const float* d_emb, const uint8_t* d_mask, int64_t n_pixels,
+                         cudaStream_t st) {
+    ctx->emb = d_emb;
+    ctx->mask = d_mask;
+    ctx->n_pixels = n_pixels;
+    const size_t nn = (size_t)(n_pixels > 0 ? n_pixels : 1);
+    MS_CUDA(cudaMemsetAsync(ctx->covered, 0, nn, st));
+    MS_CUDA(cudaMemsetAsync(ctx->dc, 0, sizeof(DevCounters), st));
+    MS_CUDA(cudaMemsetAsync(ctx->acc, 0, sizeof(unsigned long long) * (size_t)(ctx->Dp + 1) * nn, st));
+    const cudaStream_t keep = ctx->stream;
+    ctx->stream = st;
+    ms_status s = launch_ingest(ctx);
+    if (s == MS_OK && ctx->cfg.precision == MS_BF16) s = tc_pack_async(ctx);
+    ctx->stream = keep;
+    return s;
+}
+
+// Wait for the bind on `st`, check its inputs, and set the frame's host state:
+// foreground count, seed order of frame_id, N starting at n_start.
+ms_status ctx_bind_finish(ms_ctx* ctx, cudaStream_t st, uint64_t frame_id, int64_t n_start) {
+    MS_CUDA(cudaMemcpyAsync(ctx->hc, ctx->dc, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+    MS_CUDA(cudaStreamSynchronize(st));
+    if (ctx->hc->status != 0) return set_error(MS_ERR_INVALID_ARG, "a foreground embedding has zero or non-finite norm");
+    ctx->cfg.frame_id = frame_id;
+    ctx->n = ctx->hc->n_fg;
+    ctx->uncovered = ctx->n;
+    seed_order_params(ctx->n, ctx->cfg.seed, frame_id, &ctx->perm_a, &ctx->perm_b);
+    ctx->n_pad = ctx->n > 0 ? (ctx->n + 127) / 128 * 128 : 0;
+    if (ctx->cfg.precision == MS_BF16 && ctx->n > 0) {
+        ms_status s = tc_finish(ctx);
+        if (s != MS_OK) return s;
+    }
+    ctx->N = n_start;
+    ctx->N_carry = n_start;
+    ctx->phase = 0;
+    ctx->n_kept = 0;
+    ctx->m_round = 0;
+    const int64_t launches = ctx->stats.launches;
+    ctx->stats = ms_stats{};
+    ctx->stats.launches = launches;
+    ctx->stats.n_fg = ctx->n;
+    ctx->stats.uncovered = ctx->n;
+    ctx->stats.workspace_bytes = (int64_t)ctx->ws_bytes;
+    return MS_OK;
+}
+
+void ctx_free(ms_ctx* ctx) { free_ctx(ctx); }
+
+}  // namespace ms
+
+extern "C" {
+
+ms_status ms_create(const ms_config* cfg, const float* d_emb, const uint8_t* d_mask, int64_t n_pixels,
+                    void* stream, ms_ctx** out) {
+    g_err[0] = 0;
+    if (!out) return set_error(MS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    ms_status s = validate(cfg);
+    if (s != MS_OK) return s;
+    if (n_pixels < 0 || n_pixels >= (1LL << 24)) return set_error(MS_ERR_INVALID_ARG, "n_pixels must be in [0, 2^24)");
+    if (n_pixels > 0 && !d_emb) return set_error(MS_ERR_INVALID_ARG, "d_emb is NULL");
+    ms_ctx* ctx = nullptr;
+    s = ctx_alloc(cfg, n_pixels, (cudaStream_t)stream, &ctx);
+    if (s != MS_OK) return s;
+    s = ctx_bind_async(ctx, d_emb, d_mask, n_pixels, ctx->stream);
+    if (s == MS_OK) s = ctx_bind_finish(ctx, ctx->stream, cfg->frame_id, cfg->n_initial);
     if (s != MS_OK) {
         free_ctx(ctx);
         return s;
     }
-    if (ctx->hc->status != 0) {
-        free_ctx(ctx);
-        return set_error(MS_ERR_INVALID_ARG, "a foreground embedding has zero or non-finite norm");
-    }
-    ctx->n = ctx->hc->n_fg;
-    ctx->uncovered = ctx->n;
-    seed_order_params(ctx->n, cfg->seed, cfg->frame_id, &ctx->perm_a, &ctx->perm_b);
-    ctx->n_pad = ctx->n > 0 ? (ctx->n + 127) / 128 * 128 : 0;
-    if (cfg->precision == MS_BF16 && ctx->n > 0) {
-        s = tc_prepare(ctx);
-        if (s != MS_OK) {
-            free_ctx(ctx);
-            return s;
-        }
-    }
-    ctx->N = cfg->n_initial;
-    ctx->phase = 0;
-    ctx->stats.n_fg = ctx->n;
-    ctx->stats.uncovered = ctx->n;
-    ctx->stats.workspace_bytes = (int64_t)L.total;
     *out = ctx;
     return MS_OK;
 }
@@ -461,6 +503,9 @@ ms_status ms_merge_modes(ms_ctx* ctx, int32_t* n_modes_out, int64_t* n_uncovered
     const double gamma = ctx->cfg.all_seeds ? 1.0 : ctx->cfg.gamma;
     const double L = ctx->cfg.L > 0.0 ? ctx->cfg.L : ctx->cfg.alpha / gamma;
     ctx->N = schedule_next(ctx->N, ctx->n_kept, ctx->cfg.P_target, L, ctx->cfg.H, ctx->uncovered);
+    // the value a video carries into its next frame: the same updates, never
+    // clamped to this frame's uncovered pixels
+    ctx->N_carry = schedule_next(ctx->N_carry, ctx->n_kept, ctx->cfg.P_target, L, ctx->cfg.H, INT64_MAX);
     ctx->phase = 0;
     if (n_modes_out) *n_modes_out = ctx->n_kept;
     if (n_uncovered_out) *n_uncovered_out = ctx->uncovered;
@@ -562,14 +607,17 @@ ms_status ms_run_host(const ms_config* cfg, const float* h_emb, const uint8_t* h
 
 ms_status ms_get_state(const ms_ctx* ctx, int64_t* n_next_out) {
     if (!ctx || !n_next_out) return set_error(MS_ERR_INVALID_ARG, "NULL argument");
-    *n_next_out = ctx->N;
+    *n_next_out = ctx->N_carry;
     return MS_OK;
 }
 
 ms_status ms_set_state(ms_ctx* ctx, int64_t n_next) {
     if (!ctx) return set_error(MS_ERR_INVALID_ARG, "ctx is NULL");
     if (n_next < 1) return set_error(MS_ERR_INVALID_ARG, "n_next must be >= 1");
+    if (ctx->phase != 0 || ctx->stats.rounds != 0)
+        return set_error(MS_ERR_STATE, "the seed count can be set only before the frame's first round");
     ctx->N = n_next;
+    ctx->N_carry = n_next;
     return MS_OK;
 }
 

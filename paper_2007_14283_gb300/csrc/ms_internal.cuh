@@ -127,6 +127,8 @@ struct ms_ctx {
     // host-side OSOP state
     int phase;           // 0 idle, 1 seeded, 2 iterated
     int64_t N;           // seed count for the next batch
+    int64_t N_carry;     // the schedule's N without the clamp to uncovered pixels (carried across video frames)
+    int64_t max_pixels;  // the workspace holds frames of up to this many pixels
     int64_t uncovered;
     int32_t n_kept;
     int32_t m_round;
@@ -180,7 +182,13 @@ int shift_blocks_per_sm();                                  // ms_shift_fp32.cu
 ms_status launch_window_sums_fp32(const float* P32, int32_t n, const int32_t* active, const float* X,
                                   unsigned long long* acc, float c, const DevCounters* dc,
                                   cudaStream_t stream);
-ms_status tc_prepare(ms_ctx* ctx);                          // ms_shift_tc.cu
+ms_status tc_pack_async(ms_ctx* ctx);                       // ms_shift_tc.cu: split rows on ctx->stream
+ms_status tc_finish(ms_ctx* ctx);                           // kernel attributes, TMA map of the n_pad rows
+// ms_api.cu: a context's workspace, and binding frames to it (ms_create and the video form)
+ms_status ctx_alloc(const ms_config* cfg, int64_t max_pixels, cudaStream_t stream, ms_ctx** out);
+ms_status ctx_bind_async(ms_ctx* ctx, const float* d_emb, const uint8_t* d_mask, int64_t n_pixels, cudaStream_t st);
+ms_status ctx_bind_finish(ms_ctx* ctx, cudaStream_t st, uint64_t frame_id, int64_t n_start);
+void ctx_free(ms_ctx* ctx);
 ms_status launch_shift_tc(ms_ctx* ctx, const int32_t* active, int grid, int target_items, float* dbg_S);
 int tc_smem_bytes();
 

@@ -14,6 +14,9 @@ from .vmf import (  # noqa: F401
     frame_c2,
     stack_c3,
     batch_c4,
+    video_sequence,
+    overlap_discs,
+    volume,
     vmf_problem_c5,
     orthogonal_blobs,
 )

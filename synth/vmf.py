@@ -302,6 +302,134 @@ def stack_c3(seed: int = 0, d: int = 16, n_fg: int = 131072, H: int = 512, W: in
                  info=dict(seed=seed, frames=3, split_cells=split_cells.tolist()))
 
 
+def video_sequence(seed: int = 0, T: int = 8, d: int = 16, n_fg: int = 131072, H: int = 512, W: int = 512,
+                   n_cells: int = 60, drift: float = 0.02, kappa_lo: float = 20.0,
+                   kappa_hi: float = 200.0) -> List[Frame]:
+    """T consecutive frames of one time-lapse sequence, each a Frame of its own:
+    the cells keep their pixels and sizes (log-normal, median 0.98 n_fg /
+    n_cells, sigma 0.37), their mean directions drift by `drift` radians along
+    a random tangent per frame, every frame draws fresh vMF samples and 2%
+    uniform outliers; embedding norms ~ U[0.5, 2]. truth holds cell ids (-2
+    outliers, -1 background)."""
+    rng = _rng(seed)
+    n_out = int(math.floor(0.02 * n_fg))
+    sizes = _split_sizes(rng, n_fg - n_out, n_cells, 0.98 * n_fg / n_cells, 0.37)
+    owner = _carve_cells(rng, H, W, sizes)
+    means = uniform_sphere(rng, n_cells, d)
+    kappas = rng.uniform(kappa_lo, kappa_hi, size=n_cells)
+    frames = []
+    for f in range(T):
+        if f > 0:
+            for k in range(n_cells):
+                means[k] = _rotate_toward(means[k], rng.standard_normal(d), drift)
+        truth = owner.copy()
+        out_idx = rng.choice(np.flatnonzero(owner < 0), size=n_out, replace=False)
+        truth[out_idx] = -2
+        emb = rng.standard_normal((H * W, d))
+        for k in range(n_cells):
+            idx = np.flatnonzero(owner == k)
+            emb[idx] = sample_vmf(rng, means[k], float(kappas[k]), idx.size)
+        emb[out_idx] = uniform_sphere(rng, n_out, d)
+        fg = truth != -1
+        sc = rng.uniform(0.5, 2.0, size=H * W)
+        emb[fg] *= sc[fg, None]
+        mask = None if n_fg == H * W else fg.astype(np.uint8)
+        frames.append(Frame(emb=np.ascontiguousarray(emb, dtype=np.float32), mask=mask,
+                            truth=truth.astype(np.int32), means=means.copy(), kappas=kappas, H=H, W=W,
+                            info=dict(seed=seed, frame=f, n_fg=n_fg, n_cells=n_cells)))
+    return frames
+
+
+def overlap_discs(seed: int = 0, H: int = 1000, W: int = 1000, d: int = 18, n_discs: int = 8,
+                  diameter: int = 250, overlap: float = 0.0) -> Frame:
+    """The paper's overlap study (Appendix A): n_discs discs of the given
+    diameter on an H x W canvas, their centres on a ring around the canvas
+    centre, adjacent centres diameter * (1 - overlap) apart, so adjacent discs
+    intersect over `overlap` of a diameter (a later disc owns the shared
+    pixels). Disc k's pixels all hold the same unit vector +/- e_j, orthogonal
+    or opposite to every other disc's; no noise. Background is masked."""
+    rng = _rng(seed)
+    if n_discs > 2 * d:
+        raise ValueError("at most 2*d orthogonal/opposite directions")
+    spacing = diameter * (1.0 - overlap)
+    ring = spacing / (2.0 * math.sin(math.pi / n_discs))
+    phase = rng.uniform(0.0, 2.0 * math.pi)
+    yy, xx = np.divmod(np.arange(H * W), W)
+    owner = np.full(H * W, -1, dtype=np.int32)
+    for k in range(n_discs):
+        cy = H / 2.0 + ring * math.sin(phase + 2.0 * math.pi * k / n_discs)
+        cx = W / 2.0 + ring * math.cos(phase + 2.0 * math.pi * k / n_discs)
+        owner[(yy - cy) ** 2 + (xx - cx) ** 2 <= (diameter / 2.0) ** 2] = k
+    dirs = np.zeros((n_discs, d))
+    for k in range(n_discs):
+        dirs[k, k // 2] = 1.0 if k % 2 == 0 else -1.0
+    emb = np.zeros((H * W, d))
+    fg = owner >= 0
+    emb[fg] = dirs[owner[fg]]
+    emb[~fg] = rng.standard_normal((int((~fg).sum()), d))  # masked: never clustered
+    return Frame(emb=np.ascontiguousarray(emb, dtype=np.float32), mask=fg.astype(np.uint8),
+                 truth=owner, means=dirs, kappas=np.full(n_discs, np.inf), H=H, W=W,
+                 info=dict(seed=seed, overlap=overlap, n_fg=int(fg.sum()), fg_fraction=float(fg.mean())))
+
+
+def volume(seed: int = 0, D: int = 128, H: int = 256, W: int = 256, d: int = 16, n_cells: int = 400,
+           fg_fraction: float = 0.5, kappa_lo: float = 20.0, kappa_hi: float = 200.0,
+           outlier_frac: float = 0.02) -> Frame:
+    """A 3D volume of D x H x W voxels (the paper's 2D-only limitation, Sec. 5.3,
+    lifted): n_cells ellipsoidal vMF cells filling fg_fraction of the voxels,
+    sizes log-normal (sigma 0.37), kappa ~ U[kappa_lo, kappa_hi], plus
+    outlier_frac uniform-sphere voxels; norms ~ U[0.5, 2]. Voxels are listed in
+    z-major order; truth as for frames."""
+    rng = _rng(seed)
+    n_vox = D * H * W
+    n_fg = int(round(fg_fraction * n_vox))
+    n_out = int(math.floor(outlier_frac * n_fg))
+    sizes = _split_sizes(rng, n_fg - n_out, n_cells, (n_fg - n_out) / n_cells, 0.37)
+    # each cell takes the free voxels nearest its centre in its own ellipsoid metric
+    owner = np.full(n_vox, -1, dtype=np.int32)
+    zz, rem = np.divmod(np.arange(n_vox), H * W)
+    yy, xx = np.divmod(rem, W)
+    for k in np.argsort(-sizes, kind="stable"):
+        area = int(sizes[k])
+        free = np.flatnonzero(owner < 0)
+        c = free[rng.integers(free.size)]
+        cz, cy, cx = zz[c], yy[c], xx[c]
+        axes = rng.uniform(1.0, 1.6, size=3)
+        axes /= axes.prod() ** (1.0 / 3.0)
+        r = (3.0 * area / (4.0 * math.pi)) ** (1.0 / 3.0)
+        R = int(math.ceil(2.0 * r * axes.max())) + 2
+        while True:
+            z0, z1 = max(0, cz - R), min(D, cz + R + 1)
+            y0, y1 = max(0, cy - R), min(H, cy + R + 1)
+            x0, x1 = max(0, cx - R), min(W, cx + R + 1)
+            gz, gy, gx = np.meshgrid(np.arange(z0, z1), np.arange(y0, y1), np.arange(x0, x1), indexing="ij")
+            idx = (gz * H * W + gy * W + gx).ravel()
+            keep = owner[idx] < 0
+            if keep.sum() >= area or (z1 - z0 == D and y1 - y0 == H and x1 - x0 == W):
+                break
+            R *= 2
+        idx = idx[keep]
+        m = (((idx // (H * W) - cz) / axes[0]) ** 2 + (((idx // W) % H - cy) / axes[1]) ** 2
+             + ((idx % W - cx) / axes[2]) ** 2)
+        owner[idx[np.argsort(m, kind="stable")[:area]]] = k
+    truth = owner.copy()
+    out_idx = rng.choice(np.flatnonzero(owner < 0), size=n_out, replace=False)
+    truth[out_idx] = -2
+    means = uniform_sphere(rng, n_cells, d)
+    kappas = rng.uniform(kappa_lo, kappa_hi, size=n_cells)
+    emb = np.zeros((n_vox, d), dtype=np.float32)
+    for k in range(n_cells):
+        idx = np.flatnonzero(truth == k)
+        emb[idx] = sample_vmf(rng, means[k], float(kappas[k]), idx.size)
+    emb[out_idx] = uniform_sphere(rng, n_out, d)
+    fg = truth != -1
+    emb[~fg] = rng.standard_normal((int((~fg).sum()), d))
+    emb[fg] *= rng.uniform(0.5, 2.0, size=int(fg.sum()))[:, None].astype(np.float32)
+    return Frame(emb=np.ascontiguousarray(emb, dtype=np.float32), mask=fg.astype(np.uint8),
+                 truth=truth.astype(np.int32), means=means, kappas=kappas, H=D * H, W=W,
+                 info=dict(seed=seed, shape=(D, H, W), n_fg=int(fg.sum()), n_cells=n_cells))
+
+
 def batch_c4(seed: int = 0, B: int = 64, d: int = 16, n_lo: int = 2000,
              n_hi: int = 260000) -> List[Frame]:
     """B frames of uneven foreground size, log-uniform in [n_lo, n_hi], with

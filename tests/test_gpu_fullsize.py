@@ -185,9 +185,13 @@ def _equal_to_oracle(f, ref, labels, modes, seed_log=None, exact_seeds=True):
         if exact_seeds:
             assert np.array_equal(np.asarray(seed_log), ref["seed_log"])
         else:
-            n = min(len(seed_log), len(ref["seed_log"]))
-            assert abs(len(seed_log) - len(ref["seed_log"])) <= max(2, len(ref["seed_log"]) // 10000)
-            assert (np.asarray(seed_log)[:n] == ref["seed_log"][:n]).mean() >= 0.999
+            # a pixel within tol of the coverage boundary may be covered on one
+            # side and drawn as a seed on the other: apart from those few seeds
+            # the two logs are the same sequence
+            a, b = np.asarray(seed_log), np.asarray(ref["seed_log"])
+            odd = np.setxor1d(a, b)
+            assert odd.size <= max(2, b.size // 10000), odd.size
+            assert np.array_equal(a[~np.isin(a, odd)], b[~np.isin(b, odd)])
     return err.max()
 
 

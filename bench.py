@@ -480,6 +480,47 @@ def vmf_leg(n_sm, clk):
             "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz (nominal CUDA-core rate)"}
 
 
+def kernel_variants_leg(n_sm, clk):
+    """Other distances and profiles (ms_kernel_shift) at the differentiable
+    configuration's size: N = 65536 vectors, M = 1024 seeds, d = 16, T = 10.
+    CUDA events, median of 3 after a warm-up. Bound: FP32 FMA; per seed-vector
+    pair and step 2d flops for the distance (cosine: d FMAs of the dot
+    product; Euclidean: a subtraction and an FMA per component) and 2d for
+    the weighted sum."""
+    import torch
+
+    import paper_2007_14283_gb300 as ms
+    import synth
+    prob = synth.vmf_problem_c5(seed=0, N=65536, M=1024, K=32)
+    P = torch.from_numpy(prob["P"]).cuda()
+    X0 = torch.from_numpy(prob["X0"]).cuda()
+    stream = torch.cuda.current_stream()
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    out = []
+    names = {ms.MS_DIST_COSINE: "cosine", ms.MS_DIST_EUCLID: "euclidean"}
+    pnames = {ms.MS_PROFILE_FLAT: "flat", ms.MS_PROFILE_EPANECHNIKOV: "epanechnikov",
+              ms.MS_PROFILE_GAUSSIAN: "gaussian"}
+    for dist, h in ((ms.MS_DIST_COSINE, 0.1), (ms.MS_DIST_EUCLID, 0.45)):
+        for prof in (ms.MS_PROFILE_FLAT, ms.MS_PROFILE_EPANECHNIKOV, ms.MS_PROFILE_GAUSSIAN):
+            ms.ms_kernel_shift(P, X0, dist, prof, h, 10)
+            ts = []
+            for _ in range(3):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ms.ms_kernel_shift(P, X0, dist, prof, h, 10)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            t = statistics.median(ts)
+            tf = 4 * 16 * 65536 * 1024 * 10 / (t * 1e-3) / 1e12
+            out.append({"distance": names[dist], "profile": pnames[prof], "h": h, "ms": t,
+                        "achieved_tflops": tf, "frac_fp32_peak": tf / peak})
+    return {"config": "N=65536, M=1024, d=16, T=10 (synthetic vMF cells)", "rows": out,
+            "peak_tflops": peak, "algorithmic": "4d flops per seed-vector pair and step"}
+
+
 def video_leg(n_frames=16):
     """Video form on a drifting 512x512 sequence (the C2 frame recipe; cell means
     drift 0.02 rad per frame): BF16, the seed count N carried from frame to
@@ -508,8 +549,9 @@ def video_leg(n_frames=16):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3, out
 
-    def video():
-        with ms.ms_video_create(cfg, max(f.emb.shape[0] for f in fs)) as v:
+    def video(restart=0):
+        c = ms.ms_config_default(dim=DIM, precision=ms.MS_BF16, video_restart=restart)
+        with ms.ms_video_create(c, max(f.emb.shape[0] for f in fs)) as v:
             _, n_start, n_modes = ms.ms_video_run(v, embs, masks, labels)
         return n_start, n_modes
 
@@ -522,12 +564,15 @@ def video_leg(n_frames=16):
             finally:
                 ctx.close()
     tv, (n_start, n_modes) = timed_s(video)
+    tr, _ = timed_s(lambda: video(1))
     ti, _ = timed_s(independent)
     return {"config": f"{n_frames} consecutive 512x512 frames (131072 foreground px, 60 cells drifting 0.02 rad "
                       "per frame), BF16 single-frame form",
-            "video_frames_per_s": n_frames / tv, "independent_frames_per_s": n_frames / ti,
+            "video_frames_per_s": n_frames / tv, "video_restart_frames_per_s": n_frames / tr,
+            "independent_frames_per_s": n_frames / ti,
             "n_start": n_start, "modes_per_frame": sum(n_modes) / max(1, len(n_modes)),
-            "api": "ms_video_run (N carried, next frame bound on a second stream) vs ms_create + ms_run per frame"}
+            "api": "ms_video_run (N carried, next frame bound on a second stream; video_restart = 1: N back at "
+                   "N_initial each frame) vs ms_create + ms_run per frame"}
 
 
 PAPER_TABLE1_OURS_S = {1000: 1.624, 2000: 1.618, 5000: 1.664, 10000: 1.698, 20000: 1.747, 50000: 1.892,
@@ -738,6 +783,9 @@ def run_ours(args, rank, ws, local):
     video = None
     if rank == 0 and args.video_frames > 0:
         video = video_leg(args.video_frames)
+    kvar = None
+    if rank == 0 and not args.no_vmf:
+        kvar = kernel_variants_leg(n_sm, clk)
     cpu, parity = None, None
     if rank == 0 and args.cpu != "none":
         import oracle
@@ -796,7 +844,8 @@ def run_ours(args, rank, ws, local):
                            "autotune": main.tuning,
                            "fp32_rechecked_pair_fraction": tot.get("band_pairs", 0) /
                            max(1.0, float(tot["seed_iters"]) * N_FG)},
-                "roofline": roofline, "forms": forms, "smooth_kernel": vmf, "video": video,
+                "roofline": roofline, "forms": forms, "smooth_kernel": vmf, "kernel_variants": kvar,
+                "video": video,
                 "parity_vs_oracle": parity,
                 "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": int(reduce_over_ranks(tot["launches"], ws, "sum")), "clocks": clk}

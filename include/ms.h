@@ -89,7 +89,9 @@ typedef struct ms_config {
     int32_t batch_max_passes; /* ms_batch_* only: guard on passes of the graph's loop body (every
                                  iterating frame advances one iteration per pass); a batch still
                                  unfinished after it stops with MS_ERR_TIMEOUT. 0 = 200000 */
-    int32_t reserved[5];  /* zero */
+    int32_t video_restart; /* ms_video_* only: 1 = every frame starts from n_initial instead of the
+                              seed count carried from the previous frame */
+    int32_t reserved[4];  /* zero */
 } ms_config;
 
 /* Per-context counters, filled by ms_stats_get. */
@@ -186,10 +188,12 @@ MS_API ms_status ms_stats_get(const ms_ctx* ctx, ms_stats* out);
 
 /* OSOP state carried across frames of a video (Sec. 3.2.4; Sec. 4.3, Table 3):
  * the seed count N that a next frame starts from. It follows the same Eq. 19-21
- * updates as the frame's own schedule, from the frame's starting N, but is
- * never clamped to the frame's uncovered pixel count (that clamp only bounds
- * each draw inside the frame). ms_set_state sets the frame's starting N; it
- * returns MS_ERR_STATE once the frame's first round has run. */
+ * updates as the frame's own schedule, from the frame's starting N, without
+ * the clamp to the frame's uncovered pixel count (that clamp bounds the draws
+ * at the frame's end), and is bounded by the largest seed batch the frame drew
+ * (no frame can use more seeds than it has uncovered pixels). ms_set_state
+ * sets the frame's starting N; it returns MS_ERR_STATE once the frame's first
+ * round has run. */
 MS_API ms_status ms_get_state(const ms_ctx* ctx, int64_t* n_next_out);
 MS_API ms_status ms_set_state(ms_ctx* ctx, int64_t n_next);
 
@@ -236,6 +240,30 @@ MS_API ms_status ms_vmf_backward(const float* d_P, int64_t N, const float* d_X0,
                                  double kappa, int32_t T, const float* d_GT, float* d_dP, float* d_dX0,
                                  void* stream);
 
+/* Other distances and kernel profiles (Eq. 2-6 with Eq. 3, 4 and 9): T steps
+ * of the dense mean-shift update, every seed against every vector,
+ *     t = (d(x, p) / h)^2,   w = k(t),   x' = sum w p / sum w   (Eq. 6),
+ * with d the Euclidean distance ||x - p|| (Eq. 4, vectors as given) or the
+ * cosine distance 1 - cos (Eq. 9: vectors and seeds are normalised, x' is
+ * renormalised), and k flat [t <= 1] (Eq. 3), Epanechnikov max(0, 1 - t) or
+ * Gaussian exp(-t / 2). A seed whose weights are all zero stays put.
+ * d_P: device float32 [N, dim]; d_X0: device float32 [M, dim] starting seeds;
+ * d_XT: device float32 [M, dim] receives x_T; d_counts (nullable): device int32
+ * [M] receives each seed's count of vectors with nonzero weight in the last
+ * step. 1 <= dim <= 32, h > 0, T >= 0. FP32 arithmetic; results are
+ * deterministic. Allocates its workspace stream-ordered (cudaMallocAsync) on
+ * `stream` and synchronises it once, after validating the inputs on the
+ * device: MS_ERR_INVALID_ARG for a non-finite component or (cosine) a zero
+ * norm. */
+#define MS_DIST_COSINE 0
+#define MS_DIST_EUCLID 1
+#define MS_PROFILE_FLAT 0
+#define MS_PROFILE_EPANECHNIKOV 1
+#define MS_PROFILE_GAUSSIAN 2
+MS_API ms_status ms_kernel_shift(const float* d_P, int64_t N, const float* d_X0, int32_t M, int32_t dim,
+                                 int32_t distance, int32_t profile, double h, int32_t T, float* d_XT,
+                                 int32_t* d_counts, void* stream);
+
 /* Check of the BF16 tensor-core shift tile (Eq. 11 window, Eq. 8 sums) on
  * one work item: 128 seeds d_X [128, 16] (device, unit FP32) against n_pix
  * pixels d_P [n_pix, 16] (device FP32, normalised inside) with bandwidth c.
@@ -278,6 +306,10 @@ MS_API ms_status ms_window_sums_static(const float* d_X, int32_t m, const float*
  * (counting over every ms_video_run call) uses the seed order of frame_id =
  * cfg->frame_id + t, so its results equal ms_create + ms_set_state(carried N)
  * + ms_run on that frame with that frame_id.
+ *
+ * With cfg->video_restart = 1 every frame starts from cfg->n_initial instead
+ * (frames then equal ms_create + ms_run on their own; the second stream and the
+ * reused workspaces remain).
  *
  * ms_video_create allocates two workspaces for frames of up to max_pixels
  * pixels (0 <= max_pixels < 2^24) and a second, internal stream; cfg as for

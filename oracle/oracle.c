@@ -383,6 +383,7 @@ int32_t or_run(const or_config* cfg, const float* emb, const uint8_t* mask, int6
     or_perm_params(n, cfg->seed, cfg->frame_id, &a, &b);
     int64_t cursor = 0, uncovered = n, N = cfg->n_initial, drawn = 0;
     int32_t n_kept = 0;
+    int64_t n_free = N, max_draw = 0;
     st.n_carry = N;
     while (uncovered > 0 && st.rounds < cfg->max_rounds) {
         int64_t want = cfg->all_seeds ? n : N;
@@ -437,9 +438,13 @@ int32_t or_run(const or_config* cfg, const float* emb, const uint8_t* mask, int6
         st.rounds += 1;
         /* A video carries N into its next frame (Sec. 3.2.4; Sec. 4.3, Table 3).
            The carried value follows the same Eq. 19-21 updates from n_initial
-           but never takes the clamp to this frame's uncovered pixels, which
-           only bounds the draw inside one frame. */
-        st.n_carry = or_next_n(st.n_carry, n_kept, 1.0, cfg->P_target, L, cfg->H, INT64_MAX);
+           without the clamp to this frame's uncovered pixels (which only
+           bounds the draws at the frame's end), and is bounded by the largest
+           batch the frame actually drew: no frame can use more seeds than it
+           has uncovered pixels. */
+        if (m > max_draw) max_draw = m;
+        n_free = or_next_n(n_free, n_kept, 1.0, cfg->P_target, L, cfg->H, INT64_MAX);
+        st.n_carry = n_free < max_draw ? n_free : max_draw;
         N = or_next_n(N, n_kept, 1.0, cfg->P_target, L, cfg->H, uncovered);
     }
     if (n_kept > mode_cap) {

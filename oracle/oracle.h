@@ -54,8 +54,8 @@ typedef struct or_stats {
     double min_merge_margin;  /* min |max_kept cos - merge_cos| over every merge decision */
     int64_t n_carry;          /* seed count carried to the next frame of a video (Sec. 3.2.4,
                                  Sec. 4.3 / Table 3): the Eq. 19-21 updates from n_initial over
-                                 the frame's rounds, without the clamp to the frame's uncovered
-                                 count that bounds each draw */
+                                 the frame's rounds without the clamp to the frame's uncovered
+                                 count, bounded by the largest batch the frame drew */
 } or_stats;
 
 /* SplitMix64 (Steele, Lea, Flood 2014): advance *state and return the output. */

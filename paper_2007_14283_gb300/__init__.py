@@ -20,6 +20,8 @@ MS_OK, MS_ERR_INVALID_ARG, MS_ERR_CUDA, MS_ERR_OOM = 0, 1, 2, 3
 MS_ERR_NOT_CONVERGED, MS_ERR_STATE, MS_ERR_TIMEOUT = 4, 5, 6
 MS_FLAT, MS_VMF = 0, 1
 MS_FP32, MS_BF16 = 0, 1
+MS_DIST_COSINE, MS_DIST_EUCLID = 0, 1
+MS_PROFILE_FLAT, MS_PROFILE_EPANECHNIKOV, MS_PROFILE_GAUSSIAN = 0, 1, 2
 MS_INSPECT_SEED_LOG, MS_INSPECT_MODES, MS_INSPECT_SUPPORT = 1, 2, 3
 MS_INSPECT_COVERED, MS_INSPECT_ROUND_LOG, MS_INSPECT_PIXELS = 4, 5, 6
 
@@ -42,7 +44,7 @@ class ms_config(ctypes.Structure):
         ("merge_cos", ctypes.c_double), ("seed", ctypes.c_uint64), ("frame_id", ctypes.c_uint64),
         ("precision", ctypes.c_int32), ("max_rounds", ctypes.c_int32), ("eps_band", ctypes.c_double),
         ("all_seeds", ctypes.c_int32), ("batch_split", ctypes.c_int32), ("batch_max_passes", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("video_restart", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -105,6 +107,7 @@ _SIGNATURES = {
     "ms_video_state": (_i32, [_vp, _pi64, _pi64]),
     "ms_video_stats": (_i32, [_vp, _i32, ctypes.POINTER(ms_stats)]),
     "ms_video_destroy": (None, [_vp]),
+    "ms_kernel_shift": (_i32, [_vp, _i64, _vp, _i32, _i32, _i32, _i32, ctypes.c_double, _i32, _vp, _vp, _vp]),
 }
 
 
@@ -294,6 +297,20 @@ def ms_window_sums_static(X, P, acc_out, c: float = 0.9, stream=None):
     _check(load().ms_window_sums_static(_dptr(X, torch.float32, "X"), X.shape[0], _dptr(P, torch.float32, "P"),
                                         P.shape[0], c, _dptr(acc_out, torch.int64, "acc_out"),
                                         _stream_handle(stream)))
+
+
+def ms_kernel_shift(P, X0, distance: int, profile: int, h: float, T: int, stream=None):
+    """T dense mean-shift steps with the given distance (MS_DIST_*) and kernel
+    profile (MS_PROFILE_*). P CUDA float32 [N, dim], X0 [M, dim]. Returns
+    (x_T [M, dim], counts [M] of nonzero weights in the last step)."""
+    import torch
+    XT = torch.empty_like(X0)
+    counts = torch.empty(X0.shape[0], dtype=torch.int32, device=X0.device)
+    _check(load().ms_kernel_shift(_dptr(P, torch.float32, "P"), P.shape[0], _dptr(X0, torch.float32, "X0"),
+                                  X0.shape[0], X0.shape[1], int(distance), int(profile), float(h), int(T),
+                                  _dptr(XT, torch.float32, "XT"), _dptr(counts, torch.int32, "counts"),
+                                  _stream_handle(stream)))
+    return XT, counts
 
 
 def ms_vmf_forward(P, X0, kappa: float, T: int, stream=None):

@@ -354,6 +354,7 @@ ms_status ctx_bind_finish(ms_ctx* ctx, cudaStream_t st, uint64_t frame_id, int64
     }
     ctx->N = n_start;
     ctx->N_carry = n_start;
+    ctx->max_draw = 0;
     ctx->phase = 0;
     ctx->n_kept = 0;
     ctx->m_round = 0;
@@ -367,6 +368,11 @@ ms_status ctx_bind_finish(ms_ctx* ctx, cudaStream_t st, uint64_t frame_id, int64
 }
 
 void ctx_free(ms_ctx* ctx) { free_ctx(ctx); }
+
+int64_t carried_n(const ms_ctx* ctx) {
+    if (ctx->max_draw <= 0) return ctx->N_carry;
+    return ctx->N_carry < ctx->max_draw ? ctx->N_carry : ctx->max_draw;
+}
 
 }  // namespace ms
 
@@ -409,6 +415,7 @@ ms_status ms_seed_batch(ms_ctx* ctx, int32_t n_requested, int32_t* n_seeded_out)
     if (s != MS_OK) return s;
     const int32_t m = ctx->hc->n_seeded;
     ctx->m_round = m;
+    if (m > ctx->max_draw) ctx->max_draw = m;
     ctx->uncovered = ctx->hc->n_uncovered;
     ctx->stats.seeds += m;
     if ((int64_t)ctx->stats.rounds >= ctx->round_log_cap) {
@@ -503,8 +510,9 @@ ms_status ms_merge_modes(ms_ctx* ctx, int32_t* n_modes_out, int64_t* n_uncovered
     const double gamma = ctx->cfg.all_seeds ? 1.0 : ctx->cfg.gamma;
     const double L = ctx->cfg.L > 0.0 ? ctx->cfg.L : ctx->cfg.alpha / gamma;
     ctx->N = schedule_next(ctx->N, ctx->n_kept, ctx->cfg.P_target, L, ctx->cfg.H, ctx->uncovered);
-    // the value a video carries into its next frame: the same updates, never
-    // clamped to this frame's uncovered pixels
+    // the value a video carries into its next frame: the same updates without
+    // the clamp to this frame's uncovered pixels, bounded (in ms_get_state) by
+    // the largest batch the frame drew
     ctx->N_carry = schedule_next(ctx->N_carry, ctx->n_kept, ctx->cfg.P_target, L, ctx->cfg.H, INT64_MAX);
     ctx->phase = 0;
     if (n_modes_out) *n_modes_out = ctx->n_kept;
@@ -607,7 +615,7 @@ ms_status ms_run_host(const ms_config* cfg, const float* h_emb, const uint8_t* h
 
 ms_status ms_get_state(const ms_ctx* ctx, int64_t* n_next_out) {
     if (!ctx || !n_next_out) return set_error(MS_ERR_INVALID_ARG, "NULL argument");
-    *n_next_out = ctx->N_carry;
+    *n_next_out = carried_n(ctx);
     return MS_OK;
 }
 
@@ -618,6 +626,7 @@ ms_status ms_set_state(ms_ctx* ctx, int64_t n_next) {
         return set_error(MS_ERR_STATE, "the seed count can be set only before the frame's first round");
     ctx->N = n_next;
     ctx->N_carry = n_next;
+    ctx->max_draw = 0;
     return MS_OK;
 }
 

@@ -128,6 +128,7 @@ struct ms_ctx {
     int phase;           // 0 idle, 1 seeded, 2 iterated
     int64_t N;           // seed count for the next batch
     int64_t N_carry;     // the schedule's N without the clamp to uncovered pixels (carried across video frames)
+    int64_t max_draw;    // the largest seed batch of the frame so far (bounds the carried N)
     int64_t max_pixels;  // the workspace holds frames of up to this many pixels
     int64_t uncovered;
     int32_t n_kept;
@@ -189,6 +190,7 @@ ms_status ctx_alloc(const ms_config* cfg, int64_t max_pixels, cudaStream_t strea
 ms_status ctx_bind_async(ms_ctx* ctx, const float* d_emb, const uint8_t* d_mask, int64_t n_pixels, cudaStream_t st);
 ms_status ctx_bind_finish(ms_ctx* ctx, cudaStream_t st, uint64_t frame_id, int64_t n_start);
 void ctx_free(ms_ctx* ctx);
+int64_t carried_n(const ms_ctx* ctx);   // the N a video carries into its next frame
 ms_status launch_shift_tc(ms_ctx* ctx, const int32_t* active, int grid, int target_items, float* dbg_S);
 int tc_smem_bytes();
 

@@ -379,6 +379,76 @@ __global__ void k_label_fix(const int2* __restrict__ fix, const int* __restrict_
     }
 }
 
+// The same decision for one frame, with the mode reads shared: a block takes
+// 64 queued pixels at a time and streams the modes through shared memory in
+// tiles of 128, four threads per pixel each scoring a quarter of every tile
+// (so a mode is read from L2 once per 64 pixels instead of once per pixel).
+// Scores, thresholds and the FP64 tie-break are those of k_label_fix.
+constexpr int kFixPix = 64, kFixQ = 4, kFixTile = 128;
+__global__ void __launch_bounds__(kFixPix * kFixQ)
+k_label_fix_tiled(const int2* __restrict__ fix, const int* __restrict__ fix_count, const float* __restrict__ P32,
+                  const float* __restrict__ M, const int32_t* __restrict__ pix, const float* __restrict__ emb, int K,
+                  int d, int32_t* __restrict__ labels) {
+    __shared__ __align__(16) float tile[kFixTile * 16];
+    __shared__ float rb[kFixQ][kFixPix];
+    __shared__ double rc[kFixQ][kFixPix];
+    __shared__ int ri[kFixQ][kFixPix];
+    const int cnt = *fix_count;
+    const int pl = threadIdx.x % kFixPix, q = threadIdx.x / kFixPix;
+    for (int g0 = blockIdx.x * kFixPix; g0 < cnt; g0 += gridDim.x * kFixPix) {
+        const int e = g0 + pl;
+        const bool live = e < cnt;
+        const int i = live ? fix[e].y : 0;
+        float pv[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) pv[k] = live ? P32[(int64_t)i * 16 + k] : 0.f;
+        // pass 1: best FP32 score
+        float b1 = -INFINITY;
+        for (int j0 = 0; j0 < K; j0 += kFixTile) {
+            const int nt = min(kFixTile, K - j0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < nt * 4; t += blockDim.x)
+                reinterpret_cast<float4*>(tile)[t] = reinterpret_cast<const float4*>(M + (int64_t)j0 * 16)[t];
+            __syncthreads();
+            for (int j = q; j < nt; j += kFixQ) b1 = fmaxf(b1, dot_seq<16>(pv, tile + j * 16));
+        }
+        rb[q][pl] = b1;
+        __syncthreads();
+        b1 = fmaxf(fmaxf(rb[0][pl], rb[1][pl]), fmaxf(rb[2][pl], rb[3][pl]));
+        // pass 2: FP64 cosine of the raw embedding for the modes near the best
+        const float* em = emb + (int64_t)(live ? pix[i] : 0) * d;
+        double bc = -INFINITY;
+        int best = K;
+        for (int j0 = 0; j0 < K; j0 += kFixTile) {
+            const int nt = min(kFixTile, K - j0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < nt * 4; t += blockDim.x)
+                reinterpret_cast<float4*>(tile)[t] = reinterpret_cast<const float4*>(M + (int64_t)j0 * 16)[t];
+            __syncthreads();
+            if (!live) continue;
+            for (int j = q; j < nt; j += kFixQ) {
+                if (dot_seq<16>(pv, tile + j * 16) < b1 - 2.f * kEpsF32) continue;
+                const double cs = cos64(em, M + (int64_t)(j0 + j) * 16, d);
+                if (cs > bc) {  // j rises within a thread: '>' keeps the lowest index
+                    bc = cs;
+                    best = j0 + j;
+                }
+            }
+        }
+        rc[q][pl] = bc;
+        ri[q][pl] = best;
+        __syncthreads();
+        if (q == 0 && live) {
+            for (int o = 1; o < kFixQ; ++o)
+                if (rc[o][pl] > bc || (rc[o][pl] == bc && ri[o][pl] < best)) {
+                    bc = rc[o][pl];
+                    best = ri[o][pl];
+                }
+            if (best < K) labels[pix[i]] = best;
+        }
+    }
+}
+
 // Modes as BF16 split rows at the frame's Pk row offsets (padding rows hold
 // the ones only; their columns are masked out by the score readers).
 __global__ void k_pack_modes_single(const float* __restrict__ modes, int K, int K_pad, uint4* __restrict__ Mk) {
@@ -435,9 +505,9 @@ ms_status launch_label_tc_single(const CUtensorMap& pmap, void* Mk, int64_t n_pa
     k_label_tc<LbSingle><<<grid, kLThreads, kLSmemBytes, st>>>(pmap, mmap, map, out, status);
     MS_LAUNCH("k_label_tc");
     if (K > 1) {
-        k_label_fix<<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, P32, modes, nullptr, nullptr, pix, emb, K, d,
-                                          nullptr, labels);
-        MS_LAUNCH("k_label_fix");
+        k_label_fix_tiled<<<2 * grid, kFixPix * kFixQ, 0, st>>>(sc.fix, sc.fix_count, P32, modes, pix, emb, K, d,
+                                                              labels);
+        MS_LAUNCH("k_label_fix_tiled");
     }
     return MS_OK;
 }

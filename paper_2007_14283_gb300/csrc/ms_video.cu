@@ -109,7 +109,7 @@ extern "C" ms_status ms_video_run(ms_video* v, int32_t T, const float* const* d_
         if (s != MS_OK) break;
         s = cuda_check(cudaEventRecord(v->freed[v->turn], v->stream), "cudaEventRecord");
         if (s != MS_OK) break;
-        v->n_carry = cur->N_carry;
+        v->n_carry = v->cfg.video_restart ? v->cfg.n_initial : carried_n(cur);
         if (h_n_start) h_n_start[t] = n_start;
         if (h_n_modes) h_n_modes[t] = k;
         v->frames += 1;

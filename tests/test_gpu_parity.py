@@ -131,12 +131,17 @@ def test_step_api_and_state_errors(ms_lib):
     assert 0.9 * m < conv <= m
     k, unc = ms_lib.ms_merge_modes(ctx)
     assert (k, unc) == (ref.round_log[0, 2], ref.round_log[0, 3])
-    if ref.round_log.shape[0] > 1:
-        assert ms_lib.ms_get_state(ctx) == ref.round_log[1, 0]
+    # the seed count a next frame would start from: the unclamped schedule,
+    # bounded by the largest batch drawn so far (128)
+    assert ms_lib.ms_get_state(ctx) == min(oracle.next_n(128, int(k), uncovered=10 ** 12), m)
+    with pytest.raises(ms_lib.MsError) as e:
+        ms_lib.ms_set_state(ctx, 64)  # only before the frame's first round
+    assert e.value.status == ms_lib.MS_ERR_STATE
     while unc > 0:
         assert ms_lib.ms_seed_batch(ctx) > 0
         ms_lib.ms_iterate(ctx)
         k, unc = ms_lib.ms_merge_modes(ctx)
+    assert ms_lib.ms_get_state(ctx) == ref.stats["n_carry"]
     labels = torch.empty(4096, dtype=torch.int32, device="cuda")
     modes = torch.empty((k, 16), dtype=torch.float32, device="cuda")
     assert ms_lib.ms_label(ctx, labels, modes) == k

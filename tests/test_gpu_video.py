@@ -105,3 +105,16 @@ def test_video_rejects_oversized_frames_and_continues(ms_lib):
         # the video is still usable
         labels, _, _ = ms_lib.ms_video_run(v, embs, masks)
         assert (labels[0].cpu().numpy() >= -1).all()
+
+
+def test_video_restart_equals_independent_frames(ms_lib):
+    import torch
+    fs = _frames(T=3, seed=9)
+    embs, masks = _dev(fs)
+    cfg = ms_lib.ms_config_default(dim=16, precision=ms_lib.MS_BF16, video_restart=1)
+    with ms_lib.ms_video_create(cfg, max(f.emb.shape[0] for f in fs)) as v:
+        labels, n_start, _ = ms_lib.ms_video_run(v, embs, masks)
+    assert n_start == [cfg.n_initial] * len(fs)
+    for t in range(len(fs)):
+        res = ms_lib.cluster(embs[t], masks[t], precision=ms_lib.MS_BF16, frame_id=t)
+        assert torch.equal(res.labels, labels[t])

@@ -379,25 +379,27 @@ def test_masked_frame_background_is_minus_one():
     assert matched_agreement(np.where(f.mask == 1, f.truth, -1), r.labels) == 1.0
 
 
-def test_video_carry_follows_the_schedule_without_the_clamp():
+def test_video_carry_follows_the_schedule_bounded_by_the_largest_draw():
     """The seed count a video carries into its next frame (Sec. 3.2.4;
-    Sec. 4.3, Table 3) is the Eq. 19-21 update applied round by round from
-    n_initial, with the kept-mode count of each round, never clamped to the
-    frame's uncovered pixels. Hand-worked on the separable C1 frame: 8 modes
-    give N_min = ln(1 - 0.99^(1/8)) / ln(7/8) = 50.03, so N = 128 lies in
-    [2 N_min, 8 N_min] and is carried unchanged, although the frame's own N
-    was clamped to 3 for its last round."""
+    Sec. 4.3, Table 3): the Eq. 19-21 update applied round by round from
+    n_initial with each round's kept-mode count, without the clamp to the
+    frame's uncovered pixels, then bounded by the largest batch the frame
+    drew. Hand-worked on the separable C1 frame: 8 modes give
+    N_min = ln(1 - 0.99^(1/8)) / ln(7/8) = 50.03, so N = 128 lies in
+    [2 N_min, 8 N_min] and stays 128, the frame's largest draw; its own N
+    was clamped to 3 for the last round."""
     f = synth.frame_c1_separable(seed=0)
     r = oracle.run(f.emb)
     assert r.round_log[:, 0].tolist() == [128, 3]
     nmin = math.log(1 - 0.99 ** (1 / 8)) / math.log(7 / 8)
     assert 100 < 2 * nmin < 128 < 8 * nmin
     assert r.stats["n_carry"] == 128
-    # and on a frame whose modes keep N doubling: the same updates re-derived
-    # from the round log with the clamp lifted
+    # a frame whose modes keep N doubling: the unclamped updates outgrow the
+    # frame, and its largest draw bounds the carry
     g = synth.frame_c1(seed=0)
     q = oracle.run(g.emb)
     n = 128
     for kept in q.round_log[:, 2]:
         n = oracle.next_n(n, int(kept), uncovered=10 ** 12)
-    assert q.stats["n_carry"] == n > q.round_log[-1, 0]
+    assert n > q.round_log[:, 1].max()
+    assert q.stats["n_carry"] == q.round_log[:, 1].max()

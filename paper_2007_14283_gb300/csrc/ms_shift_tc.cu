@@ -52,8 +52,9 @@ constexpr int kPxPerWarp = 512 / kMaskWarps;   // pixels of a tile per mask warp
 constexpr int kSub = kPxPerWarp / 32;          // 32-pixel TMEM loads per mask warp and tile
 constexpr int kWarpTma = kMaskWarps;           // then the TMA producer and the two MMA issuers
 constexpr int kWarpG1 = kMaskWarps + 1;
-constexpr int kWarpG2 = kMaskWarps + 2;
-constexpr int kTcThreads = (kMaskWarps + 3) * 32;
+constexpr int kWarpG2 = kMaskWarps + 2;        // GEMM2 of even tiles
+constexpr int kWarpG2b = kMaskWarps + 3;       // GEMM2 of odd tiles, on another sub-partition
+constexpr int kTcThreads = (kMaskWarps + 4) * 32;
 static_assert(kMaskWarps % 4 == 0 && kPxPerWarp % 32 == 0, "mask warps cover the four TMEM quadrants evenly");
 constexpr int kStages = 11;            // pixel-tile ring
 constexpr int kTileBytes = 128 * 128;  // 128 rows x 128 bytes
@@ -68,8 +69,8 @@ constexpr float kFixScale = 68719476736.0f;  // 2^36
 constexpr int kOffA1 = 0;                              // 2 x 16 KB
 constexpr int kOffP = 2 * kTileBytes;                  // kStages x 16 KB
 constexpr int kOffBar = kOffP + kStages * kTileBytes;
-constexpr int kNumBars = 2 * kStages + 2 * 2 + 2 * kMBufs + 2 + 2 + 2;
-constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 16 + 1024;  // + alignment slack
+constexpr int kNumBars = 2 * kStages + 2 * 2 + 2 * kMBufs + 2 + 2 + 3;
+constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 32 + 1024;  // + TMEM slot, flags, alignment slack
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
 struct TcSplit {
@@ -223,9 +224,10 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
     uint64_t* a1_full = m_empty + kMBufs;         // [2] seed operand written
     uint64_t* d_full = a1_full + 2;               // Y of an item complete
     uint64_t* d_empty = d_full + 1;               // Y read by the epilogue
-    uint64_t* aux = d_empty + 1;                  // [2] drain barriers of the two MMA issuers
+    uint64_t* aux = d_empty + 1;                  // [3] drain barriers of the three MMA issuers
     uint32_t* tmem_slot = (uint32_t*)(bars + kNumBars);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
+    volatile int* g2_next = (volatile int*)(tmem_slot + 2);  // the next tile whose GEMM2 may be issued
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -242,11 +244,13 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
             mbar_init(&m_full[b], kMaskWarps);
             mbar_init(&m_empty[b], 1);
         }
-        mbar_init(d_full, 1);
+        mbar_init(d_full, 2);  // both GEMM2 issuers commit at an item's end
         mbar_init(d_empty, 128);
         mbar_init(&aux[0], 1);
         mbar_init(&aux[1], 1);
+        mbar_init(&aux[2], 1);
         *abort = 0;
+        *g2_next = 0;
         fence_mbar_init();
     }
     if (warp == kWarpTma && lane == 0) tma_prefetch_desc(&pmap);
@@ -314,10 +318,17 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
             mma_commit_warp(&aux[0]);
             drain_wait(&aux[0], 0);
         }
-    } else if (warp == kWarpG2) {
-        // ------------------------------------------------ GEMM2 issuer
+    } else if (warp == kWarpG2 || warp == kWarpG2b) {
+        // ------------------------------------------------ GEMM2 issuers
         // Y += Mask . P as soon as a mask tile is in TMEM; the pixel stage is
-        // released when these MMAs complete.
+        // released when these MMAs complete. Two warps on different
+        // sub-partitions take even and odd tiles, so neither sub-partition's
+        // mask warps carry all of GEMM2's issue cost. Y accumulates in tile
+        // order: a warp issues tile g only after the other has issued tile
+        // g-1 (g2_next, with tcgen05 fences around the hand-over). Each warp
+        // commits the releases of the tiles it issued, and both commit d_full
+        // at an item's end (a commit covers only its own thread's MMAs).
+        const int par = warp == kWarpG2 ? 0 : 1;
         const uint64_t dP2 = desc_sw128(smem_u32(Pst), kTileBytes, 1024);  // pixel tile, MN-major
         constexpr uint32_t id2 = idesc_bf16(128, 64, 0, 1);
         constexpr uint64_t kT = kTileBytes >> 4;
@@ -326,11 +337,24 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
         for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
             const TcItem ii = map.item(item);
             for (int pt = ii.pt0; pt < ii.pt1; ++pt, ++g) {
+                if ((g & 1) != par) continue;
                 const int s = g % kStages, mb = g % kMBufs;
                 const bool first = pt == ii.pt0;
                 if (!(ok = warp_wait(&m_full[mb], (g / kMBufs) & 1, abort))) break;
                 if (!(ok = warp_wait(&full[s], (g / kStages) & 1, abort))) break;
                 if (first && it >= 1 && !(ok = warp_wait(d_empty, (it - 1) & 1, abort))) break;
+                {
+                    const long long t0 = clock64();
+                    bool turn = true;
+                    while (*g2_next != g) {
+                        if (*abort || clock64() - t0 > kWaitCycles) {
+                            *abort = 1;
+                            turn = false;
+                            break;
+                        }
+                    }
+                    if (!(ok = __all_sync(0xffffffffu, turn))) break;
+                }
                 tc_fence_after();
                 const uint32_t tY = tmem + kColY;
                 const uint32_t tM = tmem + kColM + mb * 64;
@@ -340,12 +364,19 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                     mma_bf16_ts_warp(tY, tM + 8 * k, pb + k * 128, id2, (first && k == 0) ? 0u : 1u);
                 mma_commit_warp(&m_empty[mb]);
                 mma_commit_warp(&empty[s]);
-                if (pt == ii.pt1 - 1) mma_commit_warp(d_full);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence_block();
+                    *g2_next = g + 1;
+                }
             }
+            if (!ok) break;
+            mma_commit_warp(d_full);
         }
         if (__any_sync(0xffffffffu, *abort)) {
-            mma_commit_warp(&aux[1]);
-            drain_wait(&aux[1], 0);
+            mma_commit_warp(&aux[1 + par]);
+            drain_wait(&aux[1 + par], 0);
         }
     } else {
         // ------------------------------------------------ mask warps

@@ -853,7 +853,7 @@ def run_ours(args, rank, ws, local):
 
 
 def run_shift_only(args):
-    """One shift launch (Algorithm 2, lines 4-9, one iteration) of a fixed seed
+    """One shift launch (one iteration of the shift loop of Algorithm 2) of a fixed seed
     batch through the public API: the dominant kernel alone, with a known
     number of seed-iterations per launch."""
     import torch

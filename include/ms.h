@@ -10,8 +10,8 @@
  *   (Eq. 11), so a window is {i : cos(x, p_i) >= c} with c = 1 - h.
  *   Update x <- normalise(mean of the window) (Eq. 6-8, Sec. 3.2.1).
  *   Seeds in rounds sized by OSOP (Eq. 19-21, Sec. 3.2.2-3.2.4), early
- *   stopping at gamma (Sec. 3.2.3), prune/merge and labelling (Algorithm 2,
- *   lines 10-12).
+ *   stopping at gamma (Sec. 3.2.3), prune/merge and labelling (the last
+ *   steps of Algorithm 2).
  *
  * Conventions for every call:
  *  - Pointers named d_* are DEVICE pointers, h_* are HOST pointers; other
@@ -91,7 +91,12 @@ typedef struct ms_config {
                                  unfinished after it stops with MS_ERR_TIMEOUT. 0 = 200000 */
     int32_t video_restart; /* ms_video_* only: 1 = every frame starts from n_initial instead of the
                               seed count carried from the previous frame */
-    int32_t reserved[4];  /* zero */
+    int32_t tc_shape;     /* BF16 form: warp arrangement of the shift kernel, the same arithmetic in
+                             each (results bit-identical). Mask warps x pixels each per tile, GEMM2
+                             issuers: 0 = 16 x 32, two (default); 1 = 16 x 32, one; 2 = 8 x 64,
+                             two; 3 = 8 x 64, one; 4 = two groups of 8 x 64 taking alternate
+                             tiles, two; 5 = the same groups, one */
+    int32_t reserved[3];  /* zero */
 } ms_config;
 
 /* Per-context counters, filled by ms_stats_get. */
@@ -141,14 +146,14 @@ MS_API ms_status ms_workspace_bytes(const ms_config* cfg, int64_t n_pixels, int6
 MS_API ms_status ms_create(const ms_config* cfg, const float* d_emb, const uint8_t* d_mask,
                     int64_t n_pixels, void* stream, ms_ctx** out);
 
-/* Draw the next seed batch (Algorithm 2, line 2): the next n uncovered
+/* Draw the next seed batch (the seed-selection step of Algorithm 2): the next n uncovered
  * positions of the frame's fixed seed order pi(j) = (b + a j) mod n_fg.
  * n_requested <= 0 uses the OSOP schedule's current N (Sec. 3.2.4).
  * Drawn pixels count as covered. *n_seeded_out = 0 means every foreground
  * pixel is covered. MS_ERR_STATE if a previous batch was not merged. */
 MS_API ms_status ms_seed_batch(ms_ctx* ctx, int32_t n_requested, int32_t* n_seeded_out);
 
-/* Shift the current batch in lockstep (Algorithm 2, lines 4-9) until more
+/* Shift the current batch in lockstep (the shift loop of Algorithm 2) until more
  * than gamma of it has converged, none is still moving, or max_iter
  * (<= 0: cfg->max_iter) iterations; unconverged seeds are dropped
  * (Sec. 3.2.3). MS_ERR_NOT_CONVERGED if no seed converged (the batch is still
@@ -156,15 +161,15 @@ MS_API ms_status ms_seed_batch(ms_ctx* ctx, int32_t n_requested, int32_t* n_seed
 MS_API ms_status ms_iterate(ms_ctx* ctx, int32_t max_iter, int32_t* n_converged_out,
                      int32_t* n_iters_out);
 
-/* Prune and merge the batch's converged modes into the kept set (Algorithm 2,
- * line 11): in order of support (descending) then seed order, a mode is kept
+/* Prune and merge the batch's converged modes into the kept set (the
+ * prune/merge step of Algorithm 2): in order of support (descending) then seed order, a mode is kept
  * when its FP64 cosine to every kept mode is < merge_cos. Then marks pixels
  * within c of a new mode as covered and updates N by Eq. 19-21.
  * MS_ERR_STATE unless ms_iterate ran on the current batch. */
 MS_API ms_status ms_merge_modes(ms_ctx* ctx, int32_t* n_modes_out, int64_t* n_uncovered_out);
 
-/* Cluster every vector by its distance to the modes (Algorithm 2, lines
- * 10-12): label = argmax_k cos(p_i, m_k), lowest k on ties, -1 for
+/* Cluster every vector by its distance to the modes (the
+ * labelling step of Algorithm 2): label = argmax_k cos(p_i, m_k), lowest k on ties, -1 for
  * background. d_labels_out: device int32 [n_pixels], caller-owned.
  * d_modes_out: device float32 [cap, dim] or NULL. MS_ERR_INVALID_ARG if
  * d_modes_out is given and cap < the mode count (nothing written). */
@@ -408,24 +413,29 @@ MS_API ms_status ms_batch_modes(const ms_batch* b, int32_t frame, float* h_out, 
                                 int32_t* n_modes_out);
 MS_API void ms_batch_destroy(ms_batch* b);
 
-/* Work split of a batch's shift launches (the autotuned parameters):
- * batch_split 0 gives every frame the single-frame split (results equal
- * ms_run's frame by frame; target_mult is then unused); batch_split 1 shares
- * target_mult x (shift grid) work items across the iterating frames in
- * proportion to their seed x pixel work (target_mult 1..64). The tile shape
- * itself (128 seeds x 128 pixels, 11 pipeline stages) is fixed by the kernel.
- * ms_batch_configure rebuilds the graph (synchronises the stream).
- * ms_batch_autotune times ms_batch_run on the batch's own frames for each
- * candidate -- (0, 2), (1, 1), (1, 2), (1, 4), (1, 8) -- as the median of
- * `reps` graph launches (CUDA events on the batch's stream, after one
- * warm-up launch), keeps the fastest, runs it once more so the batch's
- * outputs come from it, and writes min(cap, 5) results to `results` (host). */
+/* Work split and tile shape of a batch's shift launches (the autotuned
+ * parameters): batch_split 0 gives every frame the single-frame split
+ * (results equal ms_run's frame by frame; target_mult is then unused);
+ * batch_split 1 shares target_mult x (shift grid) work items across the
+ * iterating frames in proportion to their seed x pixel work (target_mult
+ * 1..64). tc_shape is ms_config.tc_shape (0..5; the BF16 form's warp
+ * arrangement; the FP32 form ignores it). ms_batch_configure rebuilds the
+ * graph (synchronises the stream).
+ * ms_batch_autotune times ms_batch_run on the batch's own frames as the
+ * median of `reps` graph launches (CUDA events on the batch's stream, after
+ * one warm-up launch). Phase 1 times the splits (0, 2), (1, 1), (1, 2),
+ * (1, 4), (1, 8) on tc_shape 0; for a BF16 batch, phase 2 times tc_shapes
+ * 1..5 on phase 1's fastest split. It keeps the fastest of all, runs it once
+ * more so the batch's outputs come from it, and writes min(cap, 5 or 10)
+ * results to `results` (host), in the order timed. */
 typedef struct ms_tune_result {
     int32_t batch_split;
     int32_t target_mult;
+    int32_t tc_shape;
+    int32_t reserved;
     double ms;
 } ms_tune_result;
-MS_API ms_status ms_batch_configure(ms_batch* b, int32_t batch_split, int32_t target_mult);
+MS_API ms_status ms_batch_configure(ms_batch* b, int32_t batch_split, int32_t target_mult, int32_t tc_shape);
 MS_API ms_status ms_batch_autotune(ms_batch* b, int32_t reps, ms_tune_result* results, int32_t cap,
                                    int32_t* n_results);
 

@@ -388,7 +388,7 @@ int32_t or_run(const or_config* cfg, const float* emb, const uint8_t* mask, int6
     while (uncovered > 0 && st.rounds < cfg->max_rounds) {
         int64_t want = cfg->all_seeds ? n : N;
         if (want > uncovered) want = uncovered;
-        /* Seed selection (Algorithm 2, line 2): next uncovered positions. */
+        /* Seed selection (the seed-selection step of Algorithm 2): next uncovered positions. */
         int32_t m = 0;
         while (m < want && cursor < n) {
             int64_t i = or_perm_at(cursor, n, a, b);

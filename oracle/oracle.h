@@ -92,7 +92,7 @@ int32_t or_trajectory(const double* P, const double* pn, int64_t n, int32_t dim,
                       double tol, int32_t max_iter, const double* x0, double* traj,
                       int64_t* counts);
 
-/* Shift a batch of m seeds in lockstep (Algorithm 2, lines 4-9) with early
+/* Shift a batch of m seeds in lockstep (the shift loop of Algorithm 2) with early
  * stopping: after each sweep, stop when #converged > gamma*m or no seed is
  * still moving. X [m*dim] in/out; state[s] = 1 converged, 2 empty window,
  * 0 still moving (dropped); support[s] = window size of the last update;
@@ -102,7 +102,7 @@ int32_t or_shift_round(const double* P, const double* pn, int64_t n, int32_t dim
                        uint8_t* state, int64_t* support, int32_t* conv_iter,
                        int64_t* seed_iters, double* min_margin);
 
-/* Prune and merge (Algorithm 2, line 11): candidates taken in order of
+/* Prune and merge (the prune/merge step of Algorithm 2): candidates taken in order of
  * support (descending) then seed order (ascending); each is kept when its
  * cosine to every mode kept so far (kept[0..n_kept) and those kept in this
  * call) is < merge_cos. Kept modes are appended to kept (capacity cap) and
@@ -128,8 +128,8 @@ double or_p_all_seeded(double N, double I, double r);
 int64_t or_next_n(int64_t N, int64_t I, double r, double P, double L, double H,
                   int64_t uncovered);
 
-/* Cluster every vector by its distance to the modes (Algorithm 2, lines
- * 10-12): label = argmax_k cos(p_i, m_k), lowest k on ties; background -1.
+/* Cluster every vector by its distance to the modes (the
+ * labelling step of Algorithm 2): label = argmax_k cos(p_i, m_k), lowest k on ties; background -1.
  * labels [n_pixels]; margin (nullable) [n] = top1 - top2 (+inf for K = 1). */
 void or_label(const double* P, const double* pn, const int64_t* idx, int64_t n, int32_t dim,
               const double* modes, int32_t K, int64_t n_pixels, int32_t* labels,

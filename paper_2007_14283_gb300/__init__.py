@@ -44,7 +44,7 @@ class ms_config(ctypes.Structure):
         ("merge_cos", ctypes.c_double), ("seed", ctypes.c_uint64), ("frame_id", ctypes.c_uint64),
         ("precision", ctypes.c_int32), ("max_rounds", ctypes.c_int32), ("eps_band", ctypes.c_double),
         ("all_seeds", ctypes.c_int32), ("batch_split", ctypes.c_int32), ("batch_max_passes", ctypes.c_int32),
-        ("video_restart", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
+        ("video_restart", ctypes.c_int32), ("tc_shape", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -59,7 +59,8 @@ class ms_stats(ctypes.Structure):
 
 
 class ms_tune_result(ctypes.Structure):
-    _fields_ = [("batch_split", ctypes.c_int32), ("target_mult", ctypes.c_int32), ("ms", ctypes.c_double)]
+    _fields_ = [("batch_split", ctypes.c_int32), ("target_mult", ctypes.c_int32), ("tc_shape", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("ms", ctypes.c_double)]
 
 
 _lib = None
@@ -96,7 +97,7 @@ _SIGNATURES = {
     "ms_batch_stats": (_i32, [_vp, _i32, ctypes.POINTER(ms_stats)]),
     "ms_batch_profile": (_i32, [_vp, _i32]),
     "ms_batch_run_eager": (_i32, [_vp, _i32]),
-    "ms_batch_configure": (_i32, [_vp, _i32, _i32]),
+    "ms_batch_configure": (_i32, [_vp, _i32, _i32, _i32]),
     "ms_batch_autotune": (_i32, [_vp, _i32, ctypes.POINTER(ms_tune_result), _i32, _pi32]),
     "ms_batch_modes": (_i32, [_vp, _i32, _vp, _i32, _pi32]),
     "ms_batch_destroy": (None, [_vp]),
@@ -492,17 +493,19 @@ def ms_batch_run_eager(b: Batch, passes: int):
     _check(load().ms_batch_run_eager(b.handle, passes))
 
 
-def ms_batch_configure(b: Batch, batch_split: int, target_mult: int = 2):
-    _check(load().ms_batch_configure(b.handle, batch_split, target_mult))
+def ms_batch_configure(b: Batch, batch_split: int, target_mult: int = 2, tc_shape: int = 0):
+    _check(load().ms_batch_configure(b.handle, batch_split, target_mult, tc_shape))
 
 
 def ms_batch_autotune(b: Batch, reps: int = 3) -> list:
-    """Time every work-split candidate on the batch's frames and keep the
-    fastest; returns [{batch_split, target_mult, ms}] in candidate order."""
-    res = (ms_tune_result * 8)()
+    """Time the work-split candidates, then (BF16) the tile shapes on the best
+    split, on the batch's frames and keep the fastest; returns
+    [{batch_split, target_mult, tc_shape, ms}] in the order timed."""
+    res = (ms_tune_result * 16)()
     n = ctypes.c_int32()
-    _check(load().ms_batch_autotune(b.handle, reps, res, 8, ctypes.byref(n)))
-    return [{"batch_split": r.batch_split, "target_mult": r.target_mult, "ms": r.ms} for r in res[:n.value]]
+    _check(load().ms_batch_autotune(b.handle, reps, res, 16, ctypes.byref(n)))
+    return [{"batch_split": r.batch_split, "target_mult": r.target_mult, "tc_shape": r.tc_shape, "ms": r.ms}
+            for r in res[:n.value]]
 
 
 def ms_batch_profile(b: Batch, enable: bool = True):

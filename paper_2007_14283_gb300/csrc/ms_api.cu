@@ -132,6 +132,7 @@ ms_status validate(const ms_config* c) {
         return set_error(MS_ERR_INVALID_ARG, "the BF16 tensor-core form supports dim <= 16");
     if (c->max_rounds < 1) return set_error(MS_ERR_INVALID_ARG, "max_rounds must be >= 1");
     if (c->batch_max_passes < 0) return set_error(MS_ERR_INVALID_ARG, "batch_max_passes must be >= 0");
+    if (c->tc_shape < 0 || c->tc_shape >= kTcShapes) return set_error(MS_ERR_INVALID_ARG, "unknown tc_shape");
     return MS_OK;
 }
 

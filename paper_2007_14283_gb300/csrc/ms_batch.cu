@@ -70,6 +70,7 @@ struct ms_batch {
     int64_t body_launches;    // kernels per pass of the loop body
     int split;                // 0: each frame split as on its own; 1: work items shared by load
     int target_mult;          // shift work items per launch = target_mult x shift grid
+    int tc_shape;             // warp arrangement of the tensor-core shift kernel (ms_config.tc_shape)
     int64_t fixed_launches;   // set-up and labelling kernels
     bool prof;                // body brackets the shift launch with timer ticks
     int32_t h_misc[16];       // host copy of misc after the last synchronised run
@@ -1070,7 +1071,8 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     ms_status st;
     if (b->tc)
         st = launch_shift_tc_batch(b->pmap, b->P32, b->X, b->acc, cf, b->frames, b->states, b->plan, b->act[0],
-                                   b->act[1], B, b->misc + 1, (unsigned long long*)(b->misc + 2), b->tc_grid, s);
+                                   b->act[1], B, b->misc + 1, (unsigned long long*)(b->misc + 2), b->tc_grid,
+                                   b->tc_shape, s);
     else
         st = launch_shift_fp32_batch(b->P32, b->X, b->acc, cf, Dp, b->frames, b->states, b->plan, b->act[0],
                                      b->act[1], B, b->f32_grid, s);
@@ -1270,7 +1272,7 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
         cfg->n_initial < 1 || !(cfg->gamma >= 0.0 && cfg->gamma <= 1.0) ||
         !(cfg->P_target > 0.0 && cfg->P_target < 1.0) || cfg->max_rounds < 1 ||
         (cfg->precision != MS_FP32 && cfg->precision != MS_BF16) || (cfg->precision == MS_BF16 && cfg->dim > 16) ||
-        (cfg->batch_split != 0 && cfg->batch_split != 1))
+        (cfg->batch_split != 0 && cfg->batch_split != 1) || cfg->tc_shape < 0 || cfg->tc_shape >= ms::kTcShapes)
         return set_error(MS_ERR_INVALID_ARG, "invalid config");
     ms_batch* b = new (std::nothrow) ms_batch();
     if (!b) return set_error(MS_ERR_OOM, "host allocation failed");
@@ -1286,6 +1288,7 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
     b->grid = b->num_sms * 8;
     b->split = cfg->batch_split;
     b->target_mult = 2;
+    b->tc_shape = cfg->tc_shape;
     b->tc_grid = b->num_sms;
     b->f32_grid = b->num_sms * shift_blocks_per_sm();
     std::vector<BFrame> hf((size_t)B);
@@ -1457,57 +1460,70 @@ extern "C" ms_status ms_batch_run_eager(ms_batch* b, int32_t passes) {
     return MS_OK;
 }
 
-extern "C" ms_status ms_batch_configure(ms_batch* b, int32_t batch_split, int32_t target_mult) {
-    if (!b || (batch_split != 0 && batch_split != 1) || target_mult < 1 || target_mult > 64)
+extern "C" ms_status ms_batch_configure(ms_batch* b, int32_t batch_split, int32_t target_mult, int32_t tc_shape) {
+    if (!b || (batch_split != 0 && batch_split != 1) || target_mult < 1 || target_mult > 64 || tc_shape < 0 ||
+        tc_shape >= ms::kTcShapes)
         return set_error(MS_ERR_INVALID_ARG, "bad arguments");
-    if (batch_split == b->split && target_mult == b->target_mult) return MS_OK;
+    if (batch_split == b->split && target_mult == b->target_mult && tc_shape == b->tc_shape) return MS_OK;
     MS_CUDA(cudaStreamSynchronize(b->stream));
     b->split = batch_split;
     b->target_mult = target_mult;
+    b->tc_shape = tc_shape;
     return rebuild_graph(b);
 }
 
+namespace {
+// Median of `reps` graph launches of the batch as configured now, after one
+// warm-up run (which also checks the batch's status).
+ms_status time_graph(ms_batch* b, int reps, cudaEvent_t e0, cudaEvent_t e1, double* med) {
+    ms_status st = ms_batch_run(b, 1);
+    std::vector<float> t;
+    for (int r = 0; st == MS_OK && r < reps; ++r) {
+        st = cuda_check(cudaEventRecord(e0, b->stream), "cudaEventRecord");
+        if (st == MS_OK) st = cuda_check(cudaGraphLaunch(b->exec, b->stream), "cudaGraphLaunch");
+        if (st == MS_OK) st = cuda_check(cudaEventRecord(e1, b->stream), "cudaEventRecord");
+        if (st == MS_OK) st = cuda_check(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        float ms_ = 0.f;
+        if (st == MS_OK) st = cuda_check(cudaEventElapsedTime(&ms_, e0, e1), "cudaEventElapsedTime");
+        t.push_back(ms_);
+    }
+    if (st != MS_OK) return st;
+    std::sort(t.begin(), t.end());
+    *med = t[t.size() / 2];
+    return MS_OK;
+}
+}  // namespace
+
 extern "C" ms_status ms_batch_autotune(ms_batch* b, int32_t reps, ms_tune_result* results, int32_t cap,
                                        int32_t* n_results) {
-    if (!b || reps < 1 || reps > 100) return set_error(MS_ERR_INVALID_ARG, "bad arguments");
-    static const int kCand[][2] = {{0, 2}, {1, 1}, {1, 2}, {1, 4}, {1, 8}};
-    const int nc = (int)(sizeof(kCand) / sizeof(kCand[0]));
+    if (!b || reps < 1 || reps > 100 || cap < 0) return set_error(MS_ERR_INVALID_ARG, "bad arguments");
+    static const int kSplits[][2] = {{0, 2}, {1, 1}, {1, 2}, {1, 4}, {1, 8}};
+    const int ns = (int)(sizeof(kSplits) / sizeof(kSplits[0]));
+    // Phase 1: the work splits on the default shape; phase 2: the other
+    // shapes on the best split (tensor-core batches only).
+    std::vector<ms_tune_result> cand;
+    for (int c = 0; c < ns; ++c) cand.push_back({kSplits[c][0], kSplits[c][1], 0, 0, 0.0});
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     MS_CUDA(cudaEventCreate(&e0));
     ms_status st = cuda_check(cudaEventCreate(&e1), "cudaEventCreate");
     int best = -1;
-    double best_ms = 0.0;
-    for (int c = 0; st == MS_OK && c < nc; ++c) {
-        st = ms_batch_configure(b, kCand[c][0], kCand[c][1]);
-        if (st == MS_OK) st = ms_batch_run(b, 1);  // warm-up, and the error check
-        std::vector<float> t;
-        for (int r = 0; st == MS_OK && r < reps; ++r) {
-            st = cuda_check(cudaEventRecord(e0, b->stream), "cudaEventRecord");
-            if (st == MS_OK) st = cuda_check(cudaGraphLaunch(b->exec, b->stream), "cudaGraphLaunch");
-            if (st == MS_OK) st = cuda_check(cudaEventRecord(e1, b->stream), "cudaEventRecord");
-            if (st == MS_OK) st = cuda_check(cudaEventSynchronize(e1), "cudaEventSynchronize");
-            float ms_ = 0.f;
-            if (st == MS_OK) st = cuda_check(cudaEventElapsedTime(&ms_, e0, e1), "cudaEventElapsedTime");
-            t.push_back(ms_);
-        }
+    for (size_t c = 0; st == MS_OK && c < cand.size(); ++c) {
+        st = ms_batch_configure(b, cand[c].batch_split, cand[c].target_mult, cand[c].tc_shape);
+        if (st == MS_OK) st = time_graph(b, reps, e0, e1, &cand[c].ms);
         if (st != MS_OK) break;
-        std::sort(t.begin(), t.end());
-        const double med = t[t.size() / 2];
-        if (results && c < cap) {
-            results[c].batch_split = kCand[c][0];
-            results[c].target_mult = kCand[c][1];
-            results[c].ms = med;
-        }
-        if (best < 0 || med < best_ms) {
-            best = c;
-            best_ms = med;
-        }
+        if (best < 0 || cand[c].ms < cand[best].ms) best = (int)c;
+        if ((int)c == ns - 1 && b->tc)
+            for (int sh = 1; sh < ms::kTcShapes; ++sh)
+                cand.push_back({cand[best].batch_split, cand[best].target_mult, sh, 0, 0.0});
     }
     cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (st != MS_OK) return st;
-    if (n_results) *n_results = nc < cap ? nc : cap;
-    st = ms_batch_configure(b, kCand[best][0], kCand[best][1]);
+    const int n = (int)cand.size() < cap ? (int)cand.size() : cap;
+    if (results)
+        for (int c = 0; c < n; ++c) results[c] = cand[c];
+    if (n_results) *n_results = n;
+    st = ms_batch_configure(b, cand[best].batch_split, cand[best].target_mult, cand[best].tc_shape);
     if (st == MS_OK) st = ms_batch_run(b, 1);  // leave the batch's outputs from the chosen configuration
     return st;
 }

@@ -1,4 +1,4 @@
-// Labelling (Algorithm 2, lines 10-12): every foreground vector takes the
+// Labelling (the labelling step of Algorithm 2): every foreground vector takes the
 // mode of highest cosine, lowest index on ties; background stays -1.
 //
 // FP32 form (the BF16 form labels on the tensor cores, ms_label_tc.cu, with

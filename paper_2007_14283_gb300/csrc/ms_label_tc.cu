@@ -1,4 +1,4 @@
-// Labelling, BF16 tensor-core form (Algorithm 2, lines 10-12): every
+// Labelling, BF16 tensor-core form (the labelling step of Algorithm 2): every
 // foreground vector takes the mode of highest cosine, lowest index on ties.
 //
 // The pixel-by-mode score matrix is a GEMM with K = d = 16. A work item is one

@@ -1,4 +1,4 @@
-// Prune/merge of converged modes (Algorithm 2, line 11) and OSOP coverage.
+// Prune/merge of converged modes (the prune/merge step of Algorithm 2) and OSOP coverage.
 //
 // Merge rule: candidates (the round's converged seeds) are visited in order of
 // support descending, then seed order ascending; a candidate is kept when its

@@ -1,4 +1,4 @@
-// OSOP seed selection (Algorithm 2, line 2): the next `want` uncovered
+// OSOP seed selection (the seed-selection step of Algorithm 2): the next `want` uncovered
 // positions of the frame's fixed seed order pi(j) = (b + a j) mod n.
 //
 // One CTA walks the order 1024 positions at a time. Each thread tests one

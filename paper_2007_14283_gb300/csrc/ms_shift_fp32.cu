@@ -1,4 +1,4 @@
-// Shift iteration, plain FP32 form (Algorithm 2, lines 4-9; Eq. 6-8, 11).
+// Shift iteration, plain FP32 form (the shift loop of Algorithm 2; Eq. 6-8, 11).
 //
 // For every active seed x: y = sum of p_i over the window {i : x.p_i >= c},
 // cnt = |window|; then x' = y / ||y|| and the FP64 norm ||x' - x|| decides

@@ -1,4 +1,4 @@
-// Shift iteration, BF16 tensor-core form (Algorithm 2, lines 4-9; Eq. 6-8, 11).
+// Shift iteration, BF16 tensor-core form (the shift loop of Algorithm 2; Eq. 6-8, 11).
 //
 // One work item = 128 seeds x a chunk of 128-pixel tiles. Per pixel tile:
 //   GEMM1  S' = Xh.Ph + Xh.Pm + Xl.Ph - c       (4 tcgen05 MMAs, FP32 in TMEM)
@@ -42,21 +42,43 @@
 #include "ms_device.cuh"
 #include "ms_tc.cuh"
 
+#include <type_traits>
+
 namespace ms {
 namespace {
 
 using namespace tc;
 
-constexpr int kMaskWarps = 16;                 // warps 0..kMaskWarps-1 build the mask
-constexpr int kPxPerWarp = 512 / kMaskWarps;   // pixels of a tile per mask warp
-constexpr int kSub = kPxPerWarp / 32;          // 32-pixel TMEM loads per mask warp and tile
-constexpr int kWarpTma = kMaskWarps;           // then the TMA producer and the two MMA issuers
-constexpr int kWarpG1 = kMaskWarps + 1;
-constexpr int kWarpG2 = kMaskWarps + 2;        // GEMM2 of even tiles
-constexpr int kWarpG2b = kMaskWarps + 3;       // GEMM2 of odd tiles, on another sub-partition
-constexpr int kTcThreads = (kMaskWarps + 4) * 32;
-static_assert(kMaskWarps % 4 == 0 && kPxPerWarp % 32 == 0, "mask warps cover the four TMEM quadrants evenly");
-constexpr int kStages = 11;            // pixel-tile ring
+// Warp arrangement of a CTA (the tile shape the autotuner chooses among):
+// MW mask warps in G groups that take turns tile by tile (group k builds the
+// masks of tiles g with g % G == k), each warp building the mask of
+// 512 / (MW / G) pixels of its group's tiles; then the TMA producer, the
+// GEMM1 issuer and NG2 GEMM2 issuers (NG2 = 2: even and odd tiles, on two
+// sub-partitions).
+template <int MW, int NG2, int G>
+struct TcShape {
+    static constexpr int kMaskWarps = MW;           // warps 0..MW-1 build the mask
+    static constexpr int kGroups = G;
+    static constexpr int kGroupWarps = MW / G;      // mask warps per tile
+    static constexpr int kPxPerWarp = 512 / kGroupWarps;  // pixels of a tile per mask warp
+    static constexpr int kSub = kPxPerWarp / 32;    // 32-pixel TMEM loads per mask warp and tile
+    static constexpr int kWarpTma = MW;
+    static constexpr int kWarpG1 = MW + 1;
+    static constexpr int kWarpG2 = MW + 2;          // first GEMM2 issuer
+    static constexpr int kG2 = NG2;
+    static constexpr int kThreads = (MW + 2 + NG2) * 32;
+    static_assert(MW % G == 0 && kGroupWarps % 4 == 0 && kPxPerWarp % 32 == 0,
+                  "each group's mask warps cover the four TMEM quadrants evenly");
+    static_assert(NG2 == 1 || NG2 == 2, "one or two GEMM2 issuers");
+};
+// Index = ms_config.tc_shape.
+using TcShape0 = TcShape<16, 2, 1>;
+using TcShape1 = TcShape<16, 1, 1>;
+using TcShape2 = TcShape<8, 2, 1>;
+using TcShape3 = TcShape<8, 1, 1>;
+using TcShape4 = TcShape<16, 2, 2>;
+using TcShape5 = TcShape<16, 1, 2>;
+constexpr int kStages = 10;            // pixel-tile ring
 constexpr int kTileBytes = 128 * 128;  // 128 rows x 128 bytes
 constexpr uint32_t kTmemCols = 512;
 constexpr int kMBufs = 3;              // mask tiles in TMEM
@@ -68,8 +90,9 @@ constexpr float kFixScale = 68719476736.0f;  // 2^36
 
 constexpr int kOffA1 = 0;                              // 2 x 16 KB
 constexpr int kOffP = 2 * kTileBytes;                  // kStages x 16 KB
-constexpr int kOffBar = kOffP + kStages * kTileBytes;
-constexpr int kNumBars = 2 * kStages + 2 * 2 + 2 * kMBufs + 2 + 2 + 3;
+constexpr int kOffX = kOffP + kStages * kTileBytes;   // 2 x 8 KB: the item's seeds in FP32, 128 x 16
+constexpr int kOffBar = kOffX + 2 * 128 * 16 * 4;
+constexpr int kNumBars = 2 * kStages + 2 * 2 + 2 * kMBufs + 2 + 2 + 3;  // aux: GEMM1 + up to two GEMM2 issuers
 constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 32 + 1024;  // + TMEM slot, flags, alignment slack
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
@@ -134,6 +157,13 @@ __device__ __forceinline__ void write_a1(uint8_t* A1, int r, const float (&x)[16
 #pragma unroll
     for (int cidx = 5; cidx < 8; ++cidx)
         *reinterpret_cast<uint4*>(A1 + sw128_offset(r, cidx)) = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Row r of the item's FP32 seed tile in shared memory.
+__device__ __forceinline__ void write_xs(float* Xs, int r, const float (&x)[16]) {
+#pragma unroll
+    for (int k = 0; k < 16; k += 4)
+        *reinterpret_cast<float4*>(Xs + r * 16 + k) = make_float4(x[k], x[k + 1], x[k + 2], x[k + 3]);
 }
 
 // What a work item covers, in the frame it belongs to.
@@ -204,27 +234,31 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
     return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort));
 }
 
-template <bool kDebug, class Map>
-__global__ void __launch_bounds__(kTcThreads, 1)
+template <class Shape, bool kDebug, class Map>
+__global__ void __launch_bounds__(Shape::kThreads, 1)
 k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P32, const float* __restrict__ X,
            unsigned long long* __restrict__ acc, float c_f, Map map, int* status,
            unsigned long long* band_ctr, float* __restrict__ dbg_S, int64_t dbg_stride) {
+    constexpr int kGroups = Shape::kGroups, kGroupWarps = Shape::kGroupWarps;
+    constexpr int kPxPerWarp = Shape::kPxPerWarp, kSub = Shape::kSub;
+    constexpr int kWarpTma = Shape::kWarpTma, kWarpG1 = Shape::kWarpG1, kWarpG2 = Shape::kWarpG2, kG2 = Shape::kG2;
     if (!map.init()) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* A1 = smem + kOffA1;
     uint8_t* Pst = smem + kOffP;
+    float* Xs = (float*)(smem + kOffX);           // [2][128][16] seeds of an item (FP32 re-decisions)
     uint64_t* bars = (uint64_t*)(smem + kOffBar);
     uint64_t* full = bars;                        // [kStages] pixel tile landed
     uint64_t* empty = full + kStages;             // [kStages] pixel tile consumed by GEMM2
     uint64_t* s_full = empty + kStages;           // [2] GEMM1 done
-    uint64_t* s_empty = s_full + 2;               // [2] S read by the mask warps
-    uint64_t* m_full = s_empty + 2;               // [kMBufs] mask tile stored to TMEM by every mask warp
+    uint64_t* s_empty = s_full + 2;               // [2] S read by the mask warps of the tile's group
+    uint64_t* m_full = s_empty + 2;               // [kMBufs] mask tile stored to TMEM by its group's warps
     uint64_t* m_empty = m_full + kMBufs;          // [kMBufs] mask tile consumed by GEMM2
     uint64_t* a1_full = m_empty + kMBufs;         // [2] seed operand written
     uint64_t* d_full = a1_full + 2;               // Y of an item complete
     uint64_t* d_empty = d_full + 1;               // Y read by the epilogue
-    uint64_t* aux = d_empty + 1;                  // [3] drain barriers of the three MMA issuers
+    uint64_t* aux = d_empty + 1;                  // [1 + kG2] drain barriers of the MMA issuers
     uint32_t* tmem_slot = (uint32_t*)(bars + kNumBars);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
     volatile int* g2_next = (volatile int*)(tmem_slot + 2);  // the next tile whose GEMM2 may be issued
@@ -237,18 +271,16 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&s_full[b], 1);
-            mbar_init(&s_empty[b], kMaskWarps);
+            mbar_init(&s_empty[b], kGroupWarps);
             mbar_init(&a1_full[b], 128);
         }
         for (int b = 0; b < kMBufs; ++b) {
-            mbar_init(&m_full[b], kMaskWarps);
+            mbar_init(&m_full[b], kGroupWarps);
             mbar_init(&m_empty[b], 1);
         }
-        mbar_init(d_full, 2);  // both GEMM2 issuers commit at an item's end
+        mbar_init(d_full, kG2);  // every GEMM2 issuer commits at an item's end
         mbar_init(d_empty, 128);
-        mbar_init(&aux[0], 1);
-        mbar_init(&aux[1], 1);
-        mbar_init(&aux[2], 1);
+        for (int k = 0; k <= kG2; ++k) mbar_init(&aux[k], 1);
         *abort = 0;
         *g2_next = 0;
         fence_mbar_init();
@@ -318,17 +350,18 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
             mma_commit_warp(&aux[0]);
             drain_wait(&aux[0], 0);
         }
-    } else if (warp == kWarpG2 || warp == kWarpG2b) {
+    } else if (warp >= kWarpG2 && warp < kWarpG2 + kG2) {
         // ------------------------------------------------ GEMM2 issuers
         // Y += Mask . P as soon as a mask tile is in TMEM; the pixel stage is
-        // released when these MMAs complete. Two warps on different
-        // sub-partitions take even and odd tiles, so neither sub-partition's
-        // mask warps carry all of GEMM2's issue cost. Y accumulates in tile
-        // order: a warp issues tile g only after the other has issued tile
-        // g-1 (g2_next, with tcgen05 fences around the hand-over). Each warp
-        // commits the releases of the tiles it issued, and both commit d_full
-        // at an item's end (a commit covers only its own thread's MMAs).
-        const int par = warp == kWarpG2 ? 0 : 1;
+        // released when these MMAs complete. With two issuers, warps on
+        // different sub-partitions take even and odd tiles, so neither
+        // sub-partition's mask warps carry all of GEMM2's issue cost. Y
+        // accumulates in tile order: a warp issues tile g only after tile g-1
+        // was issued (g2_next, with tcgen05 fences around the hand-over).
+        // Each warp commits the releases of the tiles it issued, and every
+        // issuer commits d_full at an item's end (a commit covers only its own
+        // thread's MMAs).
+        const int par = warp - kWarpG2;
         const uint64_t dP2 = desc_sw128(smem_u32(Pst), kTileBytes, 1024);  // pixel tile, MN-major
         constexpr uint32_t id2 = idesc_bf16(128, 64, 0, 1);
         constexpr uint64_t kT = kTileBytes >> 4;
@@ -337,13 +370,13 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
         for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
             const TcItem ii = map.item(item);
             for (int pt = ii.pt0; pt < ii.pt1; ++pt, ++g) {
-                if ((g & 1) != par) continue;
+                if (g % kG2 != par) continue;
                 const int s = g % kStages, mb = g % kMBufs;
                 const bool first = pt == ii.pt0;
                 if (!(ok = warp_wait(&m_full[mb], (g / kMBufs) & 1, abort))) break;
                 if (!(ok = warp_wait(&full[s], (g / kStages) & 1, abort))) break;
                 if (first && it >= 1 && !(ok = warp_wait(d_empty, (it - 1) & 1, abort))) break;
-                {
+                if constexpr (kG2 > 1) {
                     const long long t0 = clock64();
                     bool turn = true;
                     while (*g2_next != g) {
@@ -364,11 +397,13 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                     mma_bf16_ts_warp(tY, tM + 8 * k, pb + k * 128, id2, (first && k == 0) ? 0u : 1u);
                 mma_commit_warp(&m_empty[mb]);
                 mma_commit_warp(&empty[s]);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) {
-                    __threadfence_block();
-                    *g2_next = g + 1;
+                if constexpr (kG2 > 1) {  // one thread's MMAs execute in issue order: no hand-over
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        __threadfence_block();
+                        *g2_next = g + 1;
+                    }
                 }
             }
             if (!ok) break;
@@ -380,27 +415,38 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
         }
     } else {
         // ------------------------------------------------ mask warps
-        const int q = warp & 3;                   // TMEM lane quadrant (a warp reaches lanes 32 * (warp % 4) + 0..31)
-        const int h = warp >> 2;                  // which kPxPerWarp pixels of a tile
-        const int r = q * 32 + lane;              // seed row
+        // Group grp of kGroups takes the tiles g with g % kGroups == grp; in a
+        // group, warp w reaches TMEM lanes 32 * (w % 4) + 0..31 (its seeds) and
+        // builds the mask of kPxPerWarp pixels, 32 at a time.
+        const int grp = warp / kGroupWarps;
+        const int q = warp & 3;                         // TMEM lane quadrant
+        const int h = (warp % kGroupWarps) >> 2;        // which kPxPerWarp pixels of a tile
+        const bool lead = warp < 4;                     // writes the seed operand and reads Y
+        const int r = q * 32 + lane;                    // seed row
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        // One group: the mask is stored once per tile. Two groups (64 pixels
+        // per warp): each 32-pixel part of the mask is stored as soon as it
+        // is built, which keeps fewer registers live.
+        constexpr bool kEarlyStore = kGroups > 1;
         long long band_local = 0;
-        int g = 0, it = 0, mb = 0, mph = 0;       // mask buffer and its phase, without divisions
-        float x[16];
+        int g = 0, it = 0;
+        int mbn = 0, mphn = 0;  // mask buffer of tile g and its phase, kept without divisions
         for (int item = blockIdx.x; item < items; item += gridDim.x, ++it) {
             if (__any_sync(0xffffffffu, *abort)) break;
             const TcItem ii = map.item(item);
             const int pt0 = ii.pt0, pt1 = ii.pt1;
             const int pos = ii.seed0 + r;
             const int slot = pos < ii.n_active ? ii.active[pos] : -1;
-            load_x16(X, slot, x);
-            if (h == 0) {
+            if (lead) {
                 // A1 for this item (first item only) and the next one; the next
                 // one's buffer was last read by the GEMM1s of item it-1, which
                 // completed before this warp observed s_full of that item's
                 // last tile (a commit covers every earlier MMA of its thread).
                 if (it == 0) {
+                    float x[16];
+                    load_x16(X, slot, x);
                     write_a1(A1, r, x, c_f);
+                    write_xs(Xs, r, x);
                     fence_proxy_async();
                     mbar_arrive(&a1_full[0]);
                 }
@@ -411,45 +457,60 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                     float xn[16];
                     load_x16(X, npos < ni.n_active ? ni.active[npos] : -1, xn);
                     write_a1(A1 + ((it + 1) & 1) * kTileBytes, r, xn, c_f);
+                    write_xs(Xs + ((it + 1) & 1) * 128 * 16, r, xn);
                     fence_proxy_async();
                     mbar_arrive(&a1_full[(it + 1) & 1]);
                 }
             }
-            bool ok = true;
-            for (int pt = pt0; pt < pt1; ++pt, ++g) {
+            // The item's seeds in shared memory: written by the lead warps
+            // before their a1_full arrival (at the start of the previous item,
+            // after every mask warp had finished the item before it).
+            bool ok = warp_wait(&a1_full[it & 1], (it >> 1) & 1, abort);
+            const float* xs = Xs + (it & 1) * 128 * 16 + r * 16;
+            for (int pt = pt0; pt < pt1 && ok; ++pt, ++g) {
+                const int mb = mbn, mph = mphn;
+                if (++mbn == kMBufs) {
+                    mbn = 0;
+                    mphn ^= 1;
+                }
+                if (kGroups > 1 && g % kGroups != grp) continue;
                 const int b = g & 1;
                 if (!(ok = warp_wait(&s_full[b], (g >> 1) & 1, abort))) break;
                 tc_fence_after();
-                uint32_t v[kSub][32];
-                float mnj[kSub];
+                uint32_t w[kEarlyStore ? 1 : kSub][16];
+                bool staged = false;  // pixel stage known to be complete (band path)
 #pragma unroll
-                for (int j = 0; j < kSub; ++j)
-                    tmem_ld32_minabs(tmem + kColS + b * 128 + lane_base + h * kPxPerWarp + j * 32, v[j], &mnj[j]);
-                tmem_ld_wait();
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&s_empty[b]);
-                uint32_t w[kSub][16];
-                float mn = mnj[0];
+                for (int j = 0; j < kSub; ++j) {
+                    uint32_t (&wj)[16] = w[kEarlyStore ? 0 : j];
+                    uint32_t v[32];
+                    float mn;
+                    tmem_ld32_minabs(tmem + kColS + b * 128 + lane_base + h * kPxPerWarp + j * 32, v, &mn);
+                    tmem_ld_wait();
+                    if (j == kSub - 1) {  // S read: hand the buffer back to GEMM1
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&s_empty[b]);
+                    }
 #pragma unroll
-                for (int j = 1; j < kSub; ++j) mn = fminf(mn, mnj[j]);
+                    for (int i = 0; i < 16; ++i) wj[i] = ~sign_halves(v[2 * i], v[2 * i + 1]) & 0x3F803F80u;
+                    if (__any_sync(0xffffffffu, mn < kBand)) {
+                        // Re-decide near-boundary pairs with the FP32 form's dot
+                        // product against the exact FP32 pixel rebuilt from the
+                        // tile in shared memory. Bit masks keep register-array
+                        // indices static.
+                        const int s = g % kStages;
+                        if (!staged && !(ok = warp_wait(&full[s], (g / kStages) & 1, abort))) break;
+                        staged = true;
+                        const uint8_t* stage = Pst + s * kTileBytes;
+                        float x[16];  // the seed (a padding row: zeros)
 #pragma unroll
-                for (int j = 0; j < kSub; ++j)
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) w[j][i] = ~sign_halves(v[j][2 * i], v[j][2 * i + 1]) & 0x3F803F80u;
-                if (__any_sync(0xffffffffu, mn < kBand)) {
-                    // Re-decide near-boundary pairs with the FP32 form's dot
-                    // product against the exact FP32 pixel rebuilt from the
-                    // tile in shared memory. Bit masks keep register-array
-                    // indices static.
-                    const int s = g % kStages;
-                    if (!(ok = warp_wait(&full[s], (g / kStages) & 1, abort))) break;
-                    const uint8_t* stage = Pst + s * kTileBytes;
-#pragma unroll
-                    for (int j = 0; j < kSub; ++j) {
+                        for (int k = 0; k < 16; k += 4) {
+                            const float4 t4 = *reinterpret_cast<const float4*>(xs + k);
+                            x[k] = t4.x; x[k + 1] = t4.y; x[k + 2] = t4.z; x[k + 3] = t4.w;
+                        }
                         uint32_t bandm = 0;
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) bandm |= (uint32_t)(fabsf(__uint_as_float(v[j][i])) < kBand) << i;
+                        for (int i = 0; i < 32; ++i) bandm |= (uint32_t)(fabsf(__uint_as_float(v[i])) < kBand) << i;
                         uint32_t inm = 0, todo = bandm;
                         while (todo) {
                             const int i = __ffs(todo) - 1;
@@ -468,34 +529,38 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                             const uint32_t im = (inm >> (2 * k)) & 3u;
                             const uint32_t clear = ((bm & 1u) ? 0x3F80u : 0u) | ((bm & 2u) ? 0x3F800000u : 0u);
                             const uint32_t set = ((im & 1u) ? 0x3F80u : 0u) | ((im & 2u) ? 0x3F800000u : 0u);
-                            w[j][k] = (w[j][k] & ~clear) | set;
+                            wj[k] = (wj[k] & ~clear) | set;
                         }
                     }
-                }
-                if (kDebug) {
-#pragma unroll
-                    for (int j = 0; j < kSub; ++j)
+                    if (kDebug) {
 #pragma unroll
                         for (int i = 0; i < 32; ++i)
                             dbg_S[(int64_t)r * dbg_stride + pt * 128 + h * kPxPerWarp + j * 32 + i] =
-                                __uint_as_float(v[j][i]);
+                                __uint_as_float(v[i]);
+                    }
+                    if constexpr (kEarlyStore) {
+                        if (j == 0) {
+                            if (g >= kMBufs && !(ok = warp_wait(&m_empty[mb], mph ^ 1, abort))) break;
+                            tc_fence_after();
+                        }
+                        tmem_st16(tmem + kColM + mb * 64 + lane_base + h * (kPxPerWarp / 2) + j * 16, wj);
+                    }
                 }
-                if (g >= kMBufs && !(ok = warp_wait(&m_empty[mb], mph ^ 1, abort))) break;
-                tc_fence_after();
+                if (!ok) break;
+                if constexpr (!kEarlyStore) {
+                    if (g >= kMBufs && !(ok = warp_wait(&m_empty[mb], mph ^ 1, abort))) break;
+                    tc_fence_after();
 #pragma unroll
-                for (int j = 0; j < kSub; ++j)
-                    tmem_st16(tmem + kColM + mb * 64 + lane_base + h * (kPxPerWarp / 2) + j * 16, w[j]);
+                    for (int j = 0; j < kSub; ++j)
+                        tmem_st16(tmem + kColM + mb * 64 + lane_base + h * (kPxPerWarp / 2) + j * 16, w[j]);
+                }
                 tmem_st_wait();
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&m_full[mb]);
-                if (++mb == kMBufs) {
-                    mb = 0;
-                    mph ^= 1;
-                }
             }
             if (!ok) break;
-            if (h == 0) {
+            if (lead) {
                 if (!warp_wait(d_full, it & 1, abort)) break;
                 tc_fence_after();
                 uint32_t yh[16], ym[16], yl[16], yc[16];
@@ -560,6 +625,36 @@ ms_status encode_pmap(void* Pk, int n_pad, CUtensorMap* map) {
     return MS_OK;
 }
 
+// Calls fn with a value of the shape type that `shape` (ms_config.tc_shape) names.
+template <class Fn>
+ms_status with_tc_shape(int shape, Fn&& fn) {
+    switch (shape) {
+        case 0: return fn(TcShape0{});
+        case 1: return fn(TcShape1{});
+        case 2: return fn(TcShape2{});
+        case 3: return fn(TcShape3{});
+        case 4: return fn(TcShape4{});
+        case 5: return fn(TcShape5{});
+        default: return set_error(MS_ERR_INVALID_ARG, "unknown tile shape %d", shape);
+    }
+}
+
+template <class Map>
+ms_status allow_smem_all_shapes() {
+    const auto f = [](auto sh) -> ms_status {
+        using Sh = decltype(sh);
+        MS_CUDA(cudaFuncSetAttribute(k_shift_tc<Sh, false, Map>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kSmemBytes));
+        if constexpr (std::is_same_v<Map, TcSingleMap>)  // the score dump is a single-frame self-test
+            MS_CUDA(cudaFuncSetAttribute(k_shift_tc<Sh, true, Map>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemBytes));
+        return MS_OK;
+    };
+    for (int k = 0; k < kTcShapes; ++k)
+        if (ms_status st = with_tc_shape(k, f); st != MS_OK) return st;
+    return MS_OK;
+}
+
 }  // namespace
 
 int tc_smem_bytes() { return kSmemBytes; }
@@ -574,10 +669,7 @@ ms_status tc_pack_async(ms_ctx* ctx) {
 }
 
 ms_status tc_finish(ms_ctx* ctx) {
-    MS_CUDA(cudaFuncSetAttribute(k_shift_tc<false, TcSingleMap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kSmemBytes));
-    MS_CUDA(cudaFuncSetAttribute(k_shift_tc<true, TcSingleMap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kSmemBytes));
+    if (ms_status st = allow_smem_all_shapes<TcSingleMap>(); st != MS_OK) return st;
     ctx->tc_grid = ctx->num_sms;  // one CTA per SM: it owns all 512 TMEM columns
     if (ms_status ls = label_tc_setup(); ls != MS_OK) return ls;
     return encode_pmap(ctx->Pk, (int)ctx->n_pad, &ctx->pmap);
@@ -592,14 +684,17 @@ ms_status launch_shift_tc(ms_ctx* ctx, const int32_t* active, int grid, int targ
     map.n_ptiles = (int)(ctx->n_pad / 128);
     map.target = target_items;
     unsigned long long* band = (unsigned long long*)&ctx->dc->band_pairs;
-    if (dbg_S)
-        k_shift_tc<true, TcSingleMap><<<grid, kTcThreads, kSmemBytes, ctx->stream>>>(
-            ctx->pmap, ctx->P32, ctx->X, ctx->acc, c, map, &ctx->dc->status, band, dbg_S, ctx->n_pad);
-    else
-        k_shift_tc<false, TcSingleMap><<<grid, kTcThreads, kSmemBytes, ctx->stream>>>(
-            ctx->pmap, ctx->P32, ctx->X, ctx->acc, c, map, &ctx->dc->status, band, nullptr, 0);
-    MS_LAUNCH("k_shift_tc");
-    return MS_OK;
+    return with_tc_shape(ctx->cfg.tc_shape, [&](auto sh) -> ms_status {
+        using Sh = decltype(sh);
+        if (dbg_S)
+            k_shift_tc<Sh, true, TcSingleMap><<<grid, Sh::kThreads, kSmemBytes, ctx->stream>>>(
+                ctx->pmap, ctx->P32, ctx->X, ctx->acc, c, map, &ctx->dc->status, band, dbg_S, ctx->n_pad);
+        else
+            k_shift_tc<Sh, false, TcSingleMap><<<grid, Sh::kThreads, kSmemBytes, ctx->stream>>>(
+                ctx->pmap, ctx->P32, ctx->X, ctx->acc, c, map, &ctx->dc->status, band, nullptr, 0);
+        MS_LAUNCH("k_shift_tc");
+        return MS_OK;
+    });
 }
 
 // ------------------------------------------------------------ batched form
@@ -638,15 +733,13 @@ struct TcBatchMap {
 };
 
 ms_status tc_batch_setup() {
-    MS_CUDA(cudaFuncSetAttribute(k_shift_tc<false, TcBatchMap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kSmemBytes));
-    return MS_OK;
+    return allow_smem_all_shapes<TcBatchMap>();
 }
 
 ms_status launch_shift_tc_batch(const CUtensorMap& pmap, const float* P32, const float* X, unsigned long long* acc,
                                 float c_f, const BFrame* frames, const BState* states, BPlan plan,
                                 const int32_t* act0, const int32_t* act1, int nf, int* status,
-                                unsigned long long* band, int grid, cudaStream_t st) {
+                                unsigned long long* band, int grid, int shape, cudaStream_t st) {
     TcBatchMap map;
     map.frames = frames;
     map.states = states;
@@ -655,10 +748,13 @@ ms_status launch_shift_tc_batch(const CUtensorMap& pmap, const float* P32, const
     map.act1 = act1;
     map.nf = nf;
     map.total_ = 0;
-    k_shift_tc<false, TcBatchMap><<<grid, kTcThreads, kSmemBytes, st>>>(pmap, P32, X, acc, c_f, map, status, band,
-                                                                       nullptr, 0);
-    MS_LAUNCH("k_shift_tc(batch)");
-    return MS_OK;
+    return with_tc_shape(shape, [&](auto sh) -> ms_status {
+        using Sh = decltype(sh);
+        k_shift_tc<Sh, false, TcBatchMap><<<grid, Sh::kThreads, kSmemBytes, st>>>(pmap, P32, X, acc, c_f, map,
+                                                                                 status, band, nullptr, 0);
+        MS_LAUNCH("k_shift_tc(batch)");
+        return MS_OK;
+    });
 }
 
 ms_status encode_pk_map(void* Pk, int rows, CUtensorMap* map) { return encode_pmap(Pk, rows, map); }

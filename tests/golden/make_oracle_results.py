@@ -8,9 +8,9 @@ three-frame tracking stack on 8 cores). Calls only oracle/ and synth/.
 Each <name>_oracle_result.npz holds, for synth.frame_c2(seed=0) or
 synth.stack_c3(seed=0) with the default configuration (c = 0.9, tol 1e-6,
 OSOP gamma 0.9, N_initial 128, L 2, H 8, P 0.99, merge_cos = c):
-  modes      float64 [K, 16]  kept modes in keep order (Algorithm 2, line 11)
+  modes      float64 [K, 16]  kept modes in keep order (Algorithm 2, prune/merge)
   support    int64 [K]        window size of each mode's converging update
-  labels     int32 [H*W]      argmax label per pixel, -1 background (lines 10-12)
+  labels     int32 [H*W]      argmax label per pixel, -1 background (Algorithm 2, labelling)
   margin_gt  uint8 packbits   per pixel: top-1 minus top-2 cosine > 1e-5
   seed_log   int32 [seeds]    foreground index of every seed in draw order
   round_log  int64 [rounds,4] N requested, seeds drawn, modes kept, uncovered

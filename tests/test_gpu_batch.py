@@ -211,7 +211,12 @@ def test_batch_autotune_picks_a_candidate_and_keeps_results_valid(ms_lib):
     b = _batch(ms_lib, embs, masks, precision=ms_lib.MS_BF16)
     try:
         res = ms_lib.ms_batch_autotune(b, reps=2)
-        assert [(r["batch_split"], r["target_mult"]) for r in res] == [(0, 2), (1, 1), (1, 2), (1, 4), (1, 8)]
+        splits = [(0, 2), (1, 1), (1, 2), (1, 4), (1, 8)]
+        assert [(r["batch_split"], r["target_mult"], r["tc_shape"]) for r in res[:5]] == [s + (0,) for s in splits]
+        # phase 2: the other tile shapes on phase 1's fastest split
+        best = min(res[:5], key=lambda r: r["ms"])
+        assert [(r["batch_split"], r["target_mult"], r["tc_shape"]) for r in res[5:]] == \
+            [(best["batch_split"], best["target_mult"], sh) for sh in (1, 2, 3, 4, 5)]
         assert all(r["ms"] > 0 for r in res)
         # the batch now holds the fastest candidate's outputs: still within the oracle bar
         for i, f in enumerate(fs[:2]):
@@ -219,11 +224,15 @@ def test_batch_autotune_picks_a_candidate_and_keeps_results_valid(ms_lib):
             modes = ms_lib.ms_batch_modes(b, i)
             assert mode_errors(modes, ref.modes).max() <= MODE_TOL
             assert matched_agreement(ref.labels, b.labels[i].cpu().numpy()) >= 0.999
-        # configuring the canonical split again reproduces single-frame results exactly
-        ms_lib.ms_batch_configure(b, 0, 2)
-        ms_lib.ms_batch_run(b)
+        # configuring the canonical split again reproduces single-frame results
+        # exactly, on every tile shape
         lab_s, modes_s, _ = _single(ms_lib, embs[0], masks[0], 0, precision=ms_lib.MS_BF16)
-        assert np.array_equal(ms_lib.ms_batch_modes(b, 0), modes_s)
-        assert np.array_equal(b.labels[0].cpu().numpy(), lab_s)
+        for sh in range(6):
+            ms_lib.ms_batch_configure(b, 0, 2, sh)
+            ms_lib.ms_batch_run(b)
+            assert np.array_equal(ms_lib.ms_batch_modes(b, 0), modes_s), sh
+            assert np.array_equal(b.labels[0].cpu().numpy(), lab_s), sh
+        with pytest.raises(ms_lib.MsError):
+            ms_lib.ms_batch_configure(b, 0, 2, 6)
     finally:
         b.close()

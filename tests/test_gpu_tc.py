@@ -109,3 +109,24 @@ def test_bf16_masked_ragged(ms_lib):
     assert (labels[f.mask == 0] == -1).all()
     assert mode_errors(modes, ref.modes).max() <= 1e-5
     assert matched_agreement(ref.labels, labels) >= 0.999
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5])
+def test_tile_shapes_are_bit_identical(ms_lib, shape):
+    # every warp arrangement runs the same arithmetic in the same order: the
+    # same windows, band re-decisions, sums and therefore identical outputs
+    for f in (synth.make_frame(4, 96, 96, 16, 6000, 9, 600.0, 0.3, 40.0, 200.0, 0.02), synth.frame_c1(seed=1)):
+        a = _run(ms_lib, f.emb, f.mask, precision=ms_lib.MS_BF16)
+        b = _run(ms_lib, f.emb, f.mask, precision=ms_lib.MS_BF16, tc_shape=shape)
+        assert np.array_equal(a[0], b[0])
+        assert np.array_equal(a[1], b[1])
+        for k in ("seed_log", "round_log"):
+            assert np.array_equal(a[2][k], b[2][k])
+        assert a[2]["band_pairs"] == b[2]["band_pairs"]
+
+
+def test_tile_shape_out_of_range_is_rejected(ms_lib):
+    f = synth.frame_c1_separable(seed=0)
+    with pytest.raises(ms_lib.MsError) as e:
+        _run(ms_lib, f.emb, precision=ms_lib.MS_BF16, tc_shape=6)
+    assert e.value.status == ms_lib.MS_ERR_INVALID_ARG

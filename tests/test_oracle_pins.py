@@ -348,7 +348,7 @@ def test_run_covers_every_pixel_and_schedule_follows_rule():
 
 def test_seed_selection_is_next_uncovered_positions():
     # Re-derive every round's seeds from the permutation and the coverage
-    # implied by the modes kept so far (Algorithm 2, line 2 with OSOP rounds).
+    # implied by the modes kept so far (the seed-selection step of Algorithm 2 with OSOP rounds).
     f = synth.frame_c1(seed=6)
     r = oracle.run(f.emb)
     P, _, _ = oracle.normalize(f.emb)

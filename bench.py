@@ -72,6 +72,8 @@ def parse():
                     help="batched forms: issue the graph's kernels as plain launches (for profilers)")
     ap.add_argument("--shift-only", type=int, default=0, metavar="SEEDS",
                     help="time one shift iteration of SEEDS seeds on frame 0 (fp32 or bf16 form) and exit")
+    ap.add_argument("--tc-shape", type=int, default=0,
+                    help="with --shift-only: the tensor-core shift kernel's tile shape (ms_config.tc_shape)")
     ap.add_argument("--suite", action="store_true",
                     help="the paper's simulation suite (Table 1 sizes, Appendix A overlap, Tables 3-4) and exit")
     ap.add_argument("--volume", action="store_true", help="one 3D volume (128x256x256 voxels) and exit")
@@ -865,7 +867,7 @@ def run_shift_only(args):
     e = torch.from_numpy(f.emb).cuda()
     m = torch.from_numpy(f.mask).cuda()
     prec = ms.MS_BF16 if args.form.startswith("bf16") else ms.MS_FP32
-    cfg = ms.ms_config_default(dim=DIM, precision=prec)
+    cfg = ms.ms_config_default(dim=DIM, precision=prec, tc_shape=args.tc_shape)
     times = []
     for rep in range(args.warmup + args.steps):
         ctx = ms.ms_create(cfg, e, m)
@@ -882,7 +884,7 @@ def run_shift_only(args):
             times.append(st["shift_ms"])
     t = statistics.median(times)
     flops = 4.0 * DIM * N_FG * seeded
-    print(json.dumps({"shift_only": True, "form": args.form, "seeds": seeded, "n": N_FG,
+    print(json.dumps({"shift_only": True, "form": args.form, "tc_shape": args.tc_shape, "seeds": seeded, "n": N_FG,
                       "median_ms": t, "algorithmic_tflops": flops / (t * 1e-3) / 1e12}), flush=True)
 
 

@@ -95,7 +95,9 @@ typedef struct ms_config {
                              each (results bit-identical). Mask warps x pixels each per tile, GEMM2
                              issuers: 0 = 16 x 32, two (default); 1 = 16 x 32, one; 2 = 8 x 64,
                              two; 3 = 8 x 64, one; 4 = two groups of 8 x 64 taking alternate
-                             tiles, two; 5 = the same groups, one */
+                             tiles, two; 5 = the same groups, one; 6 = GEMM1 on 64-pixel units
+                             (four S buffers, six mask buffers), two groups of 8 x 32 taking
+                             alternate units, two issuers; 7 = as 6, one issuer */
     int32_t reserved[3];  /* zero */
 } ms_config;
 
@@ -418,15 +420,15 @@ MS_API void ms_batch_destroy(ms_batch* b);
  * (results equal ms_run's frame by frame; target_mult is then unused);
  * batch_split 1 shares target_mult x (shift grid) work items across the
  * iterating frames in proportion to their seed x pixel work (target_mult
- * 1..64). tc_shape is ms_config.tc_shape (0..5; the BF16 form's warp
+ * 1..64). tc_shape is ms_config.tc_shape (0..7; the BF16 form's warp
  * arrangement; the FP32 form ignores it). ms_batch_configure rebuilds the
  * graph (synchronises the stream).
  * ms_batch_autotune times ms_batch_run on the batch's own frames as the
  * median of `reps` graph launches (CUDA events on the batch's stream, after
  * one warm-up launch). Phase 1 times the splits (0, 2), (1, 1), (1, 2),
  * (1, 4), (1, 8) on tc_shape 0; for a BF16 batch, phase 2 times tc_shapes
- * 1..5 on phase 1's fastest split. It keeps the fastest of all, runs it once
- * more so the batch's outputs come from it, and writes min(cap, 5 or 10)
+ * 1..7 on phase 1's fastest split. It keeps the fastest of all, runs it once
+ * more so the batch's outputs come from it, and writes min(cap, 5 or 12)
  * results to `results` (host), in the order timed. */
 typedef struct ms_tune_result {
     int32_t batch_split;

@@ -193,6 +193,6 @@ void ctx_free(ms_ctx* ctx);
 int64_t carried_n(const ms_ctx* ctx);   // the N a video carries into its next frame
 ms_status launch_shift_tc(ms_ctx* ctx, const int32_t* active, int grid, int target_items, float* dbg_S);
 int tc_smem_bytes();
-constexpr int kTcShapes = 6;  // values of ms_config.tc_shape (warp arrangements of k_shift_tc)
+constexpr int kTcShapes = 8;  // values of ms_config.tc_shape (warp arrangements of k_shift_tc)
 
 }  // namespace ms

@@ -49,42 +49,52 @@ namespace {
 
 using namespace tc;
 
-// Warp arrangement of a CTA (the tile shape the autotuner chooses among):
-// MW mask warps in G groups that take turns tile by tile (group k builds the
-// masks of tiles g with g % G == k), each warp building the mask of
-// 512 / (MW / G) pixels of its group's tiles; then the TMA producer, the
-// GEMM1 issuer and NG2 GEMM2 issuers (NG2 = 2: even and odd tiles, on two
-// sub-partitions).
-template <int MW, int NG2, int G>
+// Tile shape of a CTA (what the autotuner chooses among). Pixels arrive in
+// 128-pixel stages; GEMM1 scores BN of them at a time (a unit: BN = 128, one
+// unit per stage, two 128-column S buffers; BN = 64, two units per stage,
+// four 64-column S buffers), and the mask of a unit takes BN / 2 TMEM columns
+// (three or six mask buffers in the same 192 columns). MW mask warps form G
+// groups that take turns unit by unit (group k builds the masks of units u
+// with u % G == k); each warp builds the mask of 4 * BN / (MW / G) pixels of
+// its group's units. Then come the TMA producer, the GEMM1 issuer and NG2
+// GEMM2 issuers (NG2 = 2: alternate units, on two sub-partitions).
+template <int MW, int NG2, int G, int BN>
 struct TcShape {
     static constexpr int kMaskWarps = MW;           // warps 0..MW-1 build the mask
     static constexpr int kGroups = G;
-    static constexpr int kGroupWarps = MW / G;      // mask warps per tile
-    static constexpr int kPxPerWarp = 512 / kGroupWarps;  // pixels of a tile per mask warp
-    static constexpr int kSub = kPxPerWarp / 32;    // 32-pixel TMEM loads per mask warp and tile
+    static constexpr int kGroupWarps = MW / G;      // mask warps per unit
+    static constexpr int kBN = BN;                  // pixels per unit
+    static constexpr int kUPS = 128 / BN;           // units per 128-pixel stage
+    static constexpr int kSBufs = 256 / BN;         // S buffers of BN columns
+    static constexpr int kMBufs = 384 / BN;         // mask buffers of BN / 2 columns
+    static constexpr int kPxPerWarp = 4 * BN / kGroupWarps;  // pixels of a unit per mask warp
+    static constexpr int kSub = kPxPerWarp / 32;    // 32-pixel TMEM loads per mask warp and unit
     static constexpr int kWarpTma = MW;
     static constexpr int kWarpG1 = MW + 1;
     static constexpr int kWarpG2 = MW + 2;          // first GEMM2 issuer
     static constexpr int kG2 = NG2;
     static constexpr int kThreads = (MW + 2 + NG2) * 32;
-    static_assert(MW % G == 0 && kGroupWarps % 4 == 0 && kPxPerWarp % 32 == 0,
+    static_assert(BN == 128 || BN == 64, "GEMM1 unit of 128 or 64 pixels");
+    static_assert(MW % G == 0 && kGroupWarps % 4 == 0 && kPxPerWarp % 32 == 0 && kPxPerWarp >= 32,
                   "each group's mask warps cover the four TMEM quadrants evenly");
     static_assert(NG2 == 1 || NG2 == 2, "one or two GEMM2 issuers");
 };
 // Index = ms_config.tc_shape.
-using TcShape0 = TcShape<16, 2, 1>;
-using TcShape1 = TcShape<16, 1, 1>;
-using TcShape2 = TcShape<8, 2, 1>;
-using TcShape3 = TcShape<8, 1, 1>;
-using TcShape4 = TcShape<16, 2, 2>;
-using TcShape5 = TcShape<16, 1, 2>;
+using TcShape0 = TcShape<16, 2, 1, 128>;
+using TcShape1 = TcShape<16, 1, 1, 128>;
+using TcShape2 = TcShape<8, 2, 1, 128>;
+using TcShape3 = TcShape<8, 1, 1, 128>;
+using TcShape4 = TcShape<16, 2, 2, 128>;
+using TcShape5 = TcShape<16, 1, 2, 128>;
+using TcShape6 = TcShape<16, 2, 2, 64>;
+using TcShape7 = TcShape<16, 1, 2, 64>;
 constexpr int kStages = 10;            // pixel-tile ring
 constexpr int kTileBytes = 128 * 128;  // 128 rows x 128 bytes
 constexpr uint32_t kTmemCols = 512;
-constexpr int kMBufs = 3;              // mask tiles in TMEM
-constexpr uint32_t kColS = 0;          // two S accumulators, 128 columns each
+constexpr int kMaxSBufs = 4, kMaxMBufs = 6;
+constexpr uint32_t kColS = 0;          // S accumulators, 256 columns
 constexpr uint32_t kColY = 256;        // one Y accumulator, 64 columns
-constexpr uint32_t kColM = 320;        // three mask tiles (GEMM2's A), 64 columns each
+constexpr uint32_t kColM = 320;        // mask buffers (GEMM2's A), 192 columns
 constexpr float kBand = 6.103515625e-05f;    // 2^-14
 constexpr float kFixScale = 68719476736.0f;  // 2^36
 
@@ -92,7 +102,7 @@ constexpr int kOffA1 = 0;                              // 2 x 16 KB
 constexpr int kOffP = 2 * kTileBytes;                  // kStages x 16 KB
 constexpr int kOffX = kOffP + kStages * kTileBytes;   // 2 x 8 KB: the item's seeds in FP32, 128 x 16
 constexpr int kOffBar = kOffX + 2 * 128 * 16 * 4;
-constexpr int kNumBars = 2 * kStages + 2 * 2 + 2 * kMBufs + 2 + 2 + 3;  // aux: GEMM1 + up to two GEMM2 issuers
+constexpr int kNumBars = 2 * kStages + 2 * kMaxSBufs + 2 * kMaxMBufs + 2 + 2 + 3;  // aux: GEMM1 + up to two GEMM2 issuers
 constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 32 + 1024;  // + TMEM slot, flags, alignment slack
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
@@ -240,8 +250,11 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
            unsigned long long* __restrict__ acc, float c_f, Map map, int* status,
            unsigned long long* band_ctr, float* __restrict__ dbg_S, int64_t dbg_stride) {
     constexpr int kGroups = Shape::kGroups, kGroupWarps = Shape::kGroupWarps;
+    constexpr int kBN = Shape::kBN, kUPS = Shape::kUPS, kSBufs = Shape::kSBufs, kMBufs = Shape::kMBufs;
     constexpr int kPxPerWarp = Shape::kPxPerWarp, kSub = Shape::kSub;
     constexpr int kWarpTma = Shape::kWarpTma, kWarpG1 = Shape::kWarpG1, kWarpG2 = Shape::kWarpG2, kG2 = Shape::kG2;
+    // GEMM2 issuers commit a stage's release after their last unit of it.
+    constexpr int kEmptyArrivals = kUPS < kG2 ? kUPS : kG2;
     if (!map.init()) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -251,29 +264,29 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
     uint64_t* bars = (uint64_t*)(smem + kOffBar);
     uint64_t* full = bars;                        // [kStages] pixel tile landed
     uint64_t* empty = full + kStages;             // [kStages] pixel tile consumed by GEMM2
-    uint64_t* s_full = empty + kStages;           // [2] GEMM1 done
-    uint64_t* s_empty = s_full + 2;               // [2] S read by the mask warps of the tile's group
-    uint64_t* m_full = s_empty + 2;               // [kMBufs] mask tile stored to TMEM by its group's warps
-    uint64_t* m_empty = m_full + kMBufs;          // [kMBufs] mask tile consumed by GEMM2
-    uint64_t* a1_full = m_empty + kMBufs;         // [2] seed operand written
+    uint64_t* s_full = empty + kStages;           // [kSBufs] GEMM1 of a unit done
+    uint64_t* s_empty = s_full + kMaxSBufs;       // [kSBufs] S read by the mask warps of the unit's group
+    uint64_t* m_full = s_empty + kMaxSBufs;       // [kMBufs] mask of a unit stored to TMEM by its group's warps
+    uint64_t* m_empty = m_full + kMaxMBufs;       // [kMBufs] mask consumed by GEMM2
+    uint64_t* a1_full = m_empty + kMaxMBufs;      // [2] seed operand written
     uint64_t* d_full = a1_full + 2;               // Y of an item complete
     uint64_t* d_empty = d_full + 1;               // Y read by the epilogue
     uint64_t* aux = d_empty + 1;                  // [1 + kG2] drain barriers of the MMA issuers
     uint32_t* tmem_slot = (uint32_t*)(bars + kNumBars);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
-    volatile int* g2_next = (volatile int*)(tmem_slot + 2);  // the next tile whose GEMM2 may be issued
+    volatile int* g2_next = (volatile int*)(tmem_slot + 2);  // the next unit whose GEMM2 may be issued
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], kEmptyArrivals);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kSBufs; ++b) {
             mbar_init(&s_full[b], 1);
             mbar_init(&s_empty[b], kGroupWarps);
-            mbar_init(&a1_full[b], 128);
         }
+        for (int b = 0; b < 2; ++b) mbar_init(&a1_full[b], 128);
         for (int b = 0; b < kMBufs; ++b) {
             mbar_init(&m_full[b], kGroupWarps);
             mbar_init(&m_empty[b], 1);
@@ -318,32 +331,37 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
             for (int q = max(0, g - kStages); q < g; ++q) drain_wait(&full[q % kStages], (q / kStages) & 1);
     } else if (warp == kWarpG1) {
         // ------------------------------------------------ GEMM1 issuer
-        // Runs ahead of the mask warps as far as the two S buffers allow.
+        // Runs ahead of the mask warps as far as the S buffers allow.
         // Descriptors are built once; moving an operand by b bytes adds b >> 4
         // to the descriptor's start-address field (no carry: shared addresses
         // stay below 2^18).
         const uint64_t dA1 = desc_sw128(smem_u32(A1), 16, 1024);   // seed operand, K-major
         const uint64_t dP1 = desc_sw128(smem_u32(Pst), 16, 1024);  // pixel tile, K-major
-        constexpr uint32_t id1 = idesc_bf16(128, 128, 0, 0);
+        constexpr uint32_t id1 = idesc_bf16(128, kBN, 0, 0);
         constexpr uint64_t kT = kTileBytes >> 4;
+        constexpr uint64_t kU = (kBN * 128) >> 4;  // one unit of pixel rows
         bool ok = true;
         int g = 0, it = 0;
         for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
             const TcItem ii = map.item(item);
             if (!(ok = warp_wait(&a1_full[it & 1], (it >> 1) & 1, abort))) break;
             const uint64_t a = dA1 + (uint64_t)(it & 1) * kT;
-            for (int pt = ii.pt0; pt < ii.pt1; ++pt, ++g) {
-                const int s = g % kStages, b = g & 1;
+            for (int pt = ii.pt0; pt < ii.pt1 && ok; ++pt, ++g) {
+                const int s = g % kStages;
                 if (!(ok = warp_wait(&full[s], (g / kStages) & 1, abort))) break;
-                if (g >= 2 && !(ok = warp_wait(&s_empty[b], ((g >> 1) - 1) & 1, abort))) break;
-                tc_fence_after();
-                const uint32_t tS = tmem + kColS + b * 128;
-                const uint64_t pb = dP1 + (uint64_t)s * kT;
-                mma_bf16_warp(tS, a, pb, id1, 0);            // Xh . Ph
-                mma_bf16_warp(tS, a, pb + 2, id1, 1);        // Xh . Pm
-                mma_bf16_warp(tS, a + 2, pb, id1, 1);        // Xl . Ph
-                mma_bf16_warp(tS, a + 4, pb + 6, id1, 1);    // -c split . ones
-                mma_commit_warp(&s_full[b]);
+#pragma unroll
+                for (int hh = 0; hh < kUPS; ++hh) {
+                    const int u = g * kUPS + hh, b = u % kSBufs;
+                    if (u >= kSBufs && !(ok = warp_wait(&s_empty[b], ((u / kSBufs) - 1) & 1, abort))) break;
+                    tc_fence_after();
+                    const uint32_t tS = tmem + kColS + b * kBN;
+                    const uint64_t pb = dP1 + (uint64_t)s * kT + hh * kU;
+                    mma_bf16_warp(tS, a, pb, id1, 0);            // Xh . Ph
+                    mma_bf16_warp(tS, a, pb + 2, id1, 1);        // Xh . Pm
+                    mma_bf16_warp(tS, a + 2, pb, id1, 1);        // Xl . Ph
+                    mma_bf16_warp(tS, a + 4, pb + 6, id1, 1);    // -c split . ones
+                    mma_commit_warp(&s_full[b]);
+                }
             }
         }
         if (__any_sync(0xffffffffu, *abort)) {
@@ -352,57 +370,62 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
         }
     } else if (warp >= kWarpG2 && warp < kWarpG2 + kG2) {
         // ------------------------------------------------ GEMM2 issuers
-        // Y += Mask . P as soon as a mask tile is in TMEM; the pixel stage is
-        // released when these MMAs complete. With two issuers, warps on
-        // different sub-partitions take even and odd tiles, so neither
+        // Y += Mask . P as soon as a unit's mask is in TMEM; the pixel stage
+        // is released when the MMAs of its units complete. With two issuers,
+        // warps on different sub-partitions take alternate units, so neither
         // sub-partition's mask warps carry all of GEMM2's issue cost. Y
-        // accumulates in tile order: a warp issues tile g only after tile g-1
+        // accumulates in unit order: a warp issues unit u only after unit u-1
         // was issued (g2_next, with tcgen05 fences around the hand-over).
-        // Each warp commits the releases of the tiles it issued, and every
-        // issuer commits d_full at an item's end (a commit covers only its own
-        // thread's MMAs).
+        // Each warp commits the releases of the units it issued (a stage's
+        // release after its last unit of that stage), and every issuer commits
+        // d_full at an item's end (a commit covers only its own thread's MMAs).
         const int par = warp - kWarpG2;
         const uint64_t dP2 = desc_sw128(smem_u32(Pst), kTileBytes, 1024);  // pixel tile, MN-major
         constexpr uint32_t id2 = idesc_bf16(128, 64, 0, 1);
         constexpr uint64_t kT = kTileBytes >> 4;
+        constexpr int kK2 = kBN / 16;  // K = 16 pixels per MMA
         bool ok = true;
         int g = 0, it = 0;
         for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
             const TcItem ii = map.item(item);
-            for (int pt = ii.pt0; pt < ii.pt1; ++pt, ++g) {
-                if (g % kG2 != par) continue;
-                const int s = g % kStages, mb = g % kMBufs;
-                const bool first = pt == ii.pt0;
-                if (!(ok = warp_wait(&m_full[mb], (g / kMBufs) & 1, abort))) break;
-                if (!(ok = warp_wait(&full[s], (g / kStages) & 1, abort))) break;
-                if (first && it >= 1 && !(ok = warp_wait(d_empty, (it - 1) & 1, abort))) break;
-                if constexpr (kG2 > 1) {
-                    const long long t0 = clock64();
-                    bool turn = true;
-                    while (*g2_next != g) {
-                        if (*abort || clock64() - t0 > kWaitCycles) {
-                            *abort = 1;
-                            turn = false;
-                            break;
-                        }
-                    }
-                    if (!(ok = __all_sync(0xffffffffu, turn))) break;
-                }
-                tc_fence_after();
-                const uint32_t tY = tmem + kColY;
-                const uint32_t tM = tmem + kColM + mb * 64;
-                const uint64_t pb = dP2 + (uint64_t)s * kT;
+            for (int pt = ii.pt0; pt < ii.pt1 && ok; ++pt, ++g) {
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    mma_bf16_ts_warp(tY, tM + 8 * k, pb + k * 128, id2, (first && k == 0) ? 0u : 1u);
-                mma_commit_warp(&m_empty[mb]);
-                mma_commit_warp(&empty[s]);
-                if constexpr (kG2 > 1) {  // one thread's MMAs execute in issue order: no hand-over
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) {
-                        __threadfence_block();
-                        *g2_next = g + 1;
+                for (int hh = 0; hh < kUPS; ++hh) {
+                    const int u = g * kUPS + hh;
+                    if (u % kG2 != par) continue;
+                    const int s = g % kStages, mb = u % kMBufs;
+                    const bool first = pt == ii.pt0 && hh == 0;
+                    if (!(ok = warp_wait(&m_full[mb], (u / kMBufs) & 1, abort))) break;
+                    if (!(ok = warp_wait(&full[s], (g / kStages) & 1, abort))) break;
+                    if (first && it >= 1 && !(ok = warp_wait(d_empty, (it - 1) & 1, abort))) break;
+                    if constexpr (kG2 > 1) {
+                        const long long t0 = clock64();
+                        bool turn = true;
+                        while (*g2_next != u) {
+                            if (*abort || clock64() - t0 > kWaitCycles) {
+                                *abort = 1;
+                                turn = false;
+                                break;
+                            }
+                        }
+                        if (!(ok = __all_sync(0xffffffffu, turn))) break;
+                    }
+                    tc_fence_after();
+                    const uint32_t tY = tmem + kColY;
+                    const uint32_t tM = tmem + kColM + mb * (kBN / 2);
+                    const uint64_t pb = dP2 + (uint64_t)s * kT + hh * kK2 * 128;
+#pragma unroll
+                    for (int k = 0; k < kK2; ++k)
+                        mma_bf16_ts_warp(tY, tM + 8 * k, pb + k * 128, id2, (first && k == 0) ? 0u : 1u);
+                    mma_commit_warp(&m_empty[mb]);
+                    if (hh >= kUPS - kG2) mma_commit_warp(&empty[s]);
+                    if constexpr (kG2 > 1) {  // one thread's MMAs execute in issue order: no hand-over
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) {
+                            __threadfence_block();
+                            *g2_next = u + 1;
+                        }
                     }
                 }
             }
@@ -415,9 +438,9 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
         }
     } else {
         // ------------------------------------------------ mask warps
-        // Group grp of kGroups takes the tiles g with g % kGroups == grp; in a
+        // Group grp of kGroups takes the units u with u % kGroups == grp; in a
         // group, warp w reaches TMEM lanes 32 * (w % 4) + 0..31 (its seeds) and
-        // builds the mask of kPxPerWarp pixels, 32 at a time.
+        // builds the mask of kPxPerWarp pixels of the unit, 32 at a time.
         const int grp = warp / kGroupWarps;
         const int q = warp & 3;                         // TMEM lane quadrant
         const int h = (warp % kGroupWarps) >> 2;        // which kPxPerWarp pixels of a tile
@@ -468,96 +491,100 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
             bool ok = warp_wait(&a1_full[it & 1], (it >> 1) & 1, abort);
             const float* xs = Xs + (it & 1) * 128 * 16 + r * 16;
             for (int pt = pt0; pt < pt1 && ok; ++pt, ++g) {
-                const int mb = mbn, mph = mphn;
-                if (++mbn == kMBufs) {
-                    mbn = 0;
-                    mphn ^= 1;
-                }
-                if (kGroups > 1 && g % kGroups != grp) continue;
-                const int b = g & 1;
-                if (!(ok = warp_wait(&s_full[b], (g >> 1) & 1, abort))) break;
-                tc_fence_after();
-                uint32_t w[kEarlyStore ? 1 : kSub][16];
-                bool staged = false;  // pixel stage known to be complete (band path)
 #pragma unroll
-                for (int j = 0; j < kSub; ++j) {
-                    uint32_t (&wj)[16] = w[kEarlyStore ? 0 : j];
-                    uint32_t v[32];
-                    float mn;
-                    tmem_ld32_minabs(tmem + kColS + b * 128 + lane_base + h * kPxPerWarp + j * 32, v, &mn);
-                    tmem_ld_wait();
-                    if (j == kSub - 1) {  // S read: hand the buffer back to GEMM1
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&s_empty[b]);
+                for (int hh = 0; hh < kUPS; ++hh) {
+                    const int u = g * kUPS + hh;  // unit: BN pixels of stage g
+                    const int mb = mbn, mph = mphn;
+                    if (++mbn == kMBufs) {
+                        mbn = 0;
+                        mphn ^= 1;
                     }
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) wj[i] = ~sign_halves(v[2 * i], v[2 * i + 1]) & 0x3F803F80u;
-                    if (__any_sync(0xffffffffu, mn < kBand)) {
-                        // Re-decide near-boundary pairs with the FP32 form's dot
-                        // product against the exact FP32 pixel rebuilt from the
-                        // tile in shared memory. Bit masks keep register-array
-                        // indices static.
-                        const int s = g % kStages;
-                        if (!staged && !(ok = warp_wait(&full[s], (g / kStages) & 1, abort))) break;
-                        staged = true;
-                        const uint8_t* stage = Pst + s * kTileBytes;
-                        float x[16];  // the seed (a padding row: zeros)
-#pragma unroll
-                        for (int k = 0; k < 16; k += 4) {
-                            const float4 t4 = *reinterpret_cast<const float4*>(xs + k);
-                            x[k] = t4.x; x[k + 1] = t4.y; x[k + 2] = t4.z; x[k + 3] = t4.w;
+                    if (kGroups > 1 && u % kGroups != grp) continue;
+                    const int b = u % kSBufs;
+                    if (!(ok = warp_wait(&s_full[b], (u / kSBufs) & 1, abort))) break;
+                    tc_fence_after();
+                    uint32_t w[kEarlyStore ? 1 : kSub][16];
+                    bool staged = false;  // pixel stage known to be complete (band path)
+    #pragma unroll
+                    for (int j = 0; j < kSub; ++j) {
+                        uint32_t (&wj)[16] = w[kEarlyStore ? 0 : j];
+                        uint32_t v[32];
+                        float mn;
+                        tmem_ld32_minabs(tmem + kColS + b * kBN + lane_base + h * kPxPerWarp + j * 32, v, &mn);
+                        tmem_ld_wait();
+                        if (j == kSub - 1) {  // S read: hand the buffer back to GEMM1
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&s_empty[b]);
                         }
-                        uint32_t bandm = 0;
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) bandm |= (uint32_t)(fabsf(__uint_as_float(v[i])) < kBand) << i;
-                        uint32_t inm = 0, todo = bandm;
-                        while (todo) {
-                            const int i = __ffs(todo) - 1;
-                            todo &= todo - 1;
-                            const int row = h * kPxPerWarp + j * 32 + i;
-                            if (pt * 128 + row < ii.n) {
-                                ++band_local;
-                                float pv[16];
-                                stage_pixel(stage, row, pv);
-                                if (dot_seq<16>(x, pv) >= c_f) inm |= 1u << i;
+    #pragma unroll
+                        for (int i = 0; i < 16; ++i) wj[i] = ~sign_halves(v[2 * i], v[2 * i + 1]) & 0x3F803F80u;
+                        if (__any_sync(0xffffffffu, mn < kBand)) {
+                            // Re-decide near-boundary pairs with the FP32 form's dot
+                            // product against the exact FP32 pixel rebuilt from the
+                            // tile in shared memory. Bit masks keep register-array
+                            // indices static.
+                            const int s = g % kStages;
+                            if (!staged && !(ok = warp_wait(&full[s], (g / kStages) & 1, abort))) break;
+                            staged = true;
+                            const uint8_t* stage = Pst + s * kTileBytes;
+                            float x[16];  // the seed (a padding row: zeros)
+    #pragma unroll
+                            for (int k = 0; k < 16; k += 4) {
+                                const float4 t4 = *reinterpret_cast<const float4*>(xs + k);
+                                x[k] = t4.x; x[k + 1] = t4.y; x[k + 2] = t4.z; x[k + 3] = t4.w;
+                            }
+                            uint32_t bandm = 0;
+    #pragma unroll
+                            for (int i = 0; i < 32; ++i) bandm |= (uint32_t)(fabsf(__uint_as_float(v[i])) < kBand) << i;
+                            uint32_t inm = 0, todo = bandm;
+                            while (todo) {
+                                const int i = __ffs(todo) - 1;
+                                todo &= todo - 1;
+                                const int row = hh * kBN + h * kPxPerWarp + j * 32 + i;
+                                if (pt * 128 + row < ii.n) {
+                                    ++band_local;
+                                    float pv[16];
+                                    stage_pixel(stage, row, pv);
+                                    if (dot_seq<16>(x, pv) >= c_f) inm |= 1u << i;
+                                }
+                            }
+    #pragma unroll
+                            for (int k = 0; k < 16; ++k) {
+                                const uint32_t bm = (bandm >> (2 * k)) & 3u;
+                                const uint32_t im = (inm >> (2 * k)) & 3u;
+                                const uint32_t clear = ((bm & 1u) ? 0x3F80u : 0u) | ((bm & 2u) ? 0x3F800000u : 0u);
+                                const uint32_t set = ((im & 1u) ? 0x3F80u : 0u) | ((im & 2u) ? 0x3F800000u : 0u);
+                                wj[k] = (wj[k] & ~clear) | set;
                             }
                         }
-#pragma unroll
-                        for (int k = 0; k < 16; ++k) {
-                            const uint32_t bm = (bandm >> (2 * k)) & 3u;
-                            const uint32_t im = (inm >> (2 * k)) & 3u;
-                            const uint32_t clear = ((bm & 1u) ? 0x3F80u : 0u) | ((bm & 2u) ? 0x3F800000u : 0u);
-                            const uint32_t set = ((im & 1u) ? 0x3F80u : 0u) | ((im & 2u) ? 0x3F800000u : 0u);
-                            wj[k] = (wj[k] & ~clear) | set;
+                        if (kDebug) {
+    #pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                dbg_S[(int64_t)r * dbg_stride + pt * 128 + hh * kBN + h * kPxPerWarp + j * 32 + i] =
+                                    __uint_as_float(v[i]);
+                        }
+                        if constexpr (kEarlyStore) {
+                            if (j == 0) {
+                                if (u >= kMBufs && !(ok = warp_wait(&m_empty[mb], mph ^ 1, abort))) break;
+                                tc_fence_after();
+                            }
+                            tmem_st16(tmem + kColM + mb * (kBN / 2) + lane_base + h * (kPxPerWarp / 2) + j * 16, wj);
                         }
                     }
-                    if (kDebug) {
-#pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            dbg_S[(int64_t)r * dbg_stride + pt * 128 + h * kPxPerWarp + j * 32 + i] =
-                                __uint_as_float(v[i]);
+                    if (!ok) break;
+                    if constexpr (!kEarlyStore) {
+                        if (u >= kMBufs && !(ok = warp_wait(&m_empty[mb], mph ^ 1, abort))) break;
+                        tc_fence_after();
+    #pragma unroll
+                        for (int j = 0; j < kSub; ++j)
+                            tmem_st16(tmem + kColM + mb * (kBN / 2) + lane_base + h * (kPxPerWarp / 2) + j * 16, w[j]);
                     }
-                    if constexpr (kEarlyStore) {
-                        if (j == 0) {
-                            if (g >= kMBufs && !(ok = warp_wait(&m_empty[mb], mph ^ 1, abort))) break;
-                            tc_fence_after();
-                        }
-                        tmem_st16(tmem + kColM + mb * 64 + lane_base + h * (kPxPerWarp / 2) + j * 16, wj);
-                    }
+                    tmem_st_wait();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&m_full[mb]);
                 }
-                if (!ok) break;
-                if constexpr (!kEarlyStore) {
-                    if (g >= kMBufs && !(ok = warp_wait(&m_empty[mb], mph ^ 1, abort))) break;
-                    tc_fence_after();
-#pragma unroll
-                    for (int j = 0; j < kSub; ++j)
-                        tmem_st16(tmem + kColM + mb * 64 + lane_base + h * (kPxPerWarp / 2) + j * 16, w[j]);
-                }
-                tmem_st_wait();
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&m_full[mb]);
             }
             if (!ok) break;
             if (lead) {
@@ -635,6 +662,8 @@ ms_status with_tc_shape(int shape, Fn&& fn) {
         case 3: return fn(TcShape3{});
         case 4: return fn(TcShape4{});
         case 5: return fn(TcShape5{});
+        case 6: return fn(TcShape6{});
+        case 7: return fn(TcShape7{});
         default: return set_error(MS_ERR_INVALID_ARG, "unknown tile shape %d", shape);
     }
 }

@@ -216,7 +216,7 @@ def test_batch_autotune_picks_a_candidate_and_keeps_results_valid(ms_lib):
         # phase 2: the other tile shapes on phase 1's fastest split
         best = min(res[:5], key=lambda r: r["ms"])
         assert [(r["batch_split"], r["target_mult"], r["tc_shape"]) for r in res[5:]] == \
-            [(best["batch_split"], best["target_mult"], sh) for sh in (1, 2, 3, 4, 5)]
+            [(best["batch_split"], best["target_mult"], sh) for sh in (1, 2, 3, 4, 5, 6, 7)]
         assert all(r["ms"] > 0 for r in res)
         # the batch now holds the fastest candidate's outputs: still within the oracle bar
         for i, f in enumerate(fs[:2]):
@@ -227,12 +227,12 @@ def test_batch_autotune_picks_a_candidate_and_keeps_results_valid(ms_lib):
         # configuring the canonical split again reproduces single-frame results
         # exactly, on every tile shape
         lab_s, modes_s, _ = _single(ms_lib, embs[0], masks[0], 0, precision=ms_lib.MS_BF16)
-        for sh in range(6):
+        for sh in range(8):
             ms_lib.ms_batch_configure(b, 0, 2, sh)
             ms_lib.ms_batch_run(b)
             assert np.array_equal(ms_lib.ms_batch_modes(b, 0), modes_s), sh
             assert np.array_equal(b.labels[0].cpu().numpy(), lab_s), sh
         with pytest.raises(ms_lib.MsError):
-            ms_lib.ms_batch_configure(b, 0, 2, 6)
+            ms_lib.ms_batch_configure(b, 0, 2, 8)
     finally:
         b.close()

@@ -250,7 +250,7 @@ def test_c2_frames_batched_as_benchmarked(ms_lib):
         single = ms_lib.cluster(embs[0], masks[0], precision=ms_lib.MS_BF16)
         _sampled_checks(fs[0], canon_labels, canon_modes, single.stats["seed_log"])
         res = ms_lib.ms_batch_autotune(b, reps=1)
-        assert len(res) == 10
+        assert len(res) == 12
         modes = ms_lib.ms_batch_modes(b, 0)
         assert abs(modes.shape[0] - ref["n_modes"]) <= ref["n_modes"] // 1000
         assert mode_errors(modes, canon_modes).max() <= 1e-5

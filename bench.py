@@ -434,7 +434,8 @@ def roofline_of(form, tot, step_ms, clk, n_sm):
 def vmf_leg(n_sm, clk):
     """Smooth-kernel form on the differentiable configuration: N = 65536 pixels,
     M = 1024 seeds, d = 16, kappa = 20, T = 10. Times ms_vmf_forward and
-    ms_vmf_backward (CUDA events, median of 5 after 2 warm-ups).
+    ms_vmf_backward (CUDA events, median of 5 after 2 warm-ups), in FP32 and
+    with the forward steps on the tensor cores (MS_BF16).
 
     Bound: FP32 FMA on the CUDA cores. Per seed-pixel pair and step the
     forward does the 16-term dot product and the 16-term weighted sum (4d = 64
@@ -473,13 +474,31 @@ def vmf_leg(n_sm, clk):
     fma_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 TFLOP/s: 128 FMA lanes per SM
     f_tf = 64 * pairs / (fwd * 1e-3) / 1e12
     b_tf = 288 * pairs / (bwd * 1e-3) / 1e12
+    # BF16 form: every forward step on the tensor cores (k_vmf_tc + its reduce);
+    # a step's time is the slope between T = 10 and T = 1 calls (the call's
+    # fixed cost -- packing the pixels, one synchronisation -- cancels).
+    BF = ms.MS_BF16
+    fwd_b = timed_ms(lambda: ms.ms_vmf_forward(P, X0, kappa, T, precision=BF))
+    fwd_b1 = timed_ms(lambda: ms.ms_vmf_forward(P, X0, kappa, 1, precision=BF))
+    bwd_b = timed_ms(lambda: ms.ms_vmf_backward(P, X0, kappa, T, G, precision=BF))
+    step_b = (fwd_b - fwd_b1) / (T - 1)
+    bf16_peak = load_peaks().get("bf16_tflops")
+    step_tf = 64 * 65536 * 1024 / (step_b * 1e-3) / 1e12
+    xf = ms.ms_vmf_forward(P, X0, kappa, T)
+    xb = ms.ms_vmf_forward(P, X0, kappa, T, precision=BF)
     return {"config": "N=65536 pixels, M=1024 seeds, d=16, kappa=20, T=10 (synthetic vMF cells)",
             "forward_ms": fwd, "backward_ms": bwd,
             "bound": "fp32 fma", "unit": "TFLOP/s",
             "forward_achieved": f_tf, "backward_achieved": b_tf, "peak": fma_peak,
             "forward_frac": f_tf / fma_peak, "backward_frac": b_tf / fma_peak,
             "algorithmic": "64 flops per seed-pixel pair and step (forward); 288 (adjoint, with the re-run forward)",
-            "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz (nominal CUDA-core rate)"}
+            "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz (nominal CUDA-core rate)",
+            "bf16": {"forward_ms": fwd_b, "forward_T1_ms": fwd_b1, "backward_ms": bwd_b, "step_ms": step_b,
+                     "bound": "tensor", "step_achieved": step_tf, "peak": bf16_peak,
+                     "step_frac": (step_tf / bf16_peak) if bf16_peak else None,
+                     "peak_source": "of measured: cuBLAS bf16 dense, burst (MEASURED_PEAKS.json)",
+                     "max_abs_diff_vs_fp32_form": float((xb - xf).abs().max().item()),
+                     "note": "forward steps on the tensor cores; the adjoint passes stay FP32 SIMT"}}
 
 
 def kernel_variants_leg(n_sm, clk):

@@ -238,14 +238,31 @@ MS_API ms_status ms_run_host(const ms_config* cfg, const float* h_emb, const uin
  * ms_vmf_backward takes d_GT = dL/dx_T [M, dim] and writes dL/dP to d_dP
  * [N, dim] and dL/dx_0 to d_dX0 [M, dim]. It recomputes the iterates by
  * re-running the forward and recomputes every kernel weight on the fly; no
- * M x N matrix is stored. Both allocate their workspace stream-ordered
- * (cudaMallocAsync) on `stream` and return without synchronising. Results are
+ * M x N matrix is stored. Both allocate their workspace stream-ordered on
+ * `stream` from the library's own memory pool (which keeps freed memory mapped
+ * for the next call) and return without synchronising. Results are
  * deterministic. MS_ERR_INVALID_ARG on NULL pointers or bad sizes. */
 MS_API ms_status ms_vmf_forward(const float* d_P, int64_t N, const float* d_X0, int32_t M, int32_t dim,
                                 double kappa, int32_t T, float* d_XT, void* stream);
 MS_API ms_status ms_vmf_backward(const float* d_P, int64_t N, const float* d_X0, int32_t M, int32_t dim,
                                  double kappa, int32_t T, const float* d_GT, float* d_dP, float* d_dX0,
                                  void* stream);
+/* The same with a precision: MS_FP32 is the calls above; MS_BF16 runs every
+ * forward step on the tensor cores. There, GEMM1 scores kappa log2(e) (s - 1)
+ * from three-term BF16 splits of kappa log2(e) x and of p (six products, FP32
+ * accumulation), the weight w = exp(kappa (s - 1)) is formed in FP32 and split
+ * as w = wh + wl (BF16), and GEMM2 accumulates wh.[ph | pm | pl] + wl.[ph | pm]
+ * in FP32; per-chunk sums are
+ * added in a fixed order, so results are deterministic. The adjoint passes of
+ * ms_vmf_backward_ex stay FP32 and differentiate the BF16 iterates. With
+ * MS_BF16 the call synchronises `stream` once at the end to read the device
+ * status: MS_ERR_TIMEOUT if a bounded wait inside the kernel gave up (the
+ * outputs are then NaN). */
+MS_API ms_status ms_vmf_forward_ex(const float* d_P, int64_t N, const float* d_X0, int32_t M, int32_t dim,
+                                   double kappa, int32_t T, int32_t precision, float* d_XT, void* stream);
+MS_API ms_status ms_vmf_backward_ex(const float* d_P, int64_t N, const float* d_X0, int32_t M, int32_t dim,
+                                    double kappa, int32_t T, int32_t precision, const float* d_GT, float* d_dP,
+                                    float* d_dX0, void* stream);
 
 /* Other distances and kernel profiles (Eq. 2-6 with Eq. 3, 4 and 9): T steps
  * of the dense mean-shift update, every seed against every vector,
@@ -258,8 +275,8 @@ MS_API ms_status ms_vmf_backward(const float* d_P, int64_t N, const float* d_X0,
  * d_XT: device float32 [M, dim] receives x_T; d_counts (nullable): device int32
  * [M] receives each seed's count of vectors with nonzero weight in the last
  * step. 1 <= dim <= 32, h > 0, T >= 0. FP32 arithmetic; results are
- * deterministic. Allocates its workspace stream-ordered (cudaMallocAsync) on
- * `stream` and synchronises it once, after validating the inputs on the
+ * deterministic. Allocates its workspace stream-ordered on `stream` from the
+ * library's own memory pool and synchronises it once, after validating the inputs on the
  * device: MS_ERR_INVALID_ARG for a non-finite component or (cosine) a zero
  * norm. */
 #define MS_DIST_COSINE 0

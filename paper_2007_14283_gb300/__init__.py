@@ -88,6 +88,8 @@ _SIGNATURES = {
     "ms_window_sums_static": (_i32, [_vp, _i32, _vp, _i32, ctypes.c_double, _vp, _vp]),
     "ms_vmf_forward": (_i32, [_vp, _i64, _vp, _i32, _i32, ctypes.c_double, _i32, _vp, _vp]),
     "ms_vmf_backward": (_i32, [_vp, _i64, _vp, _i32, _i32, ctypes.c_double, _i32, _vp, _vp, _vp, _vp]),
+    "ms_vmf_forward_ex": (_i32, [_vp, _i64, _vp, _i32, _i32, ctypes.c_double, _i32, _i32, _vp, _vp]),
+    "ms_vmf_backward_ex": (_i32, [_vp, _i64, _vp, _i32, _i32, ctypes.c_double, _i32, _i32, _vp, _vp, _vp, _vp]),
     "ms_run_host": (_i32, [ctypes.POINTER(ms_config), _vp, _vp, _i64, _vp, _vp, _vp, _i32, _pi32,
                            ctypes.POINTER(ms_stats)]),
     "ms_batch_create": (_i32, [ctypes.POINTER(ms_config), _i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
@@ -314,26 +316,36 @@ def ms_kernel_shift(P, X0, distance: int, profile: int, h: float, T: int, stream
     return XT, counts
 
 
-def ms_vmf_forward(P, X0, kappa: float, T: int, stream=None):
-    """x_T of T smooth-kernel steps. P CUDA float32 [N, 16], X0 [M, 16]."""
+def ms_vmf_forward(P, X0, kappa: float, T: int, stream=None, precision: int = MS_FP32):
+    """x_T of T smooth-kernel steps. P CUDA float32 [N, 16], X0 [M, 16].
+    precision MS_BF16 runs the steps on the tensor cores."""
     import torch
     XT = torch.empty_like(X0)
-    _check(load().ms_vmf_forward(_dptr(P, torch.float32, "P"), P.shape[0], _dptr(X0, torch.float32, "X0"),
-                                 X0.shape[0], X0.shape[1], float(kappa), int(T), _dptr(XT, torch.float32, "XT"),
-                                 _stream_handle(stream)))
+    _check(load().ms_vmf_forward_ex(_dptr(P, torch.float32, "P"), P.shape[0], _dptr(X0, torch.float32, "X0"),
+                                    X0.shape[0], X0.shape[1], float(kappa), int(T), int(precision),
+                                    _dptr(XT, torch.float32, "XT"), _stream_handle(stream)))
     return XT
 
 
-def ms_vmf_backward(P, X0, kappa: float, T: int, GT, stream=None):
-    """(dL/dP, dL/dX0) for upstream gradient GT = dL/dx_T."""
+def ms_vmf_backward(P, X0, kappa: float, T: int, GT, stream=None, precision: int = MS_FP32):
+    """(dL/dP, dL/dX0) for upstream gradient GT = dL/dx_T (the iterates are
+    recomputed in `precision`; the adjoint passes are FP32)."""
     import torch
     dP = torch.empty_like(P)
     dX0 = torch.empty_like(X0)
-    _check(load().ms_vmf_backward(_dptr(P, torch.float32, "P"), P.shape[0], _dptr(X0, torch.float32, "X0"),
-                                  X0.shape[0], X0.shape[1], float(kappa), int(T),
-                                  _dptr(GT.contiguous(), torch.float32, "GT"), _dptr(dP, torch.float32, "dP"),
-                                  _dptr(dX0, torch.float32, "dX0"), _stream_handle(stream)))
+    _check(load().ms_vmf_backward_ex(_dptr(P, torch.float32, "P"), P.shape[0], _dptr(X0, torch.float32, "X0"),
+                                     X0.shape[0], X0.shape[1], float(kappa), int(T), int(precision),
+                                     _dptr(GT.contiguous(), torch.float32, "GT"), _dptr(dP, torch.float32, "dP"),
+                                     _dptr(dX0, torch.float32, "dX0"), _stream_handle(stream)))
     return dP, dX0
+
+
+def ms_vmf_forward_ex(P, X0, kappa: float, T: int, precision: int, stream=None):
+    return ms_vmf_forward(P, X0, kappa, T, stream, precision)
+
+
+def ms_vmf_backward_ex(P, X0, kappa: float, T: int, precision: int, GT, stream=None):
+    return ms_vmf_backward(P, X0, kappa, T, GT, stream, precision)
 
 
 def ms_get_state(ctx: Context) -> int:

@@ -16,6 +16,8 @@
 
 #include "ms_internal.cuh"
 
+#include <mutex>
+
 namespace ms {
 
 static thread_local char g_err[512] = "";
@@ -39,6 +41,37 @@ cudaError_t workspace_malloc(void** p, size_t bytes) {
         return cudaErrorMemoryAllocation;
     }
     return cudaMalloc(p, bytes);
+}
+
+// The library's own stream-ordered pool on each device. It keeps freed memory
+// mapped (release threshold: never), so calls that allocate a workspace per
+// call and synchronise do not re-map it each time; the process's default
+// pool is left as the caller configured it.
+cudaError_t scratch_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, st);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            if ((e = cudaMemPoolCreate(&pools[dev], &props)) != cudaSuccess) {
+                pools[dev] = nullptr;
+                return e;
+            }
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        pool = pools[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
 }
 
 ms_status cuda_check(cudaError_t e, const char* what) {

@@ -155,6 +155,8 @@ ms_status cuda_check(cudaError_t e, const char* what);
 // cudaMalloc of a context's or batch's workspace, failing first when a test
 // asked for it through ms_inject_alloc_failure (ms_api.cu).
 cudaError_t workspace_malloc(void** p, size_t bytes);
+// Stream-ordered scratch from the library's own pool (kept mapped between calls); free with cudaFreeAsync.
+cudaError_t scratch_malloc_async(void** p, size_t bytes, cudaStream_t st);
 #define MS_CUDA(call)                                                 \
     do {                                                              \
         ms_status _s = ::ms::cuda_check((call), #call);               \
@@ -194,5 +196,18 @@ int64_t carried_n(const ms_ctx* ctx);   // the N a video carries into its next f
 ms_status launch_shift_tc(ms_ctx* ctx, const int32_t* active, int grid, int target_items, float* dbg_S);
 int tc_smem_bytes();
 constexpr int kTcShapes = 8;  // values of ms_config.tc_shape (warp arrangements of k_shift_tc)
+ms_status encode_pk_map(void* Pk, int rows, CUtensorMap* map);  // ms_shift_tc.cu: TMA map of split rows
+
+// ms_vmf_tc.cu: the smooth-kernel step on the tensor cores.
+struct VmfTcPlan {
+    int n_ptiles, chunks, tpc, items, grid;  // 128-pixel tiles, chunks of tpc tiles, work items, CTAs
+};
+VmfTcPlan vmf_tc_plan(int32_t M, int64_t N, int grid);
+size_t vmf_tc_pk_bytes(int64_t N);
+// Packs P [N, 16] into BF16 split rows and encodes their TMA map (on st).
+ms_status vmf_tc_prepare(const float* P, int64_t N, void* Pk, CUtensorMap* map, cudaStream_t st);
+// One step x_t -> x_{t+1}; partial holds plan.items x 128 x 16 floats.
+ms_status vmf_tc_step(const CUtensorMap& map, const float* Xt, int32_t M, float kappa, const VmfTcPlan& plan,
+                      float* partial, int* status, float* Xn, float* ynorm, cudaStream_t st);
 
 }  // namespace ms

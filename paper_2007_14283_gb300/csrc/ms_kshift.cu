@@ -272,7 +272,7 @@ extern "C" ms_status ms_kernel_shift(const float* d_P, int64_t N, const float* d
     const size_t pw_b = (size_t)N * Dp * sizeof(float), x_b = (size_t)M * Dp * sizeof(float);
     const size_t part_b = (size_t)sp.tiles * sp.chunks * (Dp + 2) * seeds * sizeof(float);
     char* b = nullptr;
-    MS_CUDA(cudaMallocAsync((void**)&b, pw_b + x_b + part_b + 1024, st));
+    MS_CUDA(scratch_malloc_async((void**)&b, pw_b + x_b + part_b + 1024, st));
     float* Pw = (float*)b;
     float* X = (float*)(b + (pw_b + 255) / 256 * 256);
     float* partial = (float*)((char*)X + (x_b + 255) / 256 * 256);

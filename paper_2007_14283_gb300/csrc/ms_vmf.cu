@@ -291,6 +291,12 @@ k_vmf_bwd_pixels(const float* __restrict__ P, int64_t N, const float* __restrict
 }
 
 struct VmfWork {
+    bool tc;        // steps on the tensor cores (BF16 splits); the adjoint passes stay FP32
+    void* Pk;       // tc: BF16 split rows of P
+    float* tc_partial;
+    int* status;    // tc: raised by a bounded wait that gave up
+    CUtensorMap pmap;
+    VmfTcPlan plan;
     float* partial;
     float* iters;   // [T+1, M, 16]
     float* ynorm;   // [T, M]
@@ -318,15 +324,25 @@ ms_status vmf_validate(const float* P, int64_t N, const float* X0, int32_t M, in
     return MS_OK;
 }
 
-ms_status vmf_alloc(VmfWork* w, int64_t N, int32_t M, int32_t T, cudaStream_t st) {
+ms_status vmf_alloc(VmfWork* w, int64_t N, int32_t M, int32_t T, bool tc, cudaStream_t st) {
+    w->tc = tc;
     w->sp = vsplit(M, N, vmf_slots(k_vmf_fwd_partial, kFT), kFSeeds);
     w->spa = vsplit(M, N, vmf_slots(k_vmf_bwd_seeds, kAT), kASeeds);
     const size_t pf = (size_t)w->sp.tiles * w->sp.chunks * kFSeeds, pa = (size_t)w->spa.tiles * w->spa.chunks * kASeeds;
     const size_t pmax = pf > pa ? pf : pa;
+    size_t tc_bytes = 0;
+    if (tc) {
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        w->plan = vmf_tc_plan(M, N, sms);
+        tc_bytes = vmf_tc_pk_bytes(N) + (size_t)w->plan.items * 128 * kVD * sizeof(float) + 3 * 256;
+    }
     const size_t bytes = pmax * kVD * sizeof(float) + (size_t)(T + 1) * M * kVD * sizeof(float) +
-                         (size_t)(T > 0 ? T : 1) * M * sizeof(float) + 2 * (size_t)M * kVD * sizeof(float) + 4 * 256;
+                         (size_t)(T > 0 ? T : 1) * M * sizeof(float) + 2 * (size_t)M * kVD * sizeof(float) + 4 * 256 +
+                         tc_bytes;
     char* b = nullptr;
-    MS_CUDA(cudaMallocAsync((void**)&b, bytes, st));
+    MS_CUDA(scratch_malloc_async((void**)&b, bytes, st));
     auto take = [&](size_t n) {
         char* p = b;
         b += (n + 255) / 256 * 256;
@@ -337,6 +353,14 @@ ms_status vmf_alloc(VmfWork* w, int64_t N, int32_t M, int32_t T, cudaStream_t st
     w->ynorm = take((size_t)(T > 0 ? T : 1) * M * sizeof(float));
     w->gy = take((size_t)M * kVD * sizeof(float));
     w->g = take((size_t)M * kVD * sizeof(float));
+    w->Pk = nullptr;
+    w->tc_partial = nullptr;
+    w->status = nullptr;
+    if (tc) {
+        w->Pk = take(vmf_tc_pk_bytes(N));
+        w->tc_partial = take((size_t)w->plan.items * 128 * kVD * sizeof(float));
+        w->status = (int*)take(sizeof(int));
+    }
     return MS_OK;
 }
 
@@ -344,6 +368,21 @@ ms_status vmf_alloc(VmfWork* w, int64_t N, int32_t M, int32_t T, cudaStream_t st
 ms_status vmf_forward_steps(const float* P, int64_t N, const float* X0, int32_t M, float kappa, int32_t T,
                             VmfWork* w, cudaStream_t st) {
     MS_CUDA(cudaMemcpyAsync(w->iters, X0, sizeof(float) * (size_t)M * kVD, cudaMemcpyDeviceToDevice, st));
+    if (w->tc) {
+        MS_CUDA(cudaMemsetAsync(w->status, 0, sizeof(int), st));
+        if (ms_status s = vmf_tc_prepare(P, N, w->Pk, &w->pmap, st); s != MS_OK) return s;
+        for (int t = 0; t < T; ++t) {
+            ms_status s = vmf_tc_step(w->pmap, w->iters + (size_t)t * M * kVD, M, kappa, w->plan, w->tc_partial,
+                                      w->status, w->iters + (size_t)(t + 1) * M * kVD, w->ynorm + (size_t)t * M, st);
+            if (s != MS_OK) return s;
+        }
+        // the tensor-core steps end in a status check (a bounded wait may have given up)
+        int h_status = 0;
+        MS_CUDA(cudaMemcpyAsync(&h_status, w->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MS_CUDA(cudaStreamSynchronize(st));
+        if (h_status) return set_error(MS_ERR_TIMEOUT, "a bounded device wait in k_vmf_tc gave up");
+        return MS_OK;
+    }
     const unsigned items = (unsigned)(w->sp.tiles * w->sp.chunks);
     const unsigned rblocks = (unsigned)((M + 7) / 8);
     for (int t = 0; t < T; ++t) {
@@ -362,14 +401,15 @@ ms_status vmf_forward_steps(const float* P, int64_t N, const float* X0, int32_t 
 
 using namespace ms;
 
-extern "C" ms_status ms_vmf_forward(const float* d_P, int64_t N, const float* d_X0, int32_t M, int32_t dim,
-                                    double kappa, int32_t T, float* d_XT, void* stream) {
+extern "C" ms_status ms_vmf_forward_ex(const float* d_P, int64_t N, const float* d_X0, int32_t M, int32_t dim,
+                                       double kappa, int32_t T, int32_t precision, float* d_XT, void* stream) {
     ms_status s = vmf_validate(d_P, N, d_X0, M, dim, kappa, T);
     if (s != MS_OK) return s;
     if (!d_XT) return set_error(MS_ERR_INVALID_ARG, "d_XT is NULL");
+    if (precision != MS_FP32 && precision != MS_BF16) return set_error(MS_ERR_INVALID_ARG, "unknown precision");
     cudaStream_t st = (cudaStream_t)stream;
     VmfWork w;
-    s = vmf_alloc(&w, N, M, T, st);
+    s = vmf_alloc(&w, N, M, T, precision == MS_BF16, st);
     if (s != MS_OK) return s;
     char* base = (char*)w.partial;
     s = vmf_forward_steps(d_P, N, d_X0, M, (float)kappa, T, &w, st);
@@ -380,15 +420,16 @@ extern "C" ms_status ms_vmf_forward(const float* d_P, int64_t N, const float* d_
     return s;
 }
 
-extern "C" ms_status ms_vmf_backward(const float* d_P, int64_t N, const float* d_X0, int32_t M, int32_t dim,
-                                     double kappa, int32_t T, const float* d_GT, float* d_dP, float* d_dX0,
-                                     void* stream) {
+extern "C" ms_status ms_vmf_backward_ex(const float* d_P, int64_t N, const float* d_X0, int32_t M, int32_t dim,
+                                        double kappa, int32_t T, int32_t precision, const float* d_GT, float* d_dP,
+                                        float* d_dX0, void* stream) {
     ms_status s = vmf_validate(d_P, N, d_X0, M, dim, kappa, T);
     if (s != MS_OK) return s;
     if (!d_GT || !d_dP || !d_dX0) return set_error(MS_ERR_INVALID_ARG, "NULL output or upstream gradient");
+    if (precision != MS_FP32 && precision != MS_BF16) return set_error(MS_ERR_INVALID_ARG, "unknown precision");
     cudaStream_t st = (cudaStream_t)stream;
     VmfWork w;
-    s = vmf_alloc(&w, N, M, T, st);
+    s = vmf_alloc(&w, N, M, T, precision == MS_BF16, st);
     if (s != MS_OK) return s;
     char* base = (char*)w.partial;
     const float kf = (float)kappa;
@@ -417,4 +458,15 @@ extern "C" ms_status ms_vmf_backward(const float* d_P, int64_t N, const float* d
                        "copy dX0");
     cudaFreeAsync(base, st);
     return s;
+}
+
+extern "C" ms_status ms_vmf_forward(const float* d_P, int64_t N, const float* d_X0, int32_t M, int32_t dim,
+                                    double kappa, int32_t T, float* d_XT, void* stream) {
+    return ms_vmf_forward_ex(d_P, N, d_X0, M, dim, kappa, T, MS_FP32, d_XT, stream);
+}
+
+extern "C" ms_status ms_vmf_backward(const float* d_P, int64_t N, const float* d_X0, int32_t M, int32_t dim,
+                                     double kappa, int32_t T, const float* d_GT, float* d_dP, float* d_dX0,
+                                     void* stream) {
+    return ms_vmf_backward_ex(d_P, N, d_X0, M, dim, kappa, T, MS_FP32, d_GT, d_dP, d_dX0, stream);
 }

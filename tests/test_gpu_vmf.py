@@ -2,7 +2,8 @@
 the FP64 autograd reference (oracle/vmf_ref.py), plus the autograd.Function.
 
 Tolerances: x_T within 1e-5 (FP32 weights and sums); gradients within 1e-4
-relative L2 (FP32 recomputation of every weight in the reverse sweep)."""
+relative L2 (FP32 recomputation of every weight in the reverse sweep). The
+BF16 form (forward steps on the tensor cores) has its own bar, derived below."""
 import numpy as np
 import pytest
 import torch
@@ -95,3 +96,68 @@ def test_vmf_deterministic(ms_lib):
     a = ms_lib.ms_vmf_backward(P.cuda(), X0.cuda(), 20.0, 5, G)
     b = ms_lib.ms_vmf_backward(P.cuda(), X0.cuda(), 20.0, 5, G)
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+# ---------------------------------------------------------------- BF16 form
+# Forward steps on the tensor cores (ms_vmf_forward with MS_BF16). The
+# exponent kappa log2(e) x.p comes from six BF16 products of three-term
+# splits (terms below 2^-24 |x||p| left out) accumulated in FP32, so its error
+# is a few FP32 ulps of |kappa log2(e) x.p| <= 29 (about 2^-19 each); the
+# weight is split into two BF16 terms (relative error <= 2^-16), the low term
+# against two pixel terms. Per-weight relative errors of a few 1e-6 average
+# over the window; the bar below is 5e-6 on every component of x_T (measured:
+# at most 1.8e-6, against 1.2e-7 for the FP32 form). Gradients differentiate
+# the BF16 iterates with the FP32 adjoint; they keep the 1e-4 relative bar.
+BF16_TOL = 5e-6
+
+
+@pytest.mark.parametrize("N,M,T", [(4096, 64, 10), (3000, 37, 3), (1000, 300, 1), (129, 129, 2)])
+def test_vmf_bf16_forward_matches_fp64(ms_lib, N, M, T):
+    P, X0, _ = _problem(N, M)
+    XT = ms_lib.ms_vmf_forward(P.cuda(), X0.cuda(), 20.0, T, precision=ms_lib.MS_BF16)
+    ref = vmf_ref.vmf_forward(P.double(), X0.double(), 20.0, T)
+    assert (XT.cpu().double() - ref).abs().max().item() <= BF16_TOL
+    assert torch.allclose(XT.norm(dim=1).cpu().double(), torch.ones(M, dtype=torch.float64), atol=1e-6)
+
+
+def test_vmf_bf16_c5_full_config(ms_lib):
+    """N = 65536, M = 1024, T = 10: every seed's x_T against the FP64 reference,
+    and the loss gradient through the autograd.Function against the FP64
+    reference gradient for 128 of the seeds."""
+    from paper_2007_14283_gb300.autograd import vmf_mean_shift
+    P, X0, target = _problem(65536, 1024, seed=0, K=32)
+    XT = ms_lib.ms_vmf_forward(P.cuda(), X0.cuda(), 20.0, 10, precision=ms_lib.MS_BF16)
+    ref = vmf_ref.vmf_forward(P.double(), X0.double(), 20.0, 10)
+    assert (XT.cpu().double() - ref).abs().max().item() <= BF16_TOL
+    Pg = P.cuda().requires_grad_(True)
+    Xg = X0[:128].cuda().requires_grad_(True)
+    loss = ((vmf_mean_shift(Pg, Xg, 20.0, 10, precision=ms_lib.MS_BF16) - target[:128].cuda()) ** 2).sum()
+    loss.backward()
+    rloss, rP, rX = vmf_ref.vmf_loss_and_grads(P.double(), X0[:128].double(), target[:128].double(), 20.0, 10)
+    assert abs(loss.item() - rloss.item()) <= 1e-4 * abs(rloss.item())
+    assert rel(Pg.grad, rP) <= 1e-4 and rel(Xg.grad, rX) <= 1e-4
+
+
+def test_vmf_bf16_adjoint_matches_fp64_vjp(ms_lib):
+    P, X0, _ = _problem(4096, 64, seed=1)
+    G = torch.randn(64, 16, generator=torch.Generator().manual_seed(3))
+    dP, dX0 = ms_lib.ms_vmf_backward(P.cuda(), X0.cuda(), 20.0, 10, G.cuda(), precision=ms_lib.MS_BF16)
+    _, rP, rX = vmf_ref.vmf_vjp(P.double(), X0.double(), 20.0, 10, G.double())
+    assert rel(dP, rP) <= 1e-4, rel(dP, rP)
+    assert rel(dX0, rX) <= 1e-4, rel(dX0, rX)
+
+
+def test_vmf_bf16_deterministic_and_zero_steps(ms_lib):
+    P, X0, _ = _problem(4096, 200, seed=5)
+    a = ms_lib.ms_vmf_forward(P.cuda(), X0.cuda(), 20.0, 4, precision=ms_lib.MS_BF16)
+    b = ms_lib.ms_vmf_forward(P.cuda(), X0.cuda(), 20.0, 4, precision=ms_lib.MS_BF16)
+    assert torch.equal(a, b)
+    x0 = ms_lib.ms_vmf_forward(P.cuda(), X0.cuda(), 20.0, 0, precision=ms_lib.MS_BF16)
+    assert torch.equal(x0.cpu(), X0)
+
+
+def test_vmf_bf16_unknown_precision_rejected(ms_lib):
+    P, X0, _ = _problem(256, 8, seed=6)
+    with pytest.raises(ms_lib.MsError) as e:
+        ms_lib.ms_vmf_forward(P.cuda(), X0.cuda(), 20.0, 1, precision=7)
+    assert e.value.status == ms_lib.MS_ERR_INVALID_ARG

@@ -58,7 +58,8 @@ typedef int32_t ms_status;
 #define MS_VMF 1  /* smooth kernel exp(kappa * cos): only the ms_vmf_* calls */
 
 #define MS_FP32 0 /* plain FP32 SIMT similarity and sums */
-#define MS_BF16 1 /* BF16 tensor-core GEMMs with FP32 accumulation and an FP32 recheck band */
+#define MS_BF16 1 /* BF16 tensor-core GEMMs with FP32 accumulation and an FP32 recheck band (the
+                     shift for any dim; labelling on the tensor cores for dim <= 16, else FP32) */
 
 #define MS_MAX_DIM 32
 
@@ -376,7 +377,7 @@ MS_API void ms_video_destroy(ms_video* v);
  * conditional WHILE node whose body advances every frame by one iteration,
  * then labelling); it allocates the workspace (one cudaMalloc) and
  * synchronises `stream`. Arguments:
- *  cfg       as for ms_create (MS_FLAT; MS_BF16 needs dim <= 16).
+ *  cfg       as for ms_create (MS_FLAT).
  *  B         1..4096 frames.
  *  d_embs    host array of B device pointers, frame f float32 [n_pixels[f], dim]. Borrowed.
  *  d_masks   host array of B device pointers (uint8 [n_pixels[f]], NULL entry = all

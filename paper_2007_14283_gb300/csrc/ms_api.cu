@@ -161,8 +161,6 @@ ms_status validate(const ms_config* c) {
     if (!(c->H >= 0.0)) return set_error(MS_ERR_INVALID_ARG, "H must be >= 0");
     if (c->L <= 0.0 && !(c->alpha > 0.0)) return set_error(MS_ERR_INVALID_ARG, "L <= 0 needs alpha > 0");
     if (c->precision != MS_FP32 && c->precision != MS_BF16) return set_error(MS_ERR_INVALID_ARG, "unknown precision");
-    if (c->precision == MS_BF16 && c->dim > 16)
-        return set_error(MS_ERR_INVALID_ARG, "the BF16 tensor-core form supports dim <= 16");
     if (c->max_rounds < 1) return set_error(MS_ERR_INVALID_ARG, "max_rounds must be >= 1");
     if (c->batch_max_passes < 0) return set_error(MS_ERR_INVALID_ARG, "batch_max_passes must be >= 0");
     if (c->tc_shape < 0 || c->tc_shape >= kTcShapes) return set_error(MS_ERR_INVALID_ARG, "unknown tc_shape");
@@ -205,9 +203,9 @@ Layout plan(int64_t np, int Dp, int target_items, bool bf16) {
         n * kMergeCap * sizeof(int32_t),  // 19 conf
         ((n + 1023) / 1024 + 1) * sizeof(int32_t),  // 20 block_tmp
         sizeof(DevCounters),              // 21 dc
-        bf16 ? (n + 127) / 128 * 128 * 128 : 0,  // 22 Pk
-        bf16 ? (n + 127) / 128 * 128 * 128 : 0,  // 23 Mk
-        bf16 ? n * sizeof(int2) + 16 : 0,         // 24 label_fix + count
+        bf16 ? (n + 127) / 128 * 128 * 128 * (Dp / 16) : 0,  // 22 Pk (one array per 16 dimensions)
+        bf16 && Dp == 16 ? (n + 127) / 128 * 128 * 128 : 0,  // 23 Mk (labelling on the tensor cores: d <= 16)
+        bf16 && Dp == 16 ? n * sizeof(int2) + 16 : 0,         // 24 label_fix + count
     };
     size_t t = 0;
     for (int i = 0; i < 25; ++i) {
@@ -339,8 +337,8 @@ ms_status ctx_alloc(const ms_config* cfg, int64_t max_pixels, cudaStream_t strea
     ctx->block_tmp = (int32_t*)(b + L.off[20]);
     ctx->dc = (DevCounters*)(b + L.off[21]);
     ctx->Pk = cfg->precision == MS_BF16 ? (void*)(b + L.off[22]) : nullptr;
-    ctx->Mk = cfg->precision == MS_BF16 ? (void*)(b + L.off[23]) : nullptr;
-    ctx->label_fix = cfg->precision == MS_BF16 ? (int2*)(b + L.off[24]) : nullptr;
+    ctx->Mk = cfg->precision == MS_BF16 && ctx->Dp == 16 ? (void*)(b + L.off[23]) : nullptr;
+    ctx->label_fix = cfg->precision == MS_BF16 && ctx->Dp == 16 ? (int2*)(b + L.off[24]) : nullptr;
     ctx->round_log_cap = 64;
     ctx->round_log = new (std::nothrow) int64_t[ctx->round_log_cap * 4];
     if (!ctx->round_log) {

@@ -63,6 +63,7 @@ struct ms_batch {
     void* Mk;                 // kept modes as BF16 split rows at the frames' Pk offsets (labelling)
     int32_t** label_ptrs;     // device array of B label buffers
     CUtensorMap pmap;
+    CUtensorMap pmap1;        // d = 32: dimensions 16..31 (the second Pk array)
     CUtensorMap mmap;
     ms::LabelTcScratch lsc;
     cudaGraph_t graph;
@@ -261,11 +262,16 @@ __global__ void k_b_compact(const BFrame* __restrict__ frames, int nblk_max, con
     pix[pos] = (int32_t)i;
 }
 
-__global__ void k_b_pack(const BFrame* __restrict__ frames, const float* __restrict__ P32, uint4* __restrict__ Pk) {
+// BF16 split rows of every frame's pixels at the frame's Pk rows; for d = 32
+// a second array (after total_rows rows) holds dimensions 16..31.
+__global__ void k_b_pack(const BFrame* __restrict__ frames, const float* __restrict__ P32, int Dp, int64_t total_rows,
+                         uint4* __restrict__ Pk) {
     const BFrame& fr = frames[blockIdx.y];
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= fr.n_ptiles * 128) return;
-    tc::pack_split_row(r < fr.n ? P32 + (fr.pix0 + r) * 16 : nullptr, Pk + (int64_t)(fr.pk_row0 + r) * 8);
+    const float* p = r < fr.n ? P32 + (fr.pix0 + r) * Dp : nullptr;
+    tc::pack_split_row(p, Pk + (int64_t)(fr.pk_row0 + r) * 8);
+    if (Dp == 32) tc::pack_split_row(p ? p + 16 : nullptr, Pk + (total_rows + fr.pk_row0 + r) * 8, false);
 }
 
 __global__ void k_b_labels_clear(const BFrame* __restrict__ frames, int32_t* const* __restrict__ labels) {
@@ -1070,7 +1076,8 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     }
     ms_status st;
     if (b->tc)
-        st = launch_shift_tc_batch(b->pmap, b->P32, b->X, b->acc, cf, b->frames, b->states, b->plan, b->act[0],
+        st = launch_shift_tc_batch(b->pmap, b->pmap1, Dp, b->P32, b->X, b->acc, cf, b->frames, b->states, b->plan,
+                                   b->act[0],
                                    b->act[1], B, b->misc + 1, (unsigned long long*)(b->misc + 2), b->tc_grid,
                                    b->tc_shape, s);
     else
@@ -1155,7 +1162,7 @@ ms_status enqueue_setup(ms_batch* b, cudaStream_t s) {
     MS_LAUNCH("k_b_compact");
     if (b->tc) {
         const dim3 gp((unsigned)((b->max_pk_rows + 255) / 256), (unsigned)B);
-        k_b_pack<<<gp, 256, 0, s>>>(b->frames, b->P32, (uint4*)b->Pk);
+        k_b_pack<<<gp, 256, 0, s>>>(b->frames, b->P32, Dp, (int64_t)b->total_pk_rows, (uint4*)b->Pk);
         MS_LAUNCH("k_b_pack");
     }
     const dim3 gl((unsigned)((b->max_np + 255) / 256 < 1024 ? (b->max_np + 255) / 256 : 1024), (unsigned)B);
@@ -1166,7 +1173,7 @@ ms_status enqueue_setup(ms_batch* b, cudaStream_t s) {
 
 template <int Dp>
 ms_status enqueue_label(ms_batch* b, cudaStream_t s) {
-    if (b->tc)  // BF16 form (d <= 16): the tensor-core kernel, same labels (exact FP64 argmax)
+    if (b->Mk)  // BF16 form, d <= 16: the tensor-core kernel, same labels (exact FP64 argmax)
         return launch_label_tc_batch(b->pmap, b->mmap, b->Mk, b->frames, b->states, b->B, (int)b->max_pk_rows,
                                      b->modes, b->P32, b->pix, b->d, b->label_ptrs, b->lsc, b->num_sms, b->misc + 1,
                                      s);
@@ -1221,7 +1228,7 @@ ms_status build_graph(ms_batch* b) {
     if (st2 != MS_OK) return st2;
     MS_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
     b->body_launches = nl;
-    b->fixed_launches = b->tc ? 5 + 4 : 4 + 2;  // set-up, then labelling
+    b->fixed_launches = (b->tc ? 5 : 4) + (b->Mk ? 4 : 2);  // set-up, then labelling
     return MS_OK;
 }
 
@@ -1271,7 +1278,7 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
     if (cfg->dim < 1 || cfg->dim > MS_MAX_DIM || cfg->kernel != MS_FLAT || !(cfg->tol > 0.0) || cfg->max_iter < 1 ||
         cfg->n_initial < 1 || !(cfg->gamma >= 0.0 && cfg->gamma <= 1.0) ||
         !(cfg->P_target > 0.0 && cfg->P_target < 1.0) || cfg->max_rounds < 1 ||
-        (cfg->precision != MS_FP32 && cfg->precision != MS_BF16) || (cfg->precision == MS_BF16 && cfg->dim > 16) ||
+        (cfg->precision != MS_FP32 && cfg->precision != MS_BF16) ||
         (cfg->batch_split != 0 && cfg->batch_split != 1) || cfg->tc_shape < 0 || cfg->tc_shape >= ms::kTcShapes)
         return set_error(MS_ERR_INVALID_ARG, "invalid config");
     ms_batch* b = new (std::nothrow) ms_batch();
@@ -1320,13 +1327,14 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
     b->max_pk_rows = (b->max_np + 127) / 128 * 128;
     b->nblk_max = (b->max_np + kIT - 1) / kIT;
     const int Dp = b->Dp;
+    const bool tcl = b->tc && Dp == 16;  // labelling on the tensor cores (d <= 16)
     const size_t n = (size_t)b->total_px;
     const size_t sizes[] = {
         sizeof(BFrame) * B, sizeof(BState) * B, sizeof(int32_t) * ((B + 1) * 4 + (B + 2) * 2), 64,
         n * Dp * 4, n * 4, n, n * Dp * 4, n * 4, n * 4, n, n * 4, n * 4, n * 4,
         n * (Dp + 1) * 8, n * Dp * 4, n * 4, n * 4, n * 4, n, n * 4, n * kMergeCap * 4,
-        (size_t)B * b->nblk_max * 4 + 4, b->tc ? (size_t)b->total_pk_rows * 128 : 0, sizeof(int32_t*) * B,
-        b->tc ? (size_t)b->total_pk_rows * 128 : 0, b->tc ? n * sizeof(int2) : 0, sizeof(int32_t) * (B + 1) + 16};
+        (size_t)B * b->nblk_max * 4 + 4, b->tc ? (size_t)b->total_pk_rows * 128 * (Dp / 16) : 0, sizeof(int32_t*) * B,
+        tcl ? (size_t)b->total_pk_rows * 128 : 0, tcl ? n * sizeof(int2) : 0, sizeof(int32_t) * (B + 1) + 16};
     const int NS = (int)(sizeof(sizes) / sizeof(sizes[0]));
     size_t offs[32], tot = 0;
     for (int i = 0; i < NS; ++i) {
@@ -1371,8 +1379,8 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
     b->block_tmp = (int32_t*)(w + offs[22]);
     b->Pk = b->tc ? (void*)(w + offs[23]) : nullptr;
     b->label_ptrs = (int32_t**)(w + offs[24]);
-    b->Mk = b->tc ? (void*)(w + offs[25]) : nullptr;
-    b->lsc.fix = b->tc ? (int2*)(w + offs[26]) : nullptr;
+    b->Mk = tcl ? (void*)(w + offs[25]) : nullptr;
+    b->lsc.fix = tcl ? (int2*)(w + offs[26]) : nullptr;
     b->lsc.off = (int32_t*)(w + offs[27]);
     b->lsc.fix_count = b->lsc.off + (B + 1);
     ms_status s = cuda_check(cudaMallocHost((void**)&b->h_states, sizeof(BState) * B), "cudaMallocHost");
@@ -1385,10 +1393,13 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
                                        b->stream),
                        "copy label pointers");
     if (s == MS_OK) s = cuda_check(cudaStreamSynchronize(b->stream), "sync");
-    if (s == MS_OK && b->tc) s = tc_batch_setup();
+    if (s == MS_OK && b->tc) s = tc_batch_setup(Dp);
     if (s == MS_OK && b->tc) s = encode_pk_map(b->Pk, (int)b->total_pk_rows, &b->pmap);
-    if (s == MS_OK && b->tc) s = encode_pk_map(b->Mk, (int)b->total_pk_rows, &b->mmap);
-    if (s == MS_OK && b->tc) s = label_tc_setup();
+    if (s == MS_OK && b->tc)
+        s = encode_pk_map(Dp == 32 ? (uint8_t*)b->Pk + (size_t)b->total_pk_rows * 128 : b->Pk, (int)b->total_pk_rows,
+                          &b->pmap1);
+    if (s == MS_OK && tcl) s = encode_pk_map(b->Mk, (int)b->total_pk_rows, &b->mmap);
+    if (s == MS_OK && tcl) s = label_tc_setup();
     if (s == MS_OK) s = rebuild_graph(b);
     if (s != MS_OK) {
         free_batch(b);

@@ -49,11 +49,11 @@ struct BPlan {
 };
 
 // Tensor-core shift over all iterating frames (ms_shift_tc.cu).
-ms_status tc_batch_setup();
-ms_status launch_shift_tc_batch(const CUtensorMap& pmap, const float* P32, const float* X, unsigned long long* acc,
-                                float c_f, const BFrame* frames, const BState* states, BPlan plan,
-                                const int32_t* act0, const int32_t* act1, int nf, int* status,
-                                unsigned long long* band, int grid, int shape, cudaStream_t st);
+ms_status tc_batch_setup(int D);
+ms_status launch_shift_tc_batch(const CUtensorMap& pmap, const CUtensorMap& pmap1, int D, const float* P32,
+                                const float* X, unsigned long long* acc, float c_f, const BFrame* frames,
+                                const BState* states, BPlan plan, const int32_t* act0, const int32_t* act1, int nf,
+                                int* status, unsigned long long* band, int grid, int shape, cudaStream_t st);
 // FP32 shift over all iterating frames (ms_shift_fp32.cu).
 ms_status launch_shift_fp32_batch(const float* P32, const float* X, unsigned long long* acc, float c_f, int Dp,
                                   const BFrame* frames, const BState* states, BPlan plan, const int32_t* act0,

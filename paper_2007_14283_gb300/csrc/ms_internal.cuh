@@ -138,6 +138,7 @@ struct ms_ctx {
     void* Pk;            // [n_pad, 64] bf16: [Ph | Pm | Pl | 0] per pixel
     int64_t n_pad;       // n rounded up to 128 (0 when n = 0)
     CUtensorMap pmap;    // TMA map of Pk: boxes of 128 rows x 128 bytes, 128-byte swizzle
+    CUtensorMap pmap1;   // d = 32: the same for dimensions 16..31 (the second Pk array)
     int tc_grid;         // persistent grid of the tensor-core shift kernel
     void* Mk;            // [n_pad, 64] bf16 split rows of the kept modes (labelling)
     int2* label_fix;     // [n] near-tie queue of the tensor-core labelling, then its count
@@ -194,7 +195,7 @@ ms_status ctx_bind_finish(ms_ctx* ctx, cudaStream_t st, uint64_t frame_id, int64
 void ctx_free(ms_ctx* ctx);
 int64_t carried_n(const ms_ctx* ctx);   // the N a video carries into its next frame
 ms_status launch_shift_tc(ms_ctx* ctx, const int32_t* active, int grid, int target_items, float* dbg_S);
-int tc_smem_bytes();
+int tc_smem_bytes(int D);
 constexpr int kTcShapes = 8;  // values of ms_config.tc_shape (warp arrangements of k_shift_tc)
 ms_status encode_pk_map(void* Pk, int rows, CUtensorMap* map);  // ms_shift_tc.cu: TMA map of split rows
 

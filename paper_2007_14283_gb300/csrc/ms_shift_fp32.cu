@@ -221,7 +221,7 @@ ms_status shift_iteration_t(ms_ctx* ctx, int t, int max_iter, cudaEvent_t e0, cu
     const double gamma = ctx->cfg.all_seeds ? 1.0 : ctx->cfg.gamma;
     const unsigned fin_blocks = (unsigned)((ctx->m_round + 255) / 256);
     if (e0) MS_CUDA(cudaEventRecord(e0, ctx->stream));
-    if (Dp == 16 && ctx->cfg.precision == MS_BF16) {
+    if (ctx->cfg.precision == MS_BF16) {
         ms_status s = launch_shift_tc(ctx, a_in, ctx->tc_grid, 2 * ctx->tc_grid, nullptr);
         if (s != MS_OK) return s;
     } else {

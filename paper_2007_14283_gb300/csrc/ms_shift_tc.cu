@@ -53,7 +53,8 @@ using namespace tc;
 // 128-pixel stages; GEMM1 scores BN of them at a time (a unit: BN = 128, one
 // unit per stage, two 128-column S buffers; BN = 64, two units per stage,
 // four 64-column S buffers), and the mask of a unit takes BN / 2 TMEM columns
-// (three or six mask buffers in the same 192 columns). MW mask warps form G
+// (three or six mask buffers in 192 columns for d = 16, two or four in 128
+// for d = 32). MW mask warps form G
 // groups that take turns unit by unit (group k builds the masks of units u
 // with u % G == k); each warp builds the mask of 4 * BN / (MW / G) pixels of
 // its group's units. Then come the TMA producer, the GEMM1 issuer and NG2
@@ -66,7 +67,6 @@ struct TcShape {
     static constexpr int kBN = BN;                  // pixels per unit
     static constexpr int kUPS = 128 / BN;           // units per 128-pixel stage
     static constexpr int kSBufs = 256 / BN;         // S buffers of BN columns
-    static constexpr int kMBufs = 384 / BN;         // mask buffers of BN / 2 columns
     static constexpr int kPxPerWarp = 4 * BN / kGroupWarps;  // pixels of a unit per mask warp
     static constexpr int kSub = kPxPerWarp / 32;    // 32-pixel TMEM loads per mask warp and unit
     static constexpr int kWarpTma = MW;
@@ -88,23 +88,32 @@ using TcShape4 = TcShape<16, 2, 2, 128>;
 using TcShape5 = TcShape<16, 1, 2, 128>;
 using TcShape6 = TcShape<16, 2, 2, 64>;
 using TcShape7 = TcShape<16, 1, 2, 64>;
-constexpr int kStages = 10;            // pixel-tile ring
 constexpr int kTileBytes = 128 * 128;  // 128 rows x 128 bytes
 constexpr uint32_t kTmemCols = 512;
 constexpr int kMaxSBufs = 4, kMaxMBufs = 6;
 constexpr uint32_t kColS = 0;          // S accumulators, 256 columns
-constexpr uint32_t kColY = 256;        // one Y accumulator, 64 columns
-constexpr uint32_t kColM = 320;        // mask buffers (GEMM2's A), 192 columns
+constexpr uint32_t kColY = 256;        // Y accumulators: 64 columns per 16-dimensional half
 constexpr float kBand = 6.103515625e-05f;    // 2^-14
 constexpr float kFixScale = 68719476736.0f;  // 2^36
 
-constexpr int kOffA1 = 0;                              // 2 x 16 KB
-constexpr int kOffP = 2 * kTileBytes;                  // kStages x 16 KB
-constexpr int kOffX = kOffP + kStages * kTileBytes;   // 2 x 8 KB: the item's seeds in FP32, 128 x 16
-constexpr int kOffBar = kOffX + 2 * 128 * 16 * 4;
-constexpr int kNumBars = 2 * kStages + 2 * kMaxSBufs + 2 * kMaxMBufs + 2 + 2 + 3;  // aux: GEMM1 + up to two GEMM2 issuers
-constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 32 + 1024;  // + TMEM slot, flags, alignment slack
-static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
+// Layout for embedding dimension D: 16, or 32 as two 16-dimensional halves,
+// each with its own seed-operand tile, pixel tile (a second Pk array) and Y
+// block; the mask buffers take the TMEM columns after Y.
+template <int D>
+struct TcDim {
+    static_assert(D == 16 || D == 32, "embedding dimension 16 or 32");
+    static constexpr int kHalves = D / 16;
+    static constexpr int kStages = D == 16 ? 10 : 4;              // pixel-tile ring
+    static constexpr int kStageBytes = kHalves * kTileBytes;
+    static constexpr int kOffA1 = 0;                              // 2 items x kHalves x 16 KB
+    static constexpr int kOffP = 2 * kHalves * kTileBytes;        // kStages stages
+    static constexpr int kOffX = kOffP + kStages * kStageBytes;   // 2 x 128 x D floats: the item's seeds
+    static constexpr int kOffBar = kOffX + 2 * 128 * D * 4;
+    static constexpr int kNumBars = 2 * kStages + 2 * kMaxSBufs + 2 * kMaxMBufs + 2 + 2 + 3;  // aux: GEMM1 + two GEMM2
+    static constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 32 + 1024;  // + TMEM slot, flags, alignment slack
+    static constexpr uint32_t kColM = kColY + 64 * kHalves;       // mask buffers up to column 512
+    static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
+};
 
 struct TcSplit {
     int tiles, chunks, tpc;  // seed tiles, pixel chunks, pixel tiles per chunk
@@ -137,17 +146,10 @@ __device__ __forceinline__ uint32_t sign_halves(uint32_t a, uint32_t b) {
     return r;
 }
 
-__device__ __forceinline__ void load_x16(const float* __restrict__ X, int slot, float (&x)[16]) {
-#pragma unroll
-    for (int k = 0; k < 16; k += 4) {
-        const float4 v = slot >= 0 ? *reinterpret_cast<const float4*>(X + (int64_t)slot * 16 + k)
-                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-        x[k] = v.x; x[k + 1] = v.y; x[k + 2] = v.z; x[k + 3] = v.w;
-    }
-}
-
-// Row r of a seed operand tile: [Xh | Xl | -c split | 0], 128-byte swizzle.
-__device__ __forceinline__ void write_a1(uint8_t* A1, int r, const float (&x)[16], float c_f) {
+// Row r of one 16-dimensional half of a seed operand tile:
+// [Xh | Xl | -c split | 0] for the first half, [Xh | Xl | 0 | 0] for the
+// second (the -c column is added once), 128-byte swizzle.
+__device__ __forceinline__ void write_a1_half(uint8_t* A1, int r, const float* x, float c_f, bool with_c) {
     uint32_t wh[8], wl[8];
 #pragma unroll
     for (int k = 0; k < 16; k += 2) {
@@ -158,7 +160,7 @@ __device__ __forceinline__ void write_a1(uint8_t* A1, int r, const float (&x)[16
     const float c_hi = bf16_round(c_f);
     const float c_mid = bf16_round(c_f - c_hi);
     const float c_lo = (c_f - c_hi) - c_mid;
-    const uint32_t wc0 = pack_bf16(-c_hi, -c_mid), wc1 = pack_bf16(-c_lo, 0.f);
+    const uint32_t wc0 = with_c ? pack_bf16(-c_hi, -c_mid) : 0u, wc1 = with_c ? pack_bf16(-c_lo, 0.f) : 0u;
     *reinterpret_cast<uint4*>(A1 + sw128_offset(r, 0)) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
     *reinterpret_cast<uint4*>(A1 + sw128_offset(r, 1)) = make_uint4(wh[4], wh[5], wh[6], wh[7]);
     *reinterpret_cast<uint4*>(A1 + sw128_offset(r, 2)) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
@@ -169,11 +171,24 @@ __device__ __forceinline__ void write_a1(uint8_t* A1, int r, const float (&x)[16
         *reinterpret_cast<uint4*>(A1 + sw128_offset(r, cidx)) = make_uint4(0u, 0u, 0u, 0u);
 }
 
-// Row r of the item's FP32 seed tile in shared memory.
-__device__ __forceinline__ void write_xs(float* Xs, int r, const float (&x)[16]) {
+// Row r of an item's seed operand (one 16 KB tile per 16-dimensional half)
+// and of its FP32 seed tile in shared memory, for seed slot `slot` of X
+// (D components; a padding row, slot < 0: zeros), one half at a time.
+template <int D>
+__device__ __forceinline__ void write_seed_rows(uint8_t* A1, float* Xs, int r, const float* __restrict__ X, int slot,
+                                                float c_f) {
 #pragma unroll
-    for (int k = 0; k < 16; k += 4)
-        *reinterpret_cast<float4*>(Xs + r * 16 + k) = make_float4(x[k], x[k + 1], x[k + 2], x[k + 3]);
+    for (int hf = 0; hf < D / 16; ++hf) {
+        float x[16];
+#pragma unroll
+        for (int k = 0; k < 16; k += 4) {
+            const float4 v = slot >= 0 ? *reinterpret_cast<const float4*>(X + (int64_t)slot * D + 16 * hf + k)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[k] = v.x; x[k + 1] = v.y; x[k + 2] = v.z; x[k + 3] = v.w;
+            *reinterpret_cast<float4*>(Xs + r * D + 16 * hf + k) = v;
+        }
+        write_a1_half(A1 + hf * kTileBytes, r, x, c_f, hf == 0);
+    }
 }
 
 // What a work item covers, in the frame it belongs to.
@@ -217,10 +232,10 @@ struct TcSingleMap {
     }
 };
 
-// FP32 value of pixel row `row` of a pixel stage, rebuilt exactly from its
-// three BF16 parts (h + m) + l: the split of an FP32 value into three
-// round-to-nearest BF16 terms is exact, and so is this sum.
-__device__ __forceinline__ void stage_pixel(const uint8_t* stage, int row, float (&p)[16]) {
+// FP32 value of pixel row `row` of a 16-dimensional pixel stage, rebuilt
+// exactly from its three BF16 parts (h + m) + l: the split of an FP32 value
+// into three round-to-nearest BF16 terms is exact, and so is this sum.
+__device__ __forceinline__ void stage_pixel16(const uint8_t* stage, int row, float (&p)[16]) {
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         const uint4 hv = *reinterpret_cast<const uint4*>(stage + sw128_offset(row, c));
@@ -239,18 +254,57 @@ __device__ __forceinline__ void stage_pixel(const uint8_t* stage, int row, float
     }
 }
 
+// Dot product, in FP32 with one FMA per component in component order (the
+// FP32 form's dot_seq, bit for bit), of seed x (D floats in shared memory)
+// with pixel row `row` of a pixel stage (D / 16 tiles of 16 dimensions). The
+// pixel is rebuilt exactly from its three BF16 parts (h + m) + l: the split of
+// an FP32 value into three round-to-nearest BF16 terms is exact, and so is
+// this sum.
+template <int D>
+__device__ __forceinline__ float stage_dot(const uint8_t* stage, int row, const float* x) {
+    float acc = 0.f;
+#pragma unroll
+    for (int hf = 0; hf < D / 16; ++hf) {
+        const uint8_t* t = stage + hf * kTileBytes;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const uint4 hv = *reinterpret_cast<const uint4*>(t + sw128_offset(row, c));
+            const uint4 mv = *reinterpret_cast<const uint4*>(t + sw128_offset(row, c + 2));
+            const uint4 lv = *reinterpret_cast<const uint4*>(t + sw128_offset(row, c + 4));
+            const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, mw[4] = {mv.x, mv.y, mv.z, mv.w},
+                           lw[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float p0 = __fadd_rn(__fadd_rn(__uint_as_float(hw[k] << 16), __uint_as_float(mw[k] << 16)),
+                                           __uint_as_float(lw[k] << 16));
+                const float p1 =
+                    __fadd_rn(__fadd_rn(__uint_as_float(hw[k] & 0xFFFF0000u), __uint_as_float(mw[k] & 0xFFFF0000u)),
+                              __uint_as_float(lw[k] & 0xFFFF0000u));
+                acc = fmaf(x[16 * hf + c * 8 + 2 * k], p0, acc);
+                acc = fmaf(x[16 * hf + c * 8 + 2 * k + 1], p1, acc);
+            }
+        }
+    }
+    return acc;
+}
+
 // Warp-uniform bounded wait: every lane polls, all lanes get the same answer.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
     return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort));
 }
 
-template <class Shape, bool kDebug, class Map>
+template <class Shape, int kD, bool kDebug, class Map>
 __global__ void __launch_bounds__(Shape::kThreads, 1)
-k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P32, const float* __restrict__ X,
-           unsigned long long* __restrict__ acc, float c_f, Map map, int* status,
-           unsigned long long* band_ctr, float* __restrict__ dbg_S, int64_t dbg_stride) {
+k_shift_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap pmap1,
+           const float* __restrict__ P32, const float* __restrict__ X, unsigned long long* __restrict__ acc, float c_f,
+           Map map, int* status, unsigned long long* band_ctr, float* __restrict__ dbg_S, int64_t dbg_stride) {
+    using L = TcDim<kD>;
+    constexpr int kHalves = L::kHalves, kStages = L::kStages, kStageBytes = L::kStageBytes;
+    constexpr uint32_t kColM = L::kColM;
     constexpr int kGroups = Shape::kGroups, kGroupWarps = Shape::kGroupWarps;
-    constexpr int kBN = Shape::kBN, kUPS = Shape::kUPS, kSBufs = Shape::kSBufs, kMBufs = Shape::kMBufs;
+    constexpr int kBN = Shape::kBN, kUPS = Shape::kUPS, kSBufs = Shape::kSBufs;
+    constexpr int kMBufs = (int)(kTmemCols - kColM) / (kBN / 2);  // mask buffers of BN / 2 columns
+    static_assert(kMBufs >= 2 && kMBufs <= kMaxMBufs, "mask buffers");
     constexpr int kPxPerWarp = Shape::kPxPerWarp, kSub = Shape::kSub;
     constexpr int kWarpTma = Shape::kWarpTma, kWarpG1 = Shape::kWarpG1, kWarpG2 = Shape::kWarpG2, kG2 = Shape::kG2;
     // GEMM2 issuers commit a stage's release after their last unit of it.
@@ -258,10 +312,10 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
     if (!map.init()) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* A1 = smem + kOffA1;
-    uint8_t* Pst = smem + kOffP;
-    float* Xs = (float*)(smem + kOffX);           // [2][128][16] seeds of an item (FP32 re-decisions)
-    uint64_t* bars = (uint64_t*)(smem + kOffBar);
+    uint8_t* A1 = smem + L::kOffA1;               // [item buffer][half] 16 KB tiles
+    uint8_t* Pst = smem + L::kOffP;
+    float* Xs = (float*)(smem + L::kOffX);        // [2][128][kD] seeds of an item (FP32 re-decisions)
+    uint64_t* bars = (uint64_t*)(smem + L::kOffBar);
     uint64_t* full = bars;                        // [kStages] pixel tile landed
     uint64_t* empty = full + kStages;             // [kStages] pixel tile consumed by GEMM2
     uint64_t* s_full = empty + kStages;           // [kSBufs] GEMM1 of a unit done
@@ -272,7 +326,7 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
     uint64_t* d_full = a1_full + 2;               // Y of an item complete
     uint64_t* d_empty = d_full + 1;               // Y read by the epilogue
     uint64_t* aux = d_empty + 1;                  // [1 + kG2] drain barriers of the MMA issuers
-    uint32_t* tmem_slot = (uint32_t*)(bars + kNumBars);
+    uint32_t* tmem_slot = (uint32_t*)(bars + L::kNumBars);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
     volatile int* g2_next = (volatile int*)(tmem_slot + 2);  // the next unit whose GEMM2 may be issued
 
@@ -298,7 +352,10 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
         *g2_next = 0;
         fence_mbar_init();
     }
-    if (warp == kWarpTma && lane == 0) tma_prefetch_desc(&pmap);
+    if (warp == kWarpTma && lane == 0) {
+        tma_prefetch_desc(&pmap);
+        if (kHalves > 1) tma_prefetch_desc(&pmap1);
+    }
     if (warp == kWarpG1) {
         tmem_alloc(tmem_slot, kTmemCols);
         tmem_relinquish();
@@ -321,8 +378,10 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                 const int s = g % kStages;
                 if (g >= kStages && !(ok = warp_wait(&empty[s], ((g / kStages) - 1) & 1, abort))) break;
                 if (lane == 0) {
-                    mbar_arrive_expect_tx(&full[s], kTileBytes);
-                    tma_load_2d(Pst + s * kTileBytes, &pmap, 0, ii.pk_row0 + pt * 128, &full[s]);
+                    mbar_arrive_expect_tx(&full[s], kStageBytes);
+                    tma_load_2d(Pst + s * kStageBytes, &pmap, 0, ii.pk_row0 + pt * 128, &full[s]);
+                    if (kHalves > 1)
+                        tma_load_2d(Pst + s * kStageBytes + kTileBytes, &pmap1, 0, ii.pk_row0 + pt * 128, &full[s]);
                 }
                 __syncwarp();
             }
@@ -345,7 +404,7 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
         for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
             const TcItem ii = map.item(item);
             if (!(ok = warp_wait(&a1_full[it & 1], (it >> 1) & 1, abort))) break;
-            const uint64_t a = dA1 + (uint64_t)(it & 1) * kT;
+            const uint64_t a = dA1 + (uint64_t)(it & 1) * kHalves * kT;
             for (int pt = ii.pt0; pt < ii.pt1 && ok; ++pt, ++g) {
                 const int s = g % kStages;
                 if (!(ok = warp_wait(&full[s], (g / kStages) & 1, abort))) break;
@@ -355,11 +414,16 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                     if (u >= kSBufs && !(ok = warp_wait(&s_empty[b], ((u / kSBufs) - 1) & 1, abort))) break;
                     tc_fence_after();
                     const uint32_t tS = tmem + kColS + b * kBN;
-                    const uint64_t pb = dP1 + (uint64_t)s * kT + hh * kU;
+                    const uint64_t pb = dP1 + (uint64_t)s * kHalves * kT + hh * kU;
                     mma_bf16_warp(tS, a, pb, id1, 0);            // Xh . Ph
                     mma_bf16_warp(tS, a, pb + 2, id1, 1);        // Xh . Pm
                     mma_bf16_warp(tS, a + 2, pb, id1, 1);        // Xl . Ph
                     mma_bf16_warp(tS, a + 4, pb + 6, id1, 1);    // -c split . ones
+                    if (kHalves > 1) {                           // dimensions 16..31
+                        mma_bf16_warp(tS, a + kT, pb + kT, id1, 1);
+                        mma_bf16_warp(tS, a + kT, pb + kT + 2, id1, 1);
+                        mma_bf16_warp(tS, a + kT + 2, pb + kT, id1, 1);
+                    }
                     mma_commit_warp(&s_full[b]);
                 }
             }
@@ -411,12 +475,15 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                         if (!(ok = __all_sync(0xffffffffu, turn))) break;
                     }
                     tc_fence_after();
-                    const uint32_t tY = tmem + kColY;
                     const uint32_t tM = tmem + kColM + mb * (kBN / 2);
-                    const uint64_t pb = dP2 + (uint64_t)s * kT + hh * kK2 * 128;
 #pragma unroll
-                    for (int k = 0; k < kK2; ++k)
-                        mma_bf16_ts_warp(tY, tM + 8 * k, pb + k * 128, id2, (first && k == 0) ? 0u : 1u);
+                    for (int hf = 0; hf < kHalves; ++hf) {
+                        const uint32_t tY = tmem + kColY + 64 * hf;
+                        const uint64_t pb = dP2 + (uint64_t)(s * kHalves + hf) * kT + hh * kK2 * 128;
+#pragma unroll
+                        for (int k = 0; k < kK2; ++k)
+                            mma_bf16_ts_warp(tY, tM + 8 * k, pb + k * 128, id2, (first && k == 0) ? 0u : 1u);
+                    }
                     mma_commit_warp(&m_empty[mb]);
                     if (hh >= kUPS - kG2) mma_commit_warp(&empty[s]);
                     if constexpr (kG2 > 1) {  // one thread's MMAs execute in issue order: no hand-over
@@ -466,10 +533,7 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                 // completed before this warp observed s_full of that item's
                 // last tile (a commit covers every earlier MMA of its thread).
                 if (it == 0) {
-                    float x[16];
-                    load_x16(X, slot, x);
-                    write_a1(A1, r, x, c_f);
-                    write_xs(Xs, r, x);
+                    write_seed_rows<kD>(A1, Xs, r, X, slot, c_f);
                     fence_proxy_async();
                     mbar_arrive(&a1_full[0]);
                 }
@@ -477,10 +541,8 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                 if (nitem < items) {
                     const TcItem ni = map.item(nitem);
                     const int npos = ni.seed0 + r;
-                    float xn[16];
-                    load_x16(X, npos < ni.n_active ? ni.active[npos] : -1, xn);
-                    write_a1(A1 + ((it + 1) & 1) * kTileBytes, r, xn, c_f);
-                    write_xs(Xs + ((it + 1) & 1) * 128 * 16, r, xn);
+                    write_seed_rows<kD>(A1 + ((it + 1) & 1) * kHalves * kTileBytes, Xs + ((it + 1) & 1) * 128 * kD, r, X,
+                                        npos < ni.n_active ? ni.active[npos] : -1, c_f);
                     fence_proxy_async();
                     mbar_arrive(&a1_full[(it + 1) & 1]);
                 }
@@ -489,7 +551,7 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
             // before their a1_full arrival (at the start of the previous item,
             // after every mask warp had finished the item before it).
             bool ok = warp_wait(&a1_full[it & 1], (it >> 1) & 1, abort);
-            const float* xs = Xs + (it & 1) * 128 * 16 + r * 16;
+            const float* xs = Xs + (it & 1) * 128 * kD + r * kD;
             for (int pt = pt0; pt < pt1 && ok; ++pt, ++g) {
 #pragma unroll
                 for (int hh = 0; hh < kUPS; ++hh) {
@@ -505,7 +567,7 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                     tc_fence_after();
                     uint32_t w[kEarlyStore ? 1 : kSub][16];
                     bool staged = false;  // pixel stage known to be complete (band path)
-    #pragma unroll
+#pragma unroll
                     for (int j = 0; j < kSub; ++j) {
                         uint32_t (&wj)[16] = w[kEarlyStore ? 0 : j];
                         uint32_t v[32];
@@ -517,7 +579,7 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                             __syncwarp();
                             if (lane == 0) mbar_arrive(&s_empty[b]);
                         }
-    #pragma unroll
+#pragma unroll
                         for (int i = 0; i < 16; ++i) wj[i] = ~sign_halves(v[2 * i], v[2 * i + 1]) & 0x3F803F80u;
                         if (__any_sync(0xffffffffu, mn < kBand)) {
                             // Re-decide near-boundary pairs with the FP32 form's dot
@@ -527,15 +589,9 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                             const int s = g % kStages;
                             if (!staged && !(ok = warp_wait(&full[s], (g / kStages) & 1, abort))) break;
                             staged = true;
-                            const uint8_t* stage = Pst + s * kTileBytes;
-                            float x[16];  // the seed (a padding row: zeros)
-    #pragma unroll
-                            for (int k = 0; k < 16; k += 4) {
-                                const float4 t4 = *reinterpret_cast<const float4*>(xs + k);
-                                x[k] = t4.x; x[k + 1] = t4.y; x[k + 2] = t4.z; x[k + 3] = t4.w;
-                            }
+                            const uint8_t* stage = Pst + s * kStageBytes;
                             uint32_t bandm = 0;
-    #pragma unroll
+#pragma unroll
                             for (int i = 0; i < 32; ++i) bandm |= (uint32_t)(fabsf(__uint_as_float(v[i])) < kBand) << i;
                             uint32_t inm = 0, todo = bandm;
                             while (todo) {
@@ -544,12 +600,24 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                                 const int row = hh * kBN + h * kPxPerWarp + j * 32 + i;
                                 if (pt * 128 + row < ii.n) {
                                     ++band_local;
-                                    float pv[16];
-                                    stage_pixel(stage, row, pv);
-                                    if (dot_seq<16>(x, pv) >= c_f) inm |= 1u << i;
+                                    // xs: the seed (a padding row: zeros)
+                                    float d;
+                                    if constexpr (kD == 16) {
+                                        float x[16], pv[16];
+#pragma unroll
+                                        for (int k = 0; k < 16; k += 4) {
+                                            const float4 t4 = *reinterpret_cast<const float4*>(xs + k);
+                                            x[k] = t4.x; x[k + 1] = t4.y; x[k + 2] = t4.z; x[k + 3] = t4.w;
+                                        }
+                                        stage_pixel16(stage, row, pv);
+                                        d = dot_seq<16>(x, pv);
+                                    } else {
+                                        d = stage_dot<kD>(stage, row, xs);
+                                    }
+                                    if (d >= c_f) inm |= 1u << i;
                                 }
                             }
-    #pragma unroll
+#pragma unroll
                             for (int k = 0; k < 16; ++k) {
                                 const uint32_t bm = (bandm >> (2 * k)) & 3u;
                                 const uint32_t im = (inm >> (2 * k)) & 3u;
@@ -559,7 +627,7 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                             }
                         }
                         if (kDebug) {
-    #pragma unroll
+#pragma unroll
                             for (int i = 0; i < 32; ++i)
                                 dbg_S[(int64_t)r * dbg_stride + pt * 128 + hh * kBN + h * kPxPerWarp + j * 32 + i] =
                                     __uint_as_float(v[i]);
@@ -576,7 +644,7 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
                     if constexpr (!kEarlyStore) {
                         if (u >= kMBufs && !(ok = warp_wait(&m_empty[mb], mph ^ 1, abort))) break;
                         tc_fence_after();
-    #pragma unroll
+#pragma unroll
                         for (int j = 0; j < kSub; ++j)
                             tmem_st16(tmem + kColM + mb * (kBN / 2) + lane_base + h * (kPxPerWarp / 2) + j * 16, w[j]);
                     }
@@ -590,24 +658,40 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
             if (lead) {
                 if (!warp_wait(d_full, it & 1, abort)) break;
                 tc_fence_after();
-                uint32_t yh[16], ym[16], yl[16], yc[16];
+                // Y: per half [sum ph | sum pm | sum pl | count] (the count in
+                // half 0); Y is handed back after the last half's load, the
+                // sums go out as fixed-point reductions half by half
                 const uint32_t ty = tmem + kColY + lane_base;
-                tmem_ld16(ty, yh);
-                tmem_ld16(ty + 16, ym);
-                tmem_ld16(ty + 32, yl);
-                tmem_ld16(ty + 48, yc);
-                tmem_ld_wait();
-                tc_fence_before();
-                mbar_arrive(d_empty);
-                const float cntf = __uint_as_float(yc[0]);
-                if (slot >= 0 && cntf > 0.f) {
-                    unsigned long long* a = acc + (int64_t)slot * 17;
+                bool live = false;
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        const float y = __uint_as_float(yh[k]) + __uint_as_float(ym[k]) + __uint_as_float(yl[k]);
-                        atomicAdd(a + k, (unsigned long long)__float2ll_rn(y * kFixScale));
+                for (int hf = 0; hf < kHalves; ++hf) {
+                    uint32_t yh[16], ym[16], yl[16];
+                    tmem_ld16(ty + 64 * hf, yh);
+                    tmem_ld16(ty + 64 * hf + 16, ym);
+                    tmem_ld16(ty + 64 * hf + 32, yl);
+                    float cntf = 0.f;
+                    if (hf == 0) {
+                        uint32_t yc[16];
+                        tmem_ld16(ty + 48, yc);
+                        tmem_ld_wait();
+                        cntf = __uint_as_float(yc[0]);
+                        live = slot >= 0 && cntf > 0.f;
+                    } else {
+                        tmem_ld_wait();
                     }
-                    atomicAdd(a + 16, (unsigned long long)__float2ll_rn(cntf));
+                    if (hf == kHalves - 1) {
+                        tc_fence_before();
+                        mbar_arrive(d_empty);
+                    }
+                    if (live) {
+                        unsigned long long* a = acc + (int64_t)slot * (kD + 1);
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) {
+                            const float y = __uint_as_float(yh[k]) + __uint_as_float(ym[k]) + __uint_as_float(yl[k]);
+                            atomicAdd(a + 16 * hf + k, (unsigned long long)__float2ll_rn(y * kFixScale));
+                        }
+                        if (hf == 0) atomicAdd(a + kD, (unsigned long long)__float2ll_rn(cntf));
+                    }
                 }
             }
         }
@@ -623,12 +707,15 @@ k_shift_tc(const __grid_constant__ CUtensorMap pmap, const float* __restrict__ P
 // Pixels as BF16 splits for the tensor cores: row i = [Ph | Pm | Pl | 1 1 1 0..0]
 // (64 values, 128 bytes) with p = Ph + Pm + Pl; rows from the foreground count
 // n (read on the device) up to `rows` hold only the ones, so they score
-// S' = -c and never enter a window.
-__global__ void k_pack_bf16(const float* __restrict__ P32, const DevCounters* __restrict__ dc, int rows,
+// S' = -c and never enter a window. For D = 32 a second array of `rows` rows
+// follows, holding dimensions 16..31 the same way without the ones.
+__global__ void k_pack_bf16(const float* __restrict__ P32, const DevCounters* __restrict__ dc, int rows, int D,
                             uint4* __restrict__ Pk) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= rows) return;
-    pack_split_row(i < dc->n_fg ? P32 + (int64_t)i * 16 : nullptr, Pk + (int64_t)i * 8);
+    const bool fg = i < dc->n_fg;
+    pack_split_row(fg ? P32 + (int64_t)i * D : nullptr, Pk + (int64_t)i * 8);
+    if (D == 32) pack_split_row(fg ? P32 + (int64_t)i * D + 16 : nullptr, Pk + ((int64_t)rows + i) * 8, false);
 }
 
 ms_status encode_pmap(void* Pk, int n_pad, CUtensorMap* map) {
@@ -668,15 +755,15 @@ ms_status with_tc_shape(int shape, Fn&& fn) {
     }
 }
 
-template <class Map>
+template <class Map, int D>
 ms_status allow_smem_all_shapes() {
     const auto f = [](auto sh) -> ms_status {
         using Sh = decltype(sh);
-        MS_CUDA(cudaFuncSetAttribute(k_shift_tc<Sh, false, Map>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kSmemBytes));
-        if constexpr (std::is_same_v<Map, TcSingleMap>)  // the score dump is a single-frame self-test
-            MS_CUDA(cudaFuncSetAttribute(k_shift_tc<Sh, true, Map>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemBytes));
+        MS_CUDA(cudaFuncSetAttribute(k_shift_tc<Sh, D, false, Map>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     TcDim<D>::kSmemBytes));
+        if constexpr (std::is_same_v<Map, TcSingleMap> && D == 16)  // the score dump is a d = 16 self-test
+            MS_CUDA(cudaFuncSetAttribute(k_shift_tc<Sh, D, true, Map>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TcDim<D>::kSmemBytes));
         return MS_OK;
     };
     for (int k = 0; k < kTcShapes; ++k)
@@ -686,22 +773,30 @@ ms_status allow_smem_all_shapes() {
 
 }  // namespace
 
-int tc_smem_bytes() { return kSmemBytes; }
+int tc_smem_bytes(int D) { return D == 32 ? TcDim<32>::kSmemBytes : TcDim<16>::kSmemBytes; }
 
 ms_status tc_pack_async(ms_ctx* ctx) {
     const int rows = (int)((ctx->n_pixels + 127) / 128 * 128);
     if (rows == 0) return MS_OK;
-    k_pack_bf16<<<(unsigned)((rows + 255) / 256), 256, 0, ctx->stream>>>(ctx->P32, ctx->dc, rows, (uint4*)ctx->Pk);
+    k_pack_bf16<<<(unsigned)((rows + 255) / 256), 256, 0, ctx->stream>>>(ctx->P32, ctx->dc, rows, (int)ctx->Dp,
+                                                                         (uint4*)ctx->Pk);
     MS_LAUNCH("k_pack_bf16");
     ctx->launches += 1;
     return MS_OK;
 }
 
 ms_status tc_finish(ms_ctx* ctx) {
-    if (ms_status st = allow_smem_all_shapes<TcSingleMap>(); st != MS_OK) return st;
+    ms_status st = ctx->Dp == 32 ? allow_smem_all_shapes<TcSingleMap, 32>() : allow_smem_all_shapes<TcSingleMap, 16>();
+    if (st != MS_OK) return st;
     ctx->tc_grid = ctx->num_sms;  // one CTA per SM: it owns all 512 TMEM columns
-    if (ms_status ls = label_tc_setup(); ls != MS_OK) return ls;
-    return encode_pmap(ctx->Pk, (int)ctx->n_pad, &ctx->pmap);
+    if (ctx->Mk)
+        if (ms_status ls = label_tc_setup(); ls != MS_OK) return ls;
+    // the packed rows use the padding of the workspace (n_pixels rounded up to 128)
+    const int64_t rows = (ctx->n_pixels + 127) / 128 * 128;
+    if ((st = encode_pmap(ctx->Pk, (int)ctx->n_pad, &ctx->pmap)) != MS_OK) return st;
+    if (ctx->Dp == 32) return encode_pmap((uint8_t*)ctx->Pk + rows * 128, (int)ctx->n_pad, &ctx->pmap1);
+    ctx->pmap1 = ctx->pmap;
+    return MS_OK;
 }
 
 ms_status launch_shift_tc(ms_ctx* ctx, const int32_t* active, int grid, int target_items, float* dbg_S) {
@@ -715,12 +810,17 @@ ms_status launch_shift_tc(ms_ctx* ctx, const int32_t* active, int grid, int targ
     unsigned long long* band = (unsigned long long*)&ctx->dc->band_pairs;
     return with_tc_shape(ctx->cfg.tc_shape, [&](auto sh) -> ms_status {
         using Sh = decltype(sh);
-        if (dbg_S)
-            k_shift_tc<Sh, true, TcSingleMap><<<grid, Sh::kThreads, kSmemBytes, ctx->stream>>>(
-                ctx->pmap, ctx->P32, ctx->X, ctx->acc, c, map, &ctx->dc->status, band, dbg_S, ctx->n_pad);
-        else
-            k_shift_tc<Sh, false, TcSingleMap><<<grid, Sh::kThreads, kSmemBytes, ctx->stream>>>(
-                ctx->pmap, ctx->P32, ctx->X, ctx->acc, c, map, &ctx->dc->status, band, nullptr, 0);
+        if (ctx->Dp == 32) {
+            if (dbg_S) return set_error(MS_ERR_INVALID_ARG, "the score dump is for d <= 16");
+            k_shift_tc<Sh, 32, false, TcSingleMap><<<grid, Sh::kThreads, TcDim<32>::kSmemBytes, ctx->stream>>>(
+                ctx->pmap, ctx->pmap1, ctx->P32, ctx->X, ctx->acc, c, map, &ctx->dc->status, band, nullptr, 0);
+        } else if (dbg_S) {
+            k_shift_tc<Sh, 16, true, TcSingleMap><<<grid, Sh::kThreads, TcDim<16>::kSmemBytes, ctx->stream>>>(
+                ctx->pmap, ctx->pmap1, ctx->P32, ctx->X, ctx->acc, c, map, &ctx->dc->status, band, dbg_S, ctx->n_pad);
+        } else {
+            k_shift_tc<Sh, 16, false, TcSingleMap><<<grid, Sh::kThreads, TcDim<16>::kSmemBytes, ctx->stream>>>(
+                ctx->pmap, ctx->pmap1, ctx->P32, ctx->X, ctx->acc, c, map, &ctx->dc->status, band, nullptr, 0);
+        }
         MS_LAUNCH("k_shift_tc");
         return MS_OK;
     });
@@ -761,14 +861,14 @@ struct TcBatchMap {
     }
 };
 
-ms_status tc_batch_setup() {
-    return allow_smem_all_shapes<TcBatchMap>();
+ms_status tc_batch_setup(int D) {
+    return D == 32 ? allow_smem_all_shapes<TcBatchMap, 32>() : allow_smem_all_shapes<TcBatchMap, 16>();
 }
 
-ms_status launch_shift_tc_batch(const CUtensorMap& pmap, const float* P32, const float* X, unsigned long long* acc,
-                                float c_f, const BFrame* frames, const BState* states, BPlan plan,
-                                const int32_t* act0, const int32_t* act1, int nf, int* status,
-                                unsigned long long* band, int grid, int shape, cudaStream_t st) {
+ms_status launch_shift_tc_batch(const CUtensorMap& pmap, const CUtensorMap& pmap1, int D, const float* P32,
+                                const float* X, unsigned long long* acc, float c_f, const BFrame* frames,
+                                const BState* states, BPlan plan, const int32_t* act0, const int32_t* act1, int nf,
+                                int* status, unsigned long long* band, int grid, int shape, cudaStream_t st) {
     TcBatchMap map;
     map.frames = frames;
     map.states = states;
@@ -779,8 +879,12 @@ ms_status launch_shift_tc_batch(const CUtensorMap& pmap, const float* P32, const
     map.total_ = 0;
     return with_tc_shape(shape, [&](auto sh) -> ms_status {
         using Sh = decltype(sh);
-        k_shift_tc<Sh, false, TcBatchMap><<<grid, Sh::kThreads, kSmemBytes, st>>>(pmap, P32, X, acc, c_f, map,
-                                                                                 status, band, nullptr, 0);
+        if (D == 32)
+            k_shift_tc<Sh, 32, false, TcBatchMap><<<grid, Sh::kThreads, TcDim<32>::kSmemBytes, st>>>(
+                pmap, pmap1, P32, X, acc, c_f, map, status, band, nullptr, 0);
+        else
+            k_shift_tc<Sh, 16, false, TcBatchMap><<<grid, Sh::kThreads, TcDim<16>::kSmemBytes, st>>>(
+                pmap, pmap1, P32, X, acc, c_f, map, status, band, nullptr, 0);
         MS_LAUNCH("k_shift_tc(batch)");
         return MS_OK;
     });

@@ -232,8 +232,9 @@ __device__ __forceinline__ float bf16_round(float x) {
 // components, or nullptr for a padding row): [vh | vm | vl | 1 1 1 0..0], where
 // vh = RN(v), vm = RN(v - vh), vl = (v - vh) - vm, so v = vh + vm + vl exactly
 // (|v_k| >= 2^-100 or 0). The ones give a -c column against a split constant
-// and the shift's window size in its second GEMM.
-__device__ __forceinline__ void pack_split_row(const float* v, uint4* row) {
+// and the shift's window size in its second GEMM; ones = false leaves them 0
+// (the second half of a 32-dimensional vector's rows).
+__device__ __forceinline__ void pack_split_row(const float* v, uint4* row, bool ones = true) {
     uint32_t w[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) w[k] = 0u;
@@ -248,8 +249,10 @@ __device__ __forceinline__ void pack_split_row(const float* v, uint4* row) {
             w[16 + k / 2] = pack_bf16((p0 - h0) - m0, (p1 - h1) - m1);
         }
     }
-    w[24] = pack_bf16(1.f, 1.f);
-    w[25] = pack_bf16(1.f, 0.f);
+    if (ones) {
+        w[24] = pack_bf16(1.f, 1.f);
+        w[25] = pack_bf16(1.f, 0.f);
+    }
 #pragma unroll
     for (int c = 0; c < 8; ++c) row[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
 }

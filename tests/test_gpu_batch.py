@@ -83,9 +83,10 @@ def test_batch_equals_single_frames_bf16(ms_lib):
     _compare_to_single(ms_lib, _frames_mixed(), precision=ms_lib.MS_BF16)
 
 
-def test_batch_equals_single_frames_d32(ms_lib):
+@pytest.mark.parametrize("bf16", [False, True])
+def test_batch_equals_single_frames_d32(ms_lib, bf16):
     frames = [(f.emb, f.mask) for f in synth.batch_c4(seed=6, B=3, d=32, n_lo=800, n_hi=6000)]
-    _compare_to_single(ms_lib, frames)
+    _compare_to_single(ms_lib, frames, precision=ms_lib.MS_BF16 if bf16 else ms_lib.MS_FP32)
 
 
 def test_batch_all_seeds_algorithm1(ms_lib):
@@ -152,9 +153,9 @@ def test_batch_rejects_bad_frames(ms_lib):
         ms_lib.ms_batch_run(b)
     assert err.value.status == ms_lib.MS_ERR_INVALID_ARG
     b.close()
-    bad = ms_lib.ms_config_default(dim=32, precision=ms_lib.MS_BF16)
+    bad = ms_lib.ms_config_default(dim=33, precision=ms_lib.MS_BF16)
     with pytest.raises(ms_lib.MsError):
-        ms_lib.ms_batch_create(bad, [torch.zeros((4, 32), device="cuda")])
+        ms_lib.ms_batch_create(bad, [torch.zeros((4, 33), device="cuda")])
 
 
 def test_batch_host_buffers_and_profile(ms_lib):

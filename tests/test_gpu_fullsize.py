@@ -259,7 +259,7 @@ def test_c2_frames_batched_as_benchmarked(ms_lib):
         b.close()
 
 
-@pytest.mark.parametrize("d,bf16,n_single", [(16, True, 64), (32, False, 6)])
+@pytest.mark.parametrize("d,bf16,n_single", [(16, True, 64), (32, False, 6), (32, True, 6)])
 def test_c4_batch_equals_single_frames(ms_lib, d, bf16, n_single):
     import torch
     fs = synth.batch_c4(seed=0, B=64, d=d)

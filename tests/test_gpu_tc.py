@@ -130,3 +130,35 @@ def test_tile_shape_out_of_range_is_rejected(ms_lib):
     with pytest.raises(ms_lib.MsError) as e:
         _run(ms_lib, f.emb, precision=ms_lib.MS_BF16, tc_shape=8)
     assert e.value.status == ms_lib.MS_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------- d = 32
+# The tensor-core form for 17 <= d <= 32: two 16-dimensional halves, each with
+# its own BF16 split operand tiles (seven GEMM1 products per tile, two Y
+# blocks in GEMM2), the same FP32 re-decision band, and FP32 labelling.
+
+
+@pytest.mark.parametrize("d", [32, 18])
+def test_bf16_d32_equals_fp32_form_and_oracle(ms_lib, d):
+    f = synth.make_frame(11, 96, 96, d, 6000, 9, 600.0, 0.3, 40.0, 200.0, 0.02)
+    a = _run(ms_lib, f.emb, f.mask, precision=ms_lib.MS_FP32)
+    b = _run(ms_lib, f.emb, f.mask, precision=ms_lib.MS_BF16)
+    # identical window decisions: the same rounds, seeds and modes
+    assert np.array_equal(a[2]["round_log"], b[2]["round_log"])
+    assert np.array_equal(a[2]["seed_log"], b[2]["seed_log"])
+    assert a[1].shape == b[1].shape
+    assert same_order_errors(a[1], b[1]).max() <= 1e-6
+    assert matched_agreement(a[0], b[0]) >= 0.999
+    ref = oracle.run(f.emb, f.mask)
+    assert mode_errors(b[1], ref.modes).max() <= 1e-5
+    assert matched_agreement(ref.labels, b[0]) >= 0.999
+    assert (b[0][f.mask == 0] == -1).all()
+
+
+@pytest.mark.parametrize("shape", [2, 4, 6])
+def test_bf16_d32_tile_shapes_are_bit_identical(ms_lib, shape):
+    f = synth.make_frame(12, 64, 64, 32, 3000, 6, 400.0, 0.3, 60.0, 200.0, 0.02)
+    a = _run(ms_lib, f.emb, f.mask, precision=ms_lib.MS_BF16)
+    b = _run(ms_lib, f.emb, f.mask, precision=ms_lib.MS_BF16, tc_shape=shape)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(a[2]["round_log"], b[2]["round_log"])

@@ -501,6 +501,52 @@ def vmf_leg(n_sm, clk):
                      "note": "forward steps on the tensor cores; the adjoint passes stay FP32 SIMT"}}
 
 
+def d32_leg(n_sm):
+    """The 32-dimensional case on one 512x512 frame shaped like the headline
+    workload (131072 foreground pixels, d = 32): whole-frame time of the FP32
+    and BF16 forms through ms_run, and one shift launch of 4096 seeds (the
+    tensor-core form is two 16-dimensional halves). Algorithmic work: 4d flops
+    per seed-pixel pair."""
+    import torch
+
+    import paper_2007_14283_gb300 as ms
+    import synth
+    f = synth.frame_c2(seed=0, d=32)
+    e = torch.from_numpy(f.emb).cuda()
+    m = torch.from_numpy(f.mask).cuda()
+    out = {"config": "512x512 frame, 131072 foreground pixels, d=32 (synthetic vMF cells)"}
+    for name, prec in (("fp32", ms.MS_FP32), ("bf16", ms.MS_BF16)):
+        ts = []
+        for rep in range(3):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            res = ms.cluster(e, m, precision=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            if rep:
+                ts.append(e0.elapsed_time(e1))
+        cfg = ms.ms_config_default(dim=32, precision=prec)
+        st_ms = []
+        for rep in range(5):
+            ctx = ms.ms_create(cfg, e, m)
+            ms.ms_profile(ctx, True)
+            seeded = ms.ms_seed_batch(ctx, 4096)
+            try:
+                ms.ms_iterate(ctx, 1)
+            except ms.MsError as err:
+                if err.status != ms.MS_ERR_NOT_CONVERGED:
+                    raise
+            st_ms.append(ms.ms_stats_get(ctx)["shift_ms"])
+            ctx.close()
+        t = statistics.median(st_ms[1:])
+        out[name] = {"frame_ms": statistics.median(ts), "modes": int(res.modes.shape[0]),
+                     "shift_4096_seeds_ms": t,
+                     "shift_tflops": 4.0 * 32 * N_FG * seeded / (t * 1e-3) / 1e12}
+    return out
+
+
 def kernel_variants_leg(n_sm, clk):
     """Other distances and profiles (ms_kernel_shift) at the differentiable
     configuration's size: N = 65536 vectors, M = 1024 seeds, d = 16, T = 10.
@@ -804,9 +850,10 @@ def run_ours(args, rank, ws, local):
     video = None
     if rank == 0 and args.video_frames > 0:
         video = video_leg(args.video_frames)
-    kvar = None
+    kvar, d32 = None, None
     if rank == 0 and not args.no_vmf:
         kvar = kernel_variants_leg(n_sm, clk)
+        d32 = d32_leg(n_sm)
     cpu, parity = None, None
     if rank == 0 and args.cpu != "none":
         import oracle
@@ -865,7 +912,7 @@ def run_ours(args, rank, ws, local):
                            "autotune": main.tuning,
                            "fp32_rechecked_pair_fraction": tot.get("band_pairs", 0) /
                            max(1.0, float(tot["seed_iters"]) * N_FG)},
-                "roofline": roofline, "forms": forms, "smooth_kernel": vmf, "kernel_variants": kvar,
+                "roofline": roofline, "forms": forms, "smooth_kernel": vmf, "kernel_variants": kvar, "d32": d32,
                 "video": video,
                 "parity_vs_oracle": parity,
                 "cpu_baseline": cpu,

@@ -1128,11 +1128,21 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     k_b_merge_append<Dp><<<B, kIT, 0, s>>>(b->frames, b->states, b->X, b->cand, b->rank_cand, b->cand_state,
                                            b->modes);
     LAUNCHED("k_b_merge_append");
-    k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, B, kSelDonePixels, kPT * cov_per(Dp), 0, b->blk_off);
-    LAUNCHED("k_b_blocks");
-    k_b_cover<Dp><<<G, kPT, 0, s>>>(b->frames, b->states, B, b->blk_off, b->d, b->P32, b->pix, b->covered, b->modes,
-                                    (float)b->cfg.bandwidth_cos, b->cfg.bandwidth_cos);
-    LAUNCHED("k_b_cover");
+    if (b->Mk) {  // BF16 form, d <= 16: the pixels against the new modes on the tensor cores
+        k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, B, kSelDonePixels, 128, 0, b->blk_off);
+        LAUNCHED("k_b_blocks");
+        ms_status cs = launch_cover_tc_batch(b->pmap, b->mmap, b->Mk, b->frames, b->states, B, (int)b->max_pk_rows,
+                                             b->modes, b->P32, b->pix, b->d, b->cfg.bandwidth_cos, b->covered,
+                                             b->blk_off, b->lsc, b->num_sms, b->misc + 1, s);
+        if (cs != MS_OK) return cs;
+        nl += 3;
+    } else {
+        k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, B, kSelDonePixels, kPT * cov_per(Dp), 0, b->blk_off);
+        LAUNCHED("k_b_blocks");
+        k_b_cover<Dp><<<G, kPT, 0, s>>>(b->frames, b->states, B, b->blk_off, b->d, b->P32, b->pix, b->covered,
+                                        b->modes, (float)b->cfg.bandwidth_cos, b->cfg.bandwidth_cos);
+        LAUNCHED("k_b_cover");
+    }
     k_b_schedule<<<(B + 255) / 256, 256, 0, s>>>(b->states, B, b->cfg.P_target, L, b->cfg.H, b->cfg.max_rounds,
                                                  b->cfg.all_seeds);
     LAUNCHED("k_b_schedule");

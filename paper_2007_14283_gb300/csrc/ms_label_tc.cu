@@ -55,14 +55,16 @@ struct LbItem {
     int pk_row0;   // Pk / Mk row of the frame's pixel 0 and mode 0 (multiple of 128)
     int pt;        // pixel tile
     int n;         // the frame's foreground count
-    int K;         // the frame's kept modes
+    int K;         // the frame's kept modes (the end of the scored mode range)
+    int k0;        // the first scored mode (0 for labelling; coverage scores a round's new modes)
 };
 
 struct LbSingle {
     int n, K;
     __device__ __forceinline__ bool init() { return n > 0; }
     __device__ __forceinline__ int total() const { return (n + 127) / 128; }
-    __device__ __forceinline__ LbItem item(int i) const { return LbItem{0, 0, i, n, K}; }
+    int k0 = 0;
+    __device__ __forceinline__ LbItem item(int i) const { return LbItem{0, 0, i, n, K, k0}; }
 };
 
 struct LbBatch {
@@ -79,7 +81,28 @@ struct LbBatch {
     __device__ __forceinline__ LbItem item(int i) const {
         const int f = locate(off, B, i);
         const BFrame& fr = frames[f];
-        return LbItem{f, fr.pk_row0, i - off[f], fr.n, states[f].dc.n_kept};
+        return LbItem{f, fr.pk_row0, i - off[f], fr.n, states[f].dc.n_kept, 0};
+    }
+};
+
+// Coverage in the batch: the pixel tiles of the frames whose round ended
+// (off from k_b_blocks with 128 pixels per block), each against its frame's
+// new modes [k0, n_kept).
+struct LbBatchCover {
+    const BFrame* frames;
+    const BState* states;
+    const int32_t* off;
+    int B;
+    int total_;
+    __device__ __forceinline__ bool init() {
+        total_ = off[B];
+        return total_ > 0;
+    }
+    __device__ __forceinline__ int total() const { return total_; }
+    __device__ __forceinline__ LbItem item(int i) const {
+        const int f = locate(off, B, i);
+        const BFrame& fr = frames[f];
+        return LbItem{f, fr.pk_row0, i - off[f], fr.n, states[f].dc.n_kept, states[f].k0};
     }
 };
 
@@ -103,9 +126,19 @@ struct LbOut {
     const int32_t* pix;        // foreground index -> pixel index, all frames
     int2* fix;                 // near-ties (frame, foreground index)
     int* fix_count;
+    // coverage: the covered flags (all frames), the uncovered count (single
+    // form) or the frames' states (batch form), and c
+    uint8_t* covered;
+    int* n_uncovered;
+    float c_f;
+    BState* states;
 };
 
-template <class Map>
+// kCover = false: labelling (best and second-best mode of every pixel).
+// kCover = true: coverage of the OSOP stop rule against the modes [k0, K):
+// an uncovered pixel whose best score clears c by kEpsTc is covered; one
+// within kEpsTc of c is queued for the FP32 form's exact test.
+template <class Map, bool kCover>
 __global__ void __launch_bounds__(kLThreads, 1)
 k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap mmap, Map map, LbOut out,
            int* status) {
@@ -167,8 +200,8 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
         bool ok = true;
         for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
             const LbItem ii = map.item(item);
-            const int nmt = (ii.K + 127) / 128;
-            if (nmt == 0) continue;
+            const int nmt = (ii.K - ii.k0 + 127) / 128;
+            if (nmt <= 0) continue;
             const int ab = ia & 1;
             if (ia >= 2 && !(ok = lwarp_wait(&a_empty[ab], ((ia >> 1) - 1) & 1, abort))) break;
             if (lane == 0) {
@@ -182,7 +215,7 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
                 if (g >= kLStages && !(ok = lwarp_wait(&b_empty[s], ((g / kLStages) - 1) & 1, abort))) break;
                 if (lane == 0) {
                     mbar_arrive_expect_tx(&b_full[s], kLTile);
-                    tma_load_2d(Bst + s * kLTile, &mmap, 0, ii.pk_row0 + mt * 128, &b_full[s]);
+                    tma_load_2d(Bst + s * kLTile, &mmap, 0, ii.pk_row0 + ii.k0 + mt * 128, &b_full[s]);
                 }
                 __syncwarp();
             }
@@ -201,8 +234,8 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
         bool ok = true;
         for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
             const LbItem ii = map.item(item);
-            const int nmt = (ii.K + 127) / 128;
-            if (nmt == 0) continue;
+            const int nmt = (ii.K - ii.k0 + 127) / 128;
+            if (nmt <= 0) continue;
             const int ab = ia & 1;
             if (!(ok = lwarp_wait(&a_full[ab], (ia >> 1) & 1, abort))) break;
             const uint64_t a = dA + (uint64_t)ab * kT;
@@ -236,7 +269,8 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
         int g = 0;
         for (int item = blockIdx.x; item < items; item += gridDim.x) {
             const LbItem ii = map.item(item);
-            const int nmt = (ii.K + 127) / 128;
+            const int nmt = (ii.K - ii.k0 + 127) / 128;
+            if (kCover && nmt <= 0) continue;
             bool ok = true;
             float b1 = -INFINITY, b2 = -INFINITY;
             int i1 = -1;
@@ -250,7 +284,7 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&s_empty[b]);
-                const int col0 = mt * 128 + h * 32;
+                const int col0 = ii.k0 + mt * 128 + h * 32;
                 if (col0 + 32 > ii.K) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
@@ -259,6 +293,10 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
                 float m = __uint_as_float(v[0]);
 #pragma unroll
                 for (int j = 1; j < 32; ++j) m = fmaxf(m, __uint_as_float(v[j]));
+                if (kCover) {
+                    b1 = fmaxf(b1, m);
+                    continue;
+                }
                 // A column can change the best two only if it beats the
                 // second best; in increasing column order a tie keeps the
                 // lower index as the best.
@@ -292,7 +330,24 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
                 : "r"(ok ? 0u : 1u), "n"(kLEpi * 32)
                 : "memory");
             if (any_bad) break;
-            if (h == 0) {
+            if (kCover && h == 0) {
+                const float B1 = fmaxf(fmaxf(xb1[r], xb1[128 + r]), fmaxf(xb1[256 + r], xb1[384 + r]));
+                const int i = ii.pt * 128 + r;
+                const int64_t base = out.frames ? out.frames[ii.frame].pix0 : 0;
+                bool newly = false;
+                if (i < ii.n && !out.covered[base + i]) {
+                    if (B1 >= out.c_f + kEpsTc) {
+                        out.covered[base + i] = 1;
+                        newly = true;
+                    } else if (B1 >= out.c_f - kEpsTc) {
+                        const int slot = atomicAdd(out.fix_count, 1);
+                        out.fix[slot] = make_int2(ii.frame, i);
+                    }
+                }
+                const unsigned nb = __ballot_sync(0xffffffffu, newly);
+                if (lane == 0 && nb)
+                    atomicSub(out.states ? &out.states[ii.frame].dc.n_uncovered : out.n_uncovered, __popc(nb));
+            } else if (!kCover && h == 0) {
                 float B1 = xb1[r], B2 = xb2[r];
                 int I1 = xi1[r];
 #pragma unroll
@@ -466,6 +521,89 @@ __global__ void k_pack_modes_batch(const BFrame* __restrict__ frames, const BSta
     pack_split_row(r < K ? modes + (fr.pix0 + r) * 16 : nullptr, Mk + (int64_t)(fr.pk_row0 + r) * 8);
 }
 
+// Modes [k0, k1) of one frame as BF16 split rows at their Mk rows.
+__global__ void k_pack_modes_range(const float* __restrict__ modes, int k0, int k1, uint4* __restrict__ Mk) {
+    const int r = k0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= k1) return;
+    pack_split_row(modes + (int64_t)r * 16, Mk + (int64_t)r * 8);
+}
+
+// Coverage of the queued pixels (tensor-core score within kEpsTc of c),
+// decided exactly as the FP32 form decides it: one warp per pixel, lanes over
+// the new modes; a mode covers the pixel when its FP32 score clears c by
+// kEpsF32, or is within kEpsF32 of c and the FP64 cosine of the raw embedding
+// reaches c.
+__global__ void k_cover_fix(const int2* __restrict__ fix, const int* __restrict__ fix_count,
+                            const float* __restrict__ P32, const float* __restrict__ modes, int k0, int k1,
+                            const int32_t* __restrict__ pix, const float* __restrict__ emb, int d, float c_f, double c,
+                            uint8_t* __restrict__ covered, int* __restrict__ n_uncovered) {
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int cnt = *fix_count;
+    for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < cnt; e += gridDim.x * wpb) {
+        const int i = fix[e].y;
+        float pv[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) pv[k] = P32[(int64_t)i * 16 + k];
+        const float* em = emb + (int64_t)pix[i] * d;
+        bool cov = false;
+        for (int j = k0 + lane; j < k1 && !cov; j += 32) {
+            const float* m = modes + (int64_t)j * 16;
+            const float sc = dot_seq<16>(pv, m);
+            cov = sc >= c_f + kEpsF32 || (sc >= c_f - kEpsF32 && cos64(em, m, d) >= c);
+        }
+        if (__any_sync(0xffffffffu, cov) && lane == 0) {
+            covered[i] = 1;
+            atomicSub(n_uncovered, 1);
+        }
+    }
+}
+
+// The batch form of k_pack_modes_range: every frame whose round ended packs
+// its new modes [k0, n_kept) at its Mk rows; clears the recheck queue.
+__global__ void k_pack_modes_new_batch(const BFrame* __restrict__ frames, const BState* __restrict__ states,
+                                       const float* __restrict__ modes, uint4* __restrict__ Mk, int* fix_count) {
+    const BFrame& fr = frames[blockIdx.y];
+    const BState& st = states[blockIdx.y];
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *fix_count = 0;
+    if (st.phase != kRoundDone) return;
+    const int r = st.k0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= st.dc.n_kept) return;
+    pack_split_row(modes + (fr.pix0 + r) * 16, Mk + (int64_t)(fr.pk_row0 + r) * 8);
+}
+
+// k_cover_fix for the batch: queued (frame, foreground index) pairs, each
+// against its frame's new modes.
+__global__ void k_cover_fix_batch(const int2* __restrict__ fix, const int* __restrict__ fix_count,
+                                  const float* __restrict__ P32, const float* __restrict__ modes,
+                                  const BFrame* __restrict__ frames, BState* states, const int32_t* __restrict__ pix,
+                                  int d, float c_f, double c, uint8_t* __restrict__ covered) {
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int cnt = *fix_count;
+    for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < cnt; e += gridDim.x * wpb) {
+        const int2 fi = fix[e];
+        const int f = fi.x, i = fi.y;
+        const BFrame& fr = frames[f];
+        const int64_t base = fr.pix0;
+        const int k0 = states[f].k0, k1 = states[f].dc.n_kept;
+        float pv[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) pv[k] = P32[(base + i) * 16 + k];
+        const float* em = fr.emb + (int64_t)pix[base + i] * d;
+        bool cov = false;
+        for (int j = k0 + lane; j < k1 && !cov; j += 32) {
+            const float* m = modes + (base + j) * 16;
+            const float sc = dot_seq<16>(pv, m);
+            cov = sc >= c_f + kEpsF32 || (sc >= c_f - kEpsF32 && cos64(em, m, d) >= c);
+        }
+        if (__any_sync(0xffffffffu, cov) && lane == 0) {
+            covered[base + i] = 1;
+            atomicSub(&states[f].dc.n_uncovered, 1);
+        }
+    }
+}
+
 // Per-frame offsets of the label items (128-pixel tiles); clears the queue.
 __global__ void k_label_items(const BFrame* __restrict__ frames, int B, int32_t* __restrict__ off,
                               int* __restrict__ fix_count) {
@@ -482,8 +620,55 @@ __global__ void k_label_items(const BFrame* __restrict__ frames, int B, int32_t*
 }  // namespace
 
 ms_status label_tc_setup() {
-    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbSingle>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLSmemBytes));
-    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLSmemBytes));
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbSingle, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kLSmemBytes));
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbSingle, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kLSmemBytes));
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbBatch, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kLSmemBytes));
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbBatchCover, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kLSmemBytes));
+    return MS_OK;
+}
+
+ms_status launch_cover_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, void* Mk, const BFrame* frames,
+                                BState* states, int B, int max_pk_rows, const float* modes, const float* P32,
+                                const int32_t* pix, int d, double c, uint8_t* covered, const int32_t* tile_off,
+                                LabelTcScratch sc, int grid, int* status, cudaStream_t st) {
+    const dim3 gp((unsigned)((max_pk_rows + 255) / 256), (unsigned)B);
+    k_pack_modes_new_batch<<<gp, 256, 0, st>>>(frames, states, modes, (uint4*)Mk, sc.fix_count);
+    MS_LAUNCH("k_pack_modes_new_batch");
+    const float c_f = (float)c;
+    LbBatchCover map{frames, states, tile_off, B, 0};
+    LbOut out{nullptr, nullptr, frames, pix, sc.fix, sc.fix_count, covered, nullptr, c_f, states};
+    k_label_tc<LbBatchCover, true><<<grid, kLThreads, kLSmemBytes, st>>>(pmap, mmap, map, out, status);
+    MS_LAUNCH("k_label_tc(cover, batch)");
+    k_cover_fix_batch<<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, P32, modes, frames, states, pix, d, c_f, c,
+                                            covered);
+    MS_LAUNCH("k_cover_fix_batch");
+    return MS_OK;
+}
+
+ms_status launch_cover_tc_single(const CUtensorMap& pmap, void* Mk, int64_t n_pad, const float* modes, int k0,
+                                 int k1, int n, const float* P32, const int32_t* pix, const float* emb, int d,
+                                 double c, uint8_t* covered, int* n_uncovered, LabelTcScratch sc, int grid,
+                                 int* status, cudaStream_t st) {
+    if (n == 0 || k1 <= k0) return MS_OK;
+    MS_CUDA(cudaMemsetAsync(sc.fix_count, 0, sizeof(int), st));
+    k_pack_modes_range<<<(k1 - k0 + 255) / 256, 256, 0, st>>>(modes, k0, k1, (uint4*)Mk);
+    MS_LAUNCH("k_pack_modes_range");
+    CUtensorMap mmap;
+    ms_status s = encode_pk_map(Mk, (int)n_pad, &mmap);
+    if (s != MS_OK) return s;
+    LbSingle map{n, k1};
+    map.k0 = k0;
+    const float c_f = (float)c;
+    LbOut out{nullptr, nullptr, nullptr, pix, sc.fix, sc.fix_count, covered, n_uncovered, c_f, nullptr};
+    k_label_tc<LbSingle, true><<<grid, kLThreads, kLSmemBytes, st>>>(pmap, mmap, map, out, status);
+    MS_LAUNCH("k_label_tc(cover)");
+    k_cover_fix<<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, P32, modes, k0, k1, pix, emb, d, c_f, c, covered,
+                                      n_uncovered);
+    MS_LAUNCH("k_cover_fix");
     return MS_OK;
 }
 
@@ -501,8 +686,8 @@ ms_status launch_label_tc_single(const CUtensorMap& pmap, void* Mk, int64_t n_pa
     ms_status s = encode_pk_map(Mk, (int)n_pad, &mmap);
     if (s != MS_OK) return s;
     LbSingle map{n, K};
-    LbOut out{nullptr, labels, nullptr, pix, sc.fix, sc.fix_count};
-    k_label_tc<LbSingle><<<grid, kLThreads, kLSmemBytes, st>>>(pmap, mmap, map, out, status);
+    LbOut out{nullptr, labels, nullptr, pix, sc.fix, sc.fix_count, nullptr, nullptr, 0.f, nullptr};
+    k_label_tc<LbSingle, false><<<grid, kLThreads, kLSmemBytes, st>>>(pmap, mmap, map, out, status);
     MS_LAUNCH("k_label_tc");
     if (K > 1) {
         k_label_fix_tiled<<<2 * grid, kFixPix * kFixQ, 0, st>>>(sc.fix, sc.fix_count, P32, modes, pix, emb, K, d,
@@ -522,8 +707,8 @@ ms_status launch_label_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap
     k_label_items<<<1, 32, 0, st>>>(frames, B, sc.off, sc.fix_count);
     MS_LAUNCH("k_label_items");
     LbBatch map{frames, states, sc.off, B, 0};
-    LbOut out{labels, nullptr, frames, pix, sc.fix, sc.fix_count};
-    k_label_tc<LbBatch><<<grid, kLThreads, kLSmemBytes, st>>>(pmap, mmap, map, out, status);
+    LbOut out{labels, nullptr, frames, pix, sc.fix, sc.fix_count, nullptr, nullptr, 0.f, nullptr};
+    k_label_tc<LbBatch, false><<<grid, kLThreads, kLSmemBytes, st>>>(pmap, mmap, map, out, status);
     MS_LAUNCH("k_label_tc(batch)");
     k_label_fix<<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, P32, modes, frames, states, pix, nullptr, 0, d, labels,
                                       nullptr);

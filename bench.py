@@ -435,7 +435,7 @@ def vmf_leg(n_sm, clk):
     """Smooth-kernel form on the differentiable configuration: N = 65536 pixels,
     M = 1024 seeds, d = 16, kappa = 20, T = 10. Times ms_vmf_forward and
     ms_vmf_backward (CUDA events, median of 5 after 2 warm-ups), in FP32 and
-    with the forward steps on the tensor cores (MS_BF16).
+    on the tensor cores (MS_BF16: forward steps and both adjoint passes).
 
     Bound: FP32 FMA on the CUDA cores. Per seed-pixel pair and step the
     forward does the 16-term dot product and the 16-term weighted sum (4d = 64
@@ -481,11 +481,20 @@ def vmf_leg(n_sm, clk):
     fwd_b = timed_ms(lambda: ms.ms_vmf_forward(P, X0, kappa, T, precision=BF))
     fwd_b1 = timed_ms(lambda: ms.ms_vmf_forward(P, X0, kappa, 1, precision=BF))
     bwd_b = timed_ms(lambda: ms.ms_vmf_backward(P, X0, kappa, T, G, precision=BF))
+    bwd_b1 = timed_ms(lambda: ms.ms_vmf_backward(P, X0, kappa, 1, G, precision=BF))
     step_b = (fwd_b - fwd_b1) / (T - 1)
+    # one reverse step (k_vmf_gy, the packing, both tensor-core passes and
+    # their reduces): the backward's slope between T = 10 and T = 1 minus the
+    # re-run forward's step; 224 flops per pair (pass A 96, pass B 128)
+    adj_b = (bwd_b - bwd_b1) / (T - 1) - step_b
     bf16_peak = load_peaks().get("bf16_tflops")
     step_tf = 64 * 65536 * 1024 / (step_b * 1e-3) / 1e12
+    adj_tf = 224 * 65536 * 1024 / (adj_b * 1e-3) / 1e12
     xf = ms.ms_vmf_forward(P, X0, kappa, T)
     xb = ms.ms_vmf_forward(P, X0, kappa, T, precision=BF)
+    gf = ms.ms_vmf_backward(P, X0, kappa, T, G)
+    gb = ms.ms_vmf_backward(P, X0, kappa, T, G, precision=BF)
+    grad_rel = [float(((b - f).norm() / f.norm()).item()) for b, f in zip(gb, gf)]
     return {"config": "N=65536 pixels, M=1024 seeds, d=16, kappa=20, T=10 (synthetic vMF cells)",
             "forward_ms": fwd, "backward_ms": bwd,
             "bound": "fp32 fma", "unit": "TFLOP/s",
@@ -493,12 +502,15 @@ def vmf_leg(n_sm, clk):
             "forward_frac": f_tf / fma_peak, "backward_frac": b_tf / fma_peak,
             "algorithmic": "64 flops per seed-pixel pair and step (forward); 288 (adjoint, with the re-run forward)",
             "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz (nominal CUDA-core rate)",
-            "bf16": {"forward_ms": fwd_b, "forward_T1_ms": fwd_b1, "backward_ms": bwd_b, "step_ms": step_b,
-                     "bound": "tensor", "step_achieved": step_tf, "peak": bf16_peak,
+            "bf16": {"forward_ms": fwd_b, "forward_T1_ms": fwd_b1, "backward_ms": bwd_b, "backward_T1_ms": bwd_b1,
+                     "step_ms": step_b, "adjoint_step_ms": adj_b,
+                     "bound": "tensor", "step_achieved": step_tf, "adjoint_step_achieved": adj_tf, "peak": bf16_peak,
                      "step_frac": (step_tf / bf16_peak) if bf16_peak else None,
+                     "adjoint_step_frac": (adj_tf / bf16_peak) if bf16_peak else None,
                      "peak_source": "of measured: cuBLAS bf16 dense, burst (MEASURED_PEAKS.json)",
                      "max_abs_diff_vs_fp32_form": float((xb - xf).abs().max().item()),
-                     "note": "forward steps on the tensor cores; the adjoint passes stay FP32 SIMT"}}
+                     "grad_rel_diff_vs_fp32_form": {"dP": grad_rel[0], "dX0": grad_rel[1]},
+                     "note": "forward steps and both adjoint passes on the tensor cores"}}
 
 
 def d32_leg(n_sm):

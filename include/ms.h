@@ -254,11 +254,17 @@ MS_API ms_status ms_vmf_backward(const float* d_P, int64_t N, const float* d_X0,
  * accumulation), the weight w = exp(kappa (s - 1)) is formed in FP32 and split
  * as w = wh + wl (BF16), and GEMM2 accumulates wh.[ph | pm | pl] + wl.[ph | pm]
  * in FP32; per-chunk sums are
- * added in a fixed order, so results are deterministic. The adjoint passes of
- * ms_vmf_backward_ex stay FP32 and differentiate the BF16 iterates. With
- * MS_BF16 the call synchronises `stream` once at the end to read the device
- * status: MS_ERR_TIMEOUT if a bounded wait inside the kernel gave up (the
- * outputs are then NaN). */
+ * added in a fixed order, so results are deterministic. ms_vmf_backward_ex
+ * with MS_BF16 also runs both reverse passes of every step on the tensor
+ * cores (the derivative of the step above): with gy = (g - x'(x'.g))/|y|,
+ * the scores kappa log2(e) x.p and gy.p come from six products of three-term
+ * splits each, w and ds = kappa w (gy.p) are split into two BF16 terms, and
+ * dL/dx = sum_i ds p_i (seeds as rows) and dL/dp_i += sum_m w gy_m + ds x_m
+ * (pixels as rows) accumulate in FP32, per-chunk sums again added in a fixed
+ * order. With MS_BF16 the forward synchronises `stream` once at the end, the
+ * backward twice (after the re-run forward and at the end), to read the
+ * device status: MS_ERR_TIMEOUT if a bounded wait inside a kernel gave up
+ * (the outputs are then NaN). */
 MS_API ms_status ms_vmf_forward_ex(const float* d_P, int64_t N, const float* d_X0, int32_t M, int32_t dim,
                                    double kappa, int32_t T, int32_t precision, float* d_XT, void* stream);
 MS_API ms_status ms_vmf_backward_ex(const float* d_P, int64_t N, const float* d_X0, int32_t M, int32_t dim,

@@ -329,7 +329,7 @@ def ms_vmf_forward(P, X0, kappa: float, T: int, stream=None, precision: int = MS
 
 def ms_vmf_backward(P, X0, kappa: float, T: int, GT, stream=None, precision: int = MS_FP32):
     """(dL/dP, dL/dX0) for upstream gradient GT = dL/dx_T (the iterates are
-    recomputed in `precision`; the adjoint passes are FP32)."""
+    recomputed and the adjoint passes run in `precision`)."""
     import torch
     dP = torch.empty_like(P)
     dX0 = torch.empty_like(X0)

@@ -211,4 +211,28 @@ ms_status vmf_tc_prepare(const float* P, int64_t N, void* Pk, CUtensorMap* map, 
 ms_status vmf_tc_step(const CUtensorMap& map, const float* Xt, int32_t M, float kappa, const VmfTcPlan& plan,
                       float* partial, int* status, float* Xn, float* ynorm, cudaStream_t st);
 
+// ms_vmf_tc_adj.cu: the smooth-kernel adjoint step on the tensor cores.
+struct VmfAdjPlan {
+    int row_tiles, n_sub, chunks, spc, items, grid;  // 128-row tiles x chunks of spc 64-column sub-tiles
+};
+struct VmfAdjWork {
+    CUtensorMap pk_rows, pk_cols;  // Pk (BF16 split pixel rows) in 128-row and 64-row boxes
+    CUtensorMap v_rows, v_cols;    // Vk: split rows of kappa log2(e) x_t
+    CUtensorMap g_rows, g_cols;    // Gk: split rows of gy
+    void* Vk;
+    void* Gk;
+    float* partial;                // per item 128 rows x 16 sums
+    VmfAdjPlan pa, pb;             // pass A (rows: seeds), pass B (rows: pixels)
+    int32_t M, Mp;
+    int64_t N;
+};
+// Workspace bytes of vmf_adj_prepare for M seeds, N pixels and `grid` CTAs.
+size_t vmf_adj_bytes(int32_t M, int64_t N, int grid);
+// Lays out the workspace ws and encodes the TMA maps; Pk as vmf_tc_prepare wrote it.
+ms_status vmf_adj_prepare(void* Pk, int64_t N, int32_t M, int grid, void* ws, VmfAdjWork* w);
+// One reverse step: g_out = dL/dx_t (overwritten) and dP += dL/dp from this
+// step, given x_t and gy_t (k_vmf_gy). A raised *status poisons g_out (NaN).
+ms_status vmf_adj_step(VmfAdjWork* w, const float* Xt, const float* GY, float kappa, int* status, float* g_out,
+                       float* dP, cudaStream_t st);
+
 }  // namespace ms

@@ -20,7 +20,8 @@
 // ever stored. Reductions go through per-chunk partial sums added in a fixed
 // order, so results are deterministic for a given GPU (the chunks fill one wave
 // of resident blocks). The weights are evaluated as 2^(kappa log2(e) (s - 1))
-// with exp2f. d = 16.
+// with exp2f. d = 16. The BF16 form runs the forward steps (ms_vmf_tc.cu) and
+// both reverse passes (ms_vmf_tc_adj.cu) on the tensor cores instead.
 #include "ms_internal.cuh"
 
 namespace ms {
@@ -291,7 +292,7 @@ k_vmf_bwd_pixels(const float* __restrict__ P, int64_t N, const float* __restrict
 }
 
 struct VmfWork {
-    bool tc;        // steps on the tensor cores (BF16 splits); the adjoint passes stay FP32
+    bool tc;        // steps and adjoint passes on the tensor cores (BF16 splits)
     void* Pk;       // tc: BF16 split rows of P
     float* tc_partial;
     int* status;    // tc: raised by a bounded wait that gave up
@@ -302,8 +303,11 @@ struct VmfWork {
     float* ynorm;   // [T, M]
     float* gy;      // [M, 16]
     float* g;       // [M, 16]
+    VmfAdjWork adj; // tc backward: the tensor-core adjoint's plans, maps and buffers
     VSplit sp;      // forward items (512-seed tiles)
     VSplit spa;     // adjoint pass A items (256-seed tiles)
+    void* adj_ws;   // tc backward: workspace of the tensor-core adjoint
+    int sms;
 };
 
 // Resident blocks of a kernel over the whole GPU (blocks per SM x SMs).
@@ -324,23 +328,25 @@ ms_status vmf_validate(const float* P, int64_t N, const float* X0, int32_t M, in
     return MS_OK;
 }
 
-ms_status vmf_alloc(VmfWork* w, int64_t N, int32_t M, int32_t T, bool tc, cudaStream_t st) {
+ms_status vmf_alloc(VmfWork* w, int64_t N, int32_t M, int32_t T, bool tc, bool adjoint, cudaStream_t st) {
     w->tc = tc;
     w->sp = vsplit(M, N, vmf_slots(k_vmf_fwd_partial, kFT), kFSeeds);
     w->spa = vsplit(M, N, vmf_slots(k_vmf_bwd_seeds, kAT), kASeeds);
     const size_t pf = (size_t)w->sp.tiles * w->sp.chunks * kFSeeds, pa = (size_t)w->spa.tiles * w->spa.chunks * kASeeds;
     const size_t pmax = pf > pa ? pf : pa;
-    size_t tc_bytes = 0;
+    size_t tc_bytes = 0, adj_bytes = 0;
+    w->sms = 1;
     if (tc) {
-        int dev = 0, sms = 1;
+        int dev = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        w->plan = vmf_tc_plan(M, N, sms);
+        cudaDeviceGetAttribute(&w->sms, cudaDevAttrMultiProcessorCount, dev);
+        w->plan = vmf_tc_plan(M, N, w->sms);
         tc_bytes = vmf_tc_pk_bytes(N) + (size_t)w->plan.items * 128 * kVD * sizeof(float) + 3 * 256;
+        if (adjoint) adj_bytes = vmf_adj_bytes(M, N, w->sms) + 256;
     }
     const size_t bytes = pmax * kVD * sizeof(float) + (size_t)(T + 1) * M * kVD * sizeof(float) +
                          (size_t)(T > 0 ? T : 1) * M * sizeof(float) + 2 * (size_t)M * kVD * sizeof(float) + 4 * 256 +
-                         tc_bytes;
+                         tc_bytes + adj_bytes;
     char* b = nullptr;
     MS_CUDA(scratch_malloc_async((void**)&b, bytes, st));
     auto take = [&](size_t n) {
@@ -356,10 +362,12 @@ ms_status vmf_alloc(VmfWork* w, int64_t N, int32_t M, int32_t T, bool tc, cudaSt
     w->Pk = nullptr;
     w->tc_partial = nullptr;
     w->status = nullptr;
+    w->adj_ws = nullptr;
     if (tc) {
         w->Pk = take(vmf_tc_pk_bytes(N));
         w->tc_partial = take((size_t)w->plan.items * 128 * kVD * sizeof(float));
         w->status = (int*)take(sizeof(int));
+        if (adjoint) w->adj_ws = take(adj_bytes - 256);
     }
     return MS_OK;
 }
@@ -409,7 +417,7 @@ extern "C" ms_status ms_vmf_forward_ex(const float* d_P, int64_t N, const float*
     if (precision != MS_FP32 && precision != MS_BF16) return set_error(MS_ERR_INVALID_ARG, "unknown precision");
     cudaStream_t st = (cudaStream_t)stream;
     VmfWork w;
-    s = vmf_alloc(&w, N, M, T, precision == MS_BF16, st);
+    s = vmf_alloc(&w, N, M, T, precision == MS_BF16, false, st);
     if (s != MS_OK) return s;
     char* base = (char*)w.partial;
     s = vmf_forward_steps(d_P, N, d_X0, M, (float)kappa, T, &w, st);
@@ -429,11 +437,14 @@ extern "C" ms_status ms_vmf_backward_ex(const float* d_P, int64_t N, const float
     if (precision != MS_FP32 && precision != MS_BF16) return set_error(MS_ERR_INVALID_ARG, "unknown precision");
     cudaStream_t st = (cudaStream_t)stream;
     VmfWork w;
-    s = vmf_alloc(&w, N, M, T, precision == MS_BF16, st);
+    s = vmf_alloc(&w, N, M, T, precision == MS_BF16, true, st);
     if (s != MS_OK) return s;
     char* base = (char*)w.partial;
     const float kf = (float)kappa;
     s = vmf_forward_steps(d_P, N, d_X0, M, kf, T, &w, st);
+    // BF16 form: the reverse passes on the tensor cores, over the split
+    // pixel rows the forward steps packed
+    if (s == MS_OK && w.tc) s = vmf_adj_prepare(w.Pk, N, M, w.sms, w.adj_ws, &w.adj);
     if (s == MS_OK) s = cuda_check(cudaMemsetAsync(d_dP, 0, sizeof(float) * (size_t)N * kVD, st), "memset dP");
     if (s == MS_OK)
         s = cuda_check(cudaMemcpyAsync(w.g, d_GT, sizeof(float) * (size_t)M * kVD, cudaMemcpyDeviceToDevice, st),
@@ -445,6 +456,10 @@ extern "C" ms_status ms_vmf_backward_ex(const float* d_P, int64_t N, const float
         const float* Xn = w.iters + (size_t)(t + 1) * M * kVD;
         k_vmf_gy<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(w.g, Xn, w.ynorm + (size_t)t * M, M, w.gy);
         if ((s = cuda_check(cudaGetLastError(), "k_vmf_gy")) != MS_OK) break;
+        if (w.tc) {
+            s = vmf_adj_step(&w.adj, Xt, w.gy, kf, w.status, w.g, d_dP, st);
+            continue;
+        }
         k_vmf_bwd_pixels<<<(unsigned)((N + kBT * kBP - 1) / (kBT * kBP)), kBT, 0, st>>>(d_P, N, Xt, w.gy, M, kf,
                                                                                     d_dP);
         if ((s = cuda_check(cudaGetLastError(), "k_vmf_bwd_pixels")) != MS_OK) break;
@@ -456,6 +471,12 @@ extern "C" ms_status ms_vmf_backward_ex(const float* d_P, int64_t N, const float
     if (s == MS_OK)
         s = cuda_check(cudaMemcpyAsync(d_dX0, w.g, sizeof(float) * (size_t)M * kVD, cudaMemcpyDeviceToDevice, st),
                        "copy dX0");
+    if (s == MS_OK && w.tc && T > 0) {  // a bounded wait in the tensor-core passes may have given up
+        int h_status = 0;
+        s = cuda_check(cudaMemcpyAsync(&h_status, w.status, sizeof(int), cudaMemcpyDeviceToHost, st), "read status");
+        if (s == MS_OK) s = cuda_check(cudaStreamSynchronize(st), "synchronise");
+        if (s == MS_OK && h_status) s = set_error(MS_ERR_TIMEOUT, "a bounded device wait in k_vmf_adj_tc gave up");
+    }
     cudaFreeAsync(base, st);
     return s;
 }

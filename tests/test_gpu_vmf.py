@@ -3,7 +3,8 @@ the FP64 autograd reference (oracle/vmf_ref.py), plus the autograd.Function.
 
 Tolerances: x_T within 1e-5 (FP32 weights and sums); gradients within 1e-4
 relative L2 (FP32 recomputation of every weight in the reverse sweep). The
-BF16 form (forward steps on the tensor cores) has its own bar, derived below."""
+BF16 form (forward steps and adjoint passes on the tensor cores) has its own
+bar for x_T, derived below, and the same 1e-4 bar for gradients."""
 import numpy as np
 import pytest
 import torch
@@ -106,8 +107,12 @@ def test_vmf_deterministic(ms_lib):
 # weight is split into two BF16 terms (relative error <= 2^-16), the low term
 # against two pixel terms. Per-weight relative errors of a few 1e-6 average
 # over the window; the bar below is 5e-6 on every component of x_T (measured:
-# at most 1.8e-6, against 1.2e-7 for the FP32 form). Gradients differentiate
-# the BF16 iterates with the FP32 adjoint; they keep the 1e-4 relative bar.
+# at most 1.8e-6, against 1.2e-7 for the FP32 form). The adjoint passes run on
+# the tensor cores too: both scores of a pair (kappa log2(e) x.p and gy.p) from
+# six products of three-term splits, the weight and kappa w (gy.p) as two BF16
+# terms each against three (high term) or two (low term) data terms. Their
+# per-term relative errors (<= 2^-16) average over each sum like the
+# forward's; gradients keep the 1e-4 relative bar.
 BF16_TOL = 5e-6
 
 
@@ -147,6 +152,37 @@ def test_vmf_bf16_adjoint_matches_fp64_vjp(ms_lib):
     assert rel(dX0, rX) <= 1e-4, rel(dX0, rX)
 
 
+@pytest.mark.parametrize("N,M,T,kappa", [(3000, 37, 3, 20.0), (1000, 300, 1, 20.0), (129, 129, 2, 20.0),
+                                          (65, 1, 2, 20.0), (300, 257, 2, 50.0), (2000, 100, 2, 0.0)])
+def test_vmf_bf16_adjoint_ragged_shapes(ms_lib, N, M, T, kappa):
+    """Tensor-core adjoint on sizes that leave partial 64-column sub-tiles and
+    128-row tiles on both passes (pixels as rows, seeds as rows), one seed,
+    a single 64-pixel sub-tile, and kappa = 0 (uniform weights: the scaled seed
+    operand is zero and pass B's ds term must still vanish)."""
+    P, X0, _ = _problem(N, M, seed=7)
+    G = torch.randn(M, 16, generator=torch.Generator().manual_seed(11))
+    dP, dX0 = ms_lib.ms_vmf_backward(P.cuda(), X0.cuda(), kappa, T, G.cuda(), precision=ms_lib.MS_BF16)
+    _, rP, rX = vmf_ref.vmf_vjp(P.double(), X0.double(), kappa, T, G.double())
+    assert rel(dP, rP) <= 1e-4, rel(dP, rP)
+    if kappa == 0.0:  # uniform weights: x_T does not depend on x_0 at all
+        assert rX.abs().max().item() == 0.0 and dX0.abs().max().item() == 0.0
+    else:
+        assert rel(dX0, rX) <= 1e-4, rel(dX0, rX)
+
+
+def test_vmf_bf16_adjoint_close_to_fp32_adjoint(ms_lib):
+    """The tensor-core adjoint against the FP32 one on the same problem, row by
+    row: every pixel's and seed's gradient within 1e-4 of the FP32 form's,
+    relative to the largest row norm."""
+    P, X0, _ = _problem(8192, 256, seed=9)
+    G = torch.randn(256, 16, generator=torch.Generator().manual_seed(12))
+    a = ms_lib.ms_vmf_backward(P.cuda(), X0.cuda(), 20.0, 4, G.cuda(), precision=ms_lib.MS_BF16)
+    b = ms_lib.ms_vmf_backward(P.cuda(), X0.cuda(), 20.0, 4, G.cuda())
+    for x, y in zip(a, b):
+        scale = y.norm(dim=1).max().item()
+        assert (x - y).norm(dim=1).max().item() <= 1e-4 * scale
+
+
 def test_vmf_bf16_deterministic_and_zero_steps(ms_lib):
     P, X0, _ = _problem(4096, 200, seed=5)
     a = ms_lib.ms_vmf_forward(P.cuda(), X0.cuda(), 20.0, 4, precision=ms_lib.MS_BF16)
@@ -154,6 +190,12 @@ def test_vmf_bf16_deterministic_and_zero_steps(ms_lib):
     assert torch.equal(a, b)
     x0 = ms_lib.ms_vmf_forward(P.cuda(), X0.cuda(), 20.0, 0, precision=ms_lib.MS_BF16)
     assert torch.equal(x0.cpu(), X0)
+    G = torch.randn(200, 16, generator=torch.Generator().manual_seed(4)).cuda()
+    ga = ms_lib.ms_vmf_backward(P.cuda(), X0.cuda(), 20.0, 3, G, precision=ms_lib.MS_BF16)
+    gb = ms_lib.ms_vmf_backward(P.cuda(), X0.cuda(), 20.0, 3, G, precision=ms_lib.MS_BF16)
+    assert torch.equal(ga[0], gb[0]) and torch.equal(ga[1], gb[1])
+    g0 = ms_lib.ms_vmf_backward(P.cuda(), X0.cuda(), 20.0, 0, G, precision=ms_lib.MS_BF16)
+    assert torch.equal(g0[1], G) and not g0[0].abs().max().item()
 
 
 def test_vmf_bf16_unknown_precision_rejected(ms_lib):

@@ -217,11 +217,14 @@ struct VmfAdjPlan {
 };
 struct VmfAdjWork {
     CUtensorMap pk_rows, pk_cols;  // Pk (BF16 split pixel rows) in 128-row and 64-row boxes
-    CUtensorMap v_rows, v_cols;    // Vk: split rows of kappa log2(e) x_t
-    CUtensorMap g_rows, g_cols;    // Gk: split rows of gy
+    CUtensorMap v_rows, v_cols;    // Vk: split rows of kappa log2(e) x_t (and the -kappa log2(e) column)
+    CUtensorMap g_cols;            // Gk: split rows of gy (pass B's seed columns)
+    CUtensorMap ga_rows;           // Gak: split rows of kappa gy (pass A's seed rows)
     void* Vk;
     void* Gk;
-    float* partial;                // per item 128 rows x 16 sums
+    void* Gak;
+    float* partial_a;              // pass A: per item 128 seed rows x 16 sums
+    float* partial_b;              // pass B: per item 128 pixel rows x 16 sums, over every step
     VmfAdjPlan pa, pb;             // pass A (rows: seeds), pass B (rows: pixels)
     int32_t M, Mp;
     int64_t N;
@@ -230,9 +233,10 @@ struct VmfAdjWork {
 size_t vmf_adj_bytes(int32_t M, int64_t N, int grid);
 // Lays out the workspace ws and encodes the TMA maps; Pk as vmf_tc_prepare wrote it.
 ms_status vmf_adj_prepare(void* Pk, int64_t N, int32_t M, int grid, void* ws, VmfAdjWork* w);
-// One reverse step: g_out = dL/dx_t (overwritten) and dP += dL/dp from this
-// step, given x_t and gy_t (k_vmf_gy). A raised *status poisons g_out (NaN).
-ms_status vmf_adj_step(VmfAdjWork* w, const float* Xt, const float* GY, float kappa, int* status, float* g_out,
-                       float* dP, cudaStream_t st);
+// The whole reverse sweep over T steps on the tensor cores, from the
+// forward's iterates (iters: x_0..x_T, [T+1, M, 16]) and |y_t| ([T, M]):
+// dX0 = dL/dx_0, dP = dL/dP (overwritten). A raised *status poisons both (NaN).
+ms_status vmf_adj_backward(VmfAdjWork* w, const float* iters, const float* ynorm, int32_t T, float kappa,
+                           const float* GT, int* status, float* dP, float* dX0, cudaStream_t st);
 
 }  // namespace ms

@@ -449,17 +449,14 @@ extern "C" ms_status ms_vmf_backward_ex(const float* d_P, int64_t N, const float
     if (s == MS_OK)
         s = cuda_check(cudaMemcpyAsync(w.g, d_GT, sizeof(float) * (size_t)M * kVD, cudaMemcpyDeviceToDevice, st),
                        "copy g_T");
+    if (s == MS_OK && w.tc) s = vmf_adj_backward(&w.adj, w.iters, w.ynorm, T, kf, d_GT, w.status, d_dP, d_dX0, st);
     const unsigned items = (unsigned)(w.spa.tiles * w.spa.chunks);
     const unsigned rblocks = (unsigned)((M + 7) / 8);
-    for (int t = T - 1; t >= 0 && s == MS_OK; --t) {
+    for (int t = T - 1; t >= 0 && s == MS_OK && !w.tc; --t) {
         const float* Xt = w.iters + (size_t)t * M * kVD;
         const float* Xn = w.iters + (size_t)(t + 1) * M * kVD;
         k_vmf_gy<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(w.g, Xn, w.ynorm + (size_t)t * M, M, w.gy);
         if ((s = cuda_check(cudaGetLastError(), "k_vmf_gy")) != MS_OK) break;
-        if (w.tc) {
-            s = vmf_adj_step(&w.adj, Xt, w.gy, kf, w.status, w.g, d_dP, st);
-            continue;
-        }
         k_vmf_bwd_pixels<<<(unsigned)((N + kBT * kBP - 1) / (kBT * kBP)), kBT, 0, st>>>(d_P, N, Xt, w.gy, M, kf,
                                                                                     d_dP);
         if ((s = cuda_check(cudaGetLastError(), "k_vmf_bwd_pixels")) != MS_OK) break;
@@ -468,7 +465,7 @@ extern "C" ms_status ms_vmf_backward_ex(const float* d_P, int64_t N, const float
         k_vmf_bwd_reduce<<<rblocks, 256, 0, st>>>(w.partial, w.spa, M, w.g);
         s = cuda_check(cudaGetLastError(), "k_vmf_bwd_reduce");
     }
-    if (s == MS_OK)
+    if (s == MS_OK && !w.tc)
         s = cuda_check(cudaMemcpyAsync(d_dX0, w.g, sizeof(float) * (size_t)M * kVD, cudaMemcpyDeviceToDevice, st),
                        "copy dX0");
     if (s == MS_OK && w.tc && T > 0) {  // a bounded wait in the tensor-core passes may have given up

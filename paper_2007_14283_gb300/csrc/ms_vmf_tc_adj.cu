@@ -10,24 +10,31 @@
 //     pass B   dL/dp_i += sum_m w_mi gy_m + ds_mi x_m      rows: pixels, columns: seeds
 // Both passes are one kernel, k_vmf_adj_tc<kPassB>. A work item is a tile of
 // 128 rows against a run of 64-column sub-tiles. Per sub-tile:
-//   GEMM1  E = kappa log2(e) x.p and A = gy.p, 128 x 64 each, FP32 in TMEM.
-//          Every operand is a three-term BF16 split (v = vh + vm + vl exactly)
-//          and six products per score (hh, hm, mh, hl, mm, lh) leave out only
-//          terms below 2^-24 of |v||p|, as in the forward kernel.
-//   weights  w = 2^(E - kappa log2(e)) (one ex2.approx.ftz), and
-//          pass A: ds = kappa w a;  pass B: w and ds' = ds / (kappa log2(e))
+//   GEMM1  E = kappa log2(e) (x.p - 1) and A = gy.p (pass A: kappa gy.p),
+//          128 x 64 each, FP32 in TMEM. Every operand is a three-term BF16
+//          split (v = vh + vm + vl exactly) and six products per score (hh,
+//          hm, mh, hl, mm, lh) leave out only terms below 2^-24 of |v||p|, as
+//          in the forward kernel; -kappa log2(e) enters E as a seventh MMA, a
+//          three-term split against the pixel rows' ones column.
+//   weights  w = 2^E (one ex2.approx.ftz), and
+//          pass A: ds = w (kappa a);  pass B: w and ds' = ds / (kappa log2(e))
 //          = ln(2) w a, because pass B's seed operand is kappa log2(e) x
 //          (ds' (kappa log2(e) x) = ds x; no division, and kappa = 0 is fine).
 //          Each value becomes two BF16 terms, written over the warp's own
-//          columns of E (and A): the buffers become GEMM2's A operands.
+//          columns of E (and A): the buffers become GEMM2's A operands. The
+//          arithmetic runs on FP32 pairs (f32x2 instructions).
 //   GEMM2  pass A: Y += Dh.[Ph|Pm|Pl] + Dl.[Ph|Pm]            (8 MMAs)
 //          pass B: Y += Wh.[Gh|Gm|Gl] + Wl.[Gh|Gm]
 //                     + Dh'.[Vh|Vm|Vl] + Dl'.[Vh|Vm]          (16 MMAs)
 //          with the column tile itself (MN-major) as the B operand; the low
 //          weight terms are 2^-8 of the sum and need two data terms.
-// Per item the epilogue writes Y's FP32 sums (h + m + l) to a partial buffer
-// and k_vmf_adj_sum adds the chunks in a fixed order, so results are
-// deterministic. No seed-by-pixel matrix leaves TMEM.
+// Per item the epilogue writes Y's FP32 sums (h + m + l) to the item's slot of
+// a partial buffer; pass B adds them to the slot instead from the second
+// reverse step on (every slot belongs to one CTA per launch and launches are
+// stream-ordered), so dL/dp is summed over the chunks once, after the last
+// step. k_vmf_adj_link adds pass A's chunks, forms the next step's gy and
+// packs that step's operands in one launch. Chunks are added in a fixed
+// order, so results are deterministic. No seed-by-pixel matrix leaves TMEM.
 //
 // Roles (608 threads, one CTA per SM):
 //   warps 0-15  weights: four per TMEM lane quadrant, 16 columns of each
@@ -92,15 +99,40 @@ __device__ __forceinline__ bool adj_wait(uint64_t* bar, uint32_t parity, volatil
     return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort));
 }
 
-// Two BF16 terms of 16 values, packed pairwise: hi[i] = RN(v), lo = RN(v - hi).
-__device__ __forceinline__ void split2(const float (&v)[16], uint32_t (&hi)[8], uint32_t (&lo)[8]) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const uint32_t hp = pack_bf16(v[2 * i], v[2 * i + 1]);
-        hi[i] = hp;
-        lo[i] = pack_bf16(v[2 * i] - __uint_as_float(hp << 16), v[2 * i + 1] - __uint_as_float(hp & 0xFFFF0000u));
-    }
+// Elementwise products and differences of FP32 pairs, one instruction each.
+__device__ __forceinline__ void mul2(float& r0, float& r1, float a0, float a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 ra, rb, rr;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rr, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rr;\n\t}"
+        : "=f"(r0), "=f"(r1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
 }
+__device__ __forceinline__ void sub2(float& r0, float& r1, float a0, float a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 ra, rb, rr;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rr, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rr;\n\t}"
+        : "=f"(r0), "=f"(r1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
+// Two BF16 terms of a pair, packed: hi = RN(v), lo = RN(v - hi).
+__device__ __forceinline__ void split2_pair(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+    hi = pack_bf16(v0, v1);
+    float r0, r1;
+    sub2(r0, r1, v0, v1, __uint_as_float(hi << 16), __uint_as_float(hi & 0xFFFF0000u));
+    lo = pack_bf16(r0, r1);
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+    uint16_t r;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float bf16_value(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
 
 // Six BF16 products of three-term splits into D (a, b: K-major descriptors of
 // the [h | m | l] operand rows; +2 moves one 16-element K step).
@@ -113,15 +145,17 @@ __device__ __forceinline__ void six_products(uint32_t d, uint64_t a, uint64_t b,
     mma_bf16_warp(d, a + 4, b, id, 1);      // l . h
 }
 
-// partial[item][r][k] = the item's sum for row 128 t + r (pass A: dL/dx of a
-// seed over a pixel chunk; pass B: dL/dp of a pixel over a seed chunk).
-// Row maps: pass A rmap0 = Vk, rmap1 = Gk; pass B rmap0 = Pk. Column maps
-// (64-row boxes): pass A cmap0 = Pk; pass B cmap0 = Vk, cmap1 = Gk.
+// partial[item][r][k] (+)= the item's sum for row 128 t + r (pass A: dL/dx of
+// a seed over a pixel chunk; pass B: dL/dp of a pixel over a seed chunk; `+=`
+// when accumulate is set). Row maps: pass A rmap0 = Vk, rmap1 = Gak (kappa gy);
+// pass B rmap0 = Pk. Column maps (64-row boxes): pass A cmap0 = Pk; pass B
+// cmap0 = Vk, cmap1 = Gk. Vk rows hold -kappa log2(e) as a split in their
+// fourth 16-element slot, Pk rows three ones there.
 template <bool kPassB>
 __global__ void __launch_bounds__(kAdjThreads, 1)
 k_vmf_adj_tc(const __grid_constant__ CUtensorMap rmap0, const __grid_constant__ CUtensorMap rmap1,
-             const __grid_constant__ CUtensorMap cmap0, const __grid_constant__ CUtensorMap cmap1, float k2,
-             float kappa, AdjMap map, float* __restrict__ partial, int* status) {
+             const __grid_constant__ CUtensorMap cmap0, const __grid_constant__ CUtensorMap cmap1, AdjMap map,
+             float* __restrict__ partial, int accumulate, int* status) {
     constexpr int kRowBytes = kPassB ? kAdjTile : 2 * kAdjTile;
     constexpr int kStageBytes = kPassB ? 2 * kAdjSub : kAdjSub;
     extern __shared__ uint8_t smem_raw[];
@@ -235,7 +269,8 @@ k_vmf_adj_tc(const __grid_constant__ CUtensorMap rmap0, const __grid_constant__ 
                 const uint64_t b0 = dS + (uint64_t)s * kT;          // pass A: P; pass B: V
                 const uint64_t b1 = kPassB ? b0 + kH : b0;          // pass B: G
                 six_products(tE, a0, b0, id1);                      // E = kappa log2(e) x . p
-                six_products(tA, a1, b1, id1);                      // A = gy . p
+                mma_bf16_warp(tE, a0 + 6, b0 + 6, id1, 1);          //   - kappa log2(e) (split . ones)
+                six_products(tA, a1, b1, id1);                      // A = gy . p (pass A: kappa gy . p)
                 mma_commit_warp(&s_full[b]);
             }
             if (!ok) break;
@@ -311,24 +346,26 @@ k_vmf_adj_tc(const __grid_constant__ CUtensorMap rmap0, const __grid_constant__ 
                 tmem_ld16(tE, e);
                 tmem_ld16(tA, a);
                 tmem_ld_wait();
-                float w[16], d[16];
+                uint32_t wh[8], wl[8], dh[8], dl[8];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    w[j] = ex2_ftz(__uint_as_float(e[j]) - k2);
-                    d[j] = (kPassB ? kLn2 : kappa) * w[j] * __uint_as_float(a[j]);
+                for (int i = 0; i < 8; ++i) {
+                    const float w0 = ex2_ftz(__uint_as_float(e[2 * i])), w1 = ex2_ftz(__uint_as_float(e[2 * i + 1]));
+                    float d0, d1;
+                    mul2(d0, d1, w0, w1, __uint_as_float(a[2 * i]), __uint_as_float(a[2 * i + 1]));
+                    if constexpr (kPassB) {
+                        mul2(d0, d1, d0, d1, kLn2, kLn2);
+                        split2_pair(w0, w1, wh[i], wl[i]);
+                    }
+                    split2_pair(d0, d1, dh[i], dl[i]);
                 }
-                uint32_t hi[8], lo[8];
                 if constexpr (kPassB) {
-                    split2(w, hi, lo);
-                    tmem_st8(tE, hi);
-                    tmem_st8(tE + 8, lo);
-                    split2(d, hi, lo);
-                    tmem_st8(tA, hi);
-                    tmem_st8(tA + 8, lo);
+                    tmem_st8(tE, wh);
+                    tmem_st8(tE + 8, wl);
+                    tmem_st8(tA, dh);
+                    tmem_st8(tA + 8, dl);
                 } else {
-                    split2(d, hi, lo);
-                    tmem_st8(tE, hi);
-                    tmem_st8(tE + 8, lo);
+                    tmem_st8(tE, dh);
+                    tmem_st8(tE + 8, dl);
                 }
                 tmem_st_wait();
                 tc_fence_before();
@@ -355,6 +392,10 @@ k_vmf_adj_tc(const __grid_constant__ CUtensorMap rmap0, const __grid_constant__ 
                     o.y = (__uint_as_float(yh[k + 1]) + __uint_as_float(ym[k + 1])) + __uint_as_float(yl[k + 1]);
                     o.z = (__uint_as_float(yh[k + 2]) + __uint_as_float(ym[k + 2])) + __uint_as_float(yl[k + 2]);
                     o.w = (__uint_as_float(yh[k + 3]) + __uint_as_float(ym[k + 3])) + __uint_as_float(yl[k + 3]);
+                    if (accumulate) {
+                        const float4 p = *reinterpret_cast<const float4*>(dst + k);
+                        o.x += p.x; o.y += p.y; o.z += p.z; o.w += p.w;
+                    }
                     *reinterpret_cast<float4*>(dst + k) = o;
                 }
             }
@@ -391,21 +432,70 @@ __global__ void k_vmf_adj_sum(const float* __restrict__ partial, int64_t rows, i
     *o = accumulate ? *o + y : y;
 }
 
-// Split rows of kappa log2(e) x (Vk) and of gy (Gk) for rows [0, rows_pad);
-// rows >= M are zero. [vh | vm | vl | 0]: v = vh + vm + vl exactly.
-__global__ void k_vmf_adj_pack(const float* __restrict__ X, const float* __restrict__ GY, int M, int rows_pad, float k2,
-                               uint4* __restrict__ Vk, uint4* __restrict__ Gk) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows_pad) return;
-    if (i < M) {
-        float v[16];
+// The link between two reverse steps, 16 threads per row (one per
+// component) over the Mp padded rows, for the gradient g = dL/dx_s:
+//   g = pass A's chunk sums for row m, added in chunk order (or g_in, the
+//       upstream gradient, before the first step);
+//   s = 0 (x_prev == nullptr): g_out = g, i.e. dL/dx_0;
+//   else gy = (g - x_s (x_s . g)) / |y_(s-1)| and the operands of step s - 1:
+//       Vk = split(kappa log2(e) x_(s-1)) with -kappa log2(e) split into its
+//       fourth slot, Gk = split(gy), Gak = split(kappa gy).
+// A split row is [h | m | l | slot 4] (16 BF16 values each), v = h + m + l
+// exactly; rows >= M are zero (and carry the constant). A raised status
+// poisons g (NaN).
+__global__ void __launch_bounds__(256)
+k_vmf_adj_link(const float* __restrict__ partial, int chunks, const float* __restrict__ g_in,
+               const float* __restrict__ x_s, const float* __restrict__ x_prev, const float* __restrict__ yn_prev,
+               int M, int Mp, float k2, float kappa, const int* __restrict__ status, float* __restrict__ g_out,
+               uint16_t* __restrict__ Vk, uint16_t* __restrict__ Gk, uint16_t* __restrict__ Gak) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = (int)(gid >> 4), k = (int)(gid & 15);
+    if (m >= Mp) return;  // never splits a row: Mp is a multiple of 128
+    const bool live = m < M;
+    float g = 0.f;
+    if (live) {
+        if (partial) {
+            const int t = m / 128, r = m % 128;
+            const float* src = partial + ((int64_t)t * chunks * 128 + r) * 16 + k;
+            for (int ch0 = 0; ch0 < chunks; ch0 += 8) {  // eight loads in flight, added in chunk order
+                float v[8];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] = k2 * X[(int64_t)i * 16 + k];
-        pack_split_row(v, Vk + (int64_t)i * 8, false);
-        pack_split_row(GY + (int64_t)i * 16, Gk + (int64_t)i * 8, false);
-    } else {
-        pack_split_row(nullptr, Vk + (int64_t)i * 8, false);
-        pack_split_row(nullptr, Gk + (int64_t)i * 8, false);
+                for (int j = 0; j < 8; ++j) v[j] = ch0 + j < chunks ? src[(int64_t)(ch0 + j) * 128 * 16] : 0.f;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) g += v[j];
+            }
+            if (*status) g = __int_as_float(0x7fc00000);
+        } else {
+            g = g_in[(int64_t)m * 16 + k];
+        }
+    }
+    if (!x_prev) {
+        if (live) g_out[(int64_t)m * 16 + k] = g;
+        return;
+    }
+    const float xs = live ? x_s[(int64_t)m * 16 + k] : 0.f;
+    float xg = xs * g;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) xg += __shfl_xor_sync(0xffffffffu, xg, o, 16);
+    const float gy = live ? (g - xs * xg) * (1.f / yn_prev[m]) : 0.f;
+    const float v = live ? k2 * x_prev[(int64_t)m * 16 + k] : 0.f;
+    const float c_hi = bf16_value(bf16_bits(k2));
+    const float c_mid = bf16_value(bf16_bits(k2 - c_hi));
+    const float c_lo = (k2 - c_hi) - c_mid;
+    const float c_k = k == 0 ? -c_hi : k == 1 ? -c_mid : k == 2 ? -c_lo : 0.f;
+    const float vals[3] = {v, gy, kappa * gy};
+    uint16_t* rows[3] = {Vk, Gk, Gak};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float x = vals[q];
+        const uint16_t h = bf16_bits(x);
+        const uint16_t mi = bf16_bits(x - bf16_value(h));
+        const uint16_t l = bf16_bits((x - bf16_value(h)) - bf16_value(mi));
+        uint16_t* row = rows[q] + (int64_t)m * 64;
+        row[k] = h;
+        row[16 + k] = mi;
+        row[32 + k] = l;
+        row[48 + k] = q == 0 ? bf16_bits(c_k) : (uint16_t)0;
     }
 }
 
@@ -463,8 +553,8 @@ size_t vmf_adj_bytes(int32_t M, int64_t N, int grid) {
     const int64_t n_pad = (N + 127) / 128 * 128;
     const VmfAdjPlan pa = adj_plan(Mp / 128, (int)((N + 63) / 64), grid);
     const VmfAdjPlan pb = adj_plan((int)(n_pad / 128), (M + 63) / 64, grid);
-    const int items = pa.items > pb.items ? pa.items : pb.items;
-    return 2 * align256((size_t)Mp * 128) + align256((size_t)items * 128 * 16 * sizeof(float));
+    return 3 * align256((size_t)Mp * 128) + align256((size_t)pa.items * 128 * 16 * sizeof(float)) +
+           align256((size_t)pb.items * 128 * 16 * sizeof(float));
 }
 
 ms_status vmf_adj_prepare(void* Pk, int64_t N, int32_t M, int grid, void* ws, VmfAdjWork* w) {
@@ -485,45 +575,62 @@ ms_status vmf_adj_prepare(void* Pk, int64_t N, int32_t M, int grid, void* ws, Vm
     b += align256((size_t)w->Mp * 128);
     w->Gk = b;
     b += align256((size_t)w->Mp * 128);
-    w->partial = (float*)b;
+    w->Gak = b;
+    b += align256((size_t)w->Mp * 128);
+    w->partial_a = (float*)b;
+    b += align256((size_t)w->pa.items * 128 * 16 * sizeof(float));
+    w->partial_b = (float*)b;
     ms_status s;
     if ((s = encode_rows(Pk, (int)n_pad, 128, &w->pk_rows)) != MS_OK) return s;
     if ((s = encode_rows(Pk, (int)n_pad, 64, &w->pk_cols)) != MS_OK) return s;
     if ((s = encode_rows(w->Vk, w->Mp, 128, &w->v_rows)) != MS_OK) return s;
     if ((s = encode_rows(w->Vk, w->Mp, 64, &w->v_cols)) != MS_OK) return s;
-    if ((s = encode_rows(w->Gk, w->Mp, 128, &w->g_rows)) != MS_OK) return s;
+    if ((s = encode_rows(w->Gak, w->Mp, 128, &w->ga_rows)) != MS_OK) return s;
     return encode_rows(w->Gk, w->Mp, 64, &w->g_cols);
 }
 
-ms_status vmf_adj_step(VmfAdjWork* w, const float* Xt, const float* GY, float kappa, int* status, float* g_out,
-                       float* dP, cudaStream_t st) {
+ms_status vmf_adj_backward(VmfAdjWork* w, const float* iters, const float* ynorm, int32_t T, float kappa,
+                           const float* GT, int* status, float* dP, float* dX0, cudaStream_t st) {
     const float k2 = (float)((double)kappa * 1.4426950408889634);  // kappa log2(e)
-    k_vmf_adj_pack<<<(unsigned)((w->Mp + 127) / 128), 128, 0, st>>>(Xt, GY, w->M, w->Mp, k2, (uint4*)w->Vk,
-                                                                    (uint4*)w->Gk);
-    MS_LAUNCH("k_vmf_adj_pack");
-    // pass B: dL/dp over every seed, into dP
-    AdjMap mb;
-    mb.chunks = w->pb.chunks;
-    mb.spc = w->pb.spc;
-    mb.n_sub = w->pb.n_sub;
-    mb.items = w->pb.items;
-    k_vmf_adj_tc<true><<<(unsigned)w->pb.grid, kAdjThreads, kAdjSmemBytes, st>>>(
-        w->pk_rows, w->pk_rows, w->v_cols, w->g_cols, k2, kappa, mb, w->partial, status);
-    MS_LAUNCH("k_vmf_adj_tc(pixels)");
-    k_vmf_adj_sum<<<(unsigned)((w->N * 16 + 255) / 256), 256, 0, st>>>(w->partial, w->N, w->pb.chunks, status, dP, 1);
-    MS_LAUNCH("k_vmf_adj_sum(pixels)");
-    // pass A: dL/dx_t over every pixel, into g_out
-    AdjMap ma;
+    const int64_t MD = (int64_t)w->M * 16;
+    const unsigned lblocks = (unsigned)(w->Mp * 16 / 256);
+    if (T == 0) {  // x_T = x_0: dL/dx_0 = GT, and dP stays as the caller set it
+        MS_CUDA(cudaMemcpyAsync(dX0, GT, sizeof(float) * (size_t)MD, cudaMemcpyDeviceToDevice, st));
+        return MS_OK;
+    }
+    AdjMap ma, mb;
     ma.chunks = w->pa.chunks;
     ma.spc = w->pa.spc;
     ma.n_sub = w->pa.n_sub;
     ma.items = w->pa.items;
-    k_vmf_adj_tc<false><<<(unsigned)w->pa.grid, kAdjThreads, kAdjSmemBytes, st>>>(
-        w->v_rows, w->g_rows, w->pk_cols, w->pk_cols, k2, kappa, ma, w->partial, status);
-    MS_LAUNCH("k_vmf_adj_tc(seeds)");
-    k_vmf_adj_sum<<<(unsigned)(((int64_t)w->M * 16 + 255) / 256), 256, 0, st>>>(w->partial, w->M, w->pa.chunks,
-                                                                                 status, g_out, 0);
-    MS_LAUNCH("k_vmf_adj_sum(seeds)");
+    mb.chunks = w->pb.chunks;
+    mb.spc = w->pb.spc;
+    mb.n_sub = w->pb.n_sub;
+    mb.items = w->pb.items;
+    // gy of step T-1 from the upstream gradient, and that step's operands
+    k_vmf_adj_link<<<lblocks, 256, 0, st>>>(nullptr, 0, GT, iters + (size_t)T * MD, iters + (size_t)(T - 1) * MD,
+                                          ynorm + (size_t)(T - 1) * w->M, w->M, w->Mp, k2, kappa, status, nullptr,
+                                          (uint16_t*)w->Vk, (uint16_t*)w->Gk, (uint16_t*)w->Gak);
+    MS_LAUNCH("k_vmf_adj_link");
+    for (int t = T - 1; t >= 0; --t) {
+        // pass B: dL/dp over every seed, added to the chunk slots
+        k_vmf_adj_tc<true><<<(unsigned)w->pb.grid, kAdjThreads, kAdjSmemBytes, st>>>(
+            w->pk_rows, w->pk_rows, w->v_cols, w->g_cols, mb, w->partial_b, t < T - 1 ? 1 : 0, status);
+        MS_LAUNCH("k_vmf_adj_tc(pixels)");
+        // pass A: dL/dx_t over every pixel
+        k_vmf_adj_tc<false><<<(unsigned)w->pa.grid, kAdjThreads, kAdjSmemBytes, st>>>(
+            w->v_rows, w->ga_rows, w->pk_cols, w->pk_cols, ma, w->partial_a, 0, status);
+        MS_LAUNCH("k_vmf_adj_tc(seeds)");
+        // dL/dx_t; then gy of step t-1 and its operands, or dL/dx_0
+        k_vmf_adj_link<<<lblocks, 256, 0, st>>>(
+            w->partial_a, ma.chunks, nullptr, iters + (size_t)t * MD, t > 0 ? iters + (size_t)(t - 1) * MD : nullptr,
+            t > 0 ? ynorm + (size_t)(t - 1) * w->M : nullptr, w->M, w->Mp, k2, kappa, status, dX0, (uint16_t*)w->Vk,
+            (uint16_t*)w->Gk, (uint16_t*)w->Gak);
+        MS_LAUNCH("k_vmf_adj_link");
+    }
+    k_vmf_adj_sum<<<(unsigned)((w->N * 16 + 255) / 256), 256, 0, st>>>(w->partial_b, w->N, w->pb.chunks, status, dP,
+                                                                       0);
+    MS_LAUNCH("k_vmf_adj_sum");
     return MS_OK;
 }
 

@@ -2,9 +2,10 @@
 FP64 oracle and the generators' ground truth.
 
 - Sec. 4.2 (Table 1 design): 18-d points from 10 blob clusters whose centres
-  are orthogonal or opposite, sigma = 0.01, h = 0.1; the FP32 form (d = 18 is
-  padded to 32) must keep the oracle's 10 modes in order and its labels, which
-  equal the truth up to renaming.
+  are orthogonal or opposite, sigma = 0.01, h = 0.1; the FP32 form and the
+  BF16 tensor-core form (d = 18 is padded to 32: two 16-dimensional halves)
+  must keep the oracle's 10 modes in order and its labels, which equal the
+  truth up to renaming.
 - Appendix A: discs with identical, mutually orthogonal embeddings overlapping
   by a growing share of a diameter, P = 0.95 in Eq. 19: one mode per disc and
   the truth's labels at every overlap.
@@ -31,11 +32,12 @@ def _gpu(ms, emb, mask=None, **cfg):
     return res.labels.cpu().numpy(), res.modes.cpu().numpy(), res.stats
 
 
-@pytest.mark.parametrize("n", [1000, 5000])
-def test_table1_blobs_18d_equal_oracle_and_truth(ms_lib, n):
+@pytest.mark.parametrize("bf16", [False, True])
+@pytest.mark.parametrize("n", [1000, 5000, 20000])
+def test_table1_blobs_18d_equal_oracle_and_truth(ms_lib, n, bf16):
     emb, truth = synth.orthogonal_blobs(seed=n, n=n, d=18, K=10, sigma=0.01)
     ref = oracle.run(emb)
-    labels, modes, st = _gpu(ms_lib, emb, precision=ms_lib.MS_FP32)
+    labels, modes, st = _gpu(ms_lib, emb, precision=ms_lib.MS_BF16 if bf16 else ms_lib.MS_FP32)
     assert modes.shape[0] == ref.modes.shape[0] == 10
     labels_equal_oracle(ref.labels, ref.label_margin, labels, ref.modes, modes)
     assert matched_agreement(truth, labels) == 1.0

@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--cpu-seeds", type=int, default=8192, help="seeds in the oracle's sampled run")
     ap.add_argument("--cpu-runs", type=int, default=3,
                     help="--cpu full: also the median of this many sampled runs and a one-core run (0: none)")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-vmf", action="store_true", help="skip the smooth-kernel (vMF) forward/adjoint leg")
     ap.add_argument("--video-frames", type=int, default=16,
                     help="frames of the video-form leg (drifting 512x512 sequence; 0 skips it)")
@@ -804,15 +804,18 @@ def e2e_leg(args, runner, ws):
     torch.cuda.synchronize()
     barrier(ws)
     t0 = time.perf_counter()
+    walls = []
     for _ in range(args.e2e_steps):
+        w0 = time.perf_counter()
         one()
+        walls.append(1e3 * (time.perf_counter() - w0))
     torch.cuda.synchronize()
     t = reduce_over_ranks(time.perf_counter() - t0, ws, "max")
     value = reduce_over_ranks(args.e2e_steps * len(frames), ws, "sum") / t
     assert torch.equal(h_labels[0], runner.labels[0].cpu()), "host-buffer run disagrees with the device run"
     api = "ms_batch_run_host" if runner.batched else "ms_run_host"
     return {"value": value, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "api": api, "steps": args.e2e_steps}
+            "api": api, "steps": args.e2e_steps, "step_wall_ms": walls}
 
 
 def run_ours(args, rank, ws, local):

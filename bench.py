@@ -803,6 +803,8 @@ def e2e_leg(args, runner, ws):
     one()
     torch.cuda.synchronize()
     barrier(ws)
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
     t0 = time.perf_counter()
     walls = []
     for _ in range(args.e2e_steps):
@@ -811,11 +813,21 @@ def e2e_leg(args, runner, ws):
         walls.append(1e3 * (time.perf_counter() - w0))
     torch.cuda.synchronize()
     t = reduce_over_ranks(time.perf_counter() - t0, ws, "max")
+    # one device-resident step right after, on the same clock state: the
+    # difference to the host-buffer steps is the copies' share
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    ev0.record(stream)
+    runner.step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
     value = reduce_over_ranks(args.e2e_steps * len(frames), ws, "sum") / t
     assert torch.equal(h_labels[0], runner.labels[0].cpu()), "host-buffer run disagrees with the device run"
     api = "ms_batch_run_host" if runner.batched else "ms_run_host"
     return {"value": value, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "api": api, "steps": args.e2e_steps, "step_wall_ms": walls}
+            "api": api, "steps": args.e2e_steps, "step_wall_ms": walls,
+            "device_step_ms_after": ev0.elapsed_time(ev1), "clocks": clk}
 
 
 def run_ours(args, rank, ws, local):

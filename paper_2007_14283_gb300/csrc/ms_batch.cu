@@ -55,6 +55,8 @@ struct ms_batch {
     int32_t* cand;
     int32_t* cand_rank;
     int32_t* rank_cand;
+    float* Xr;                // candidates' seed positions in rank order (merge)
+    uint8_t* removed_r;       // candidates removed by a mode of an earlier round, in rank order
     uint8_t* cand_state;
     int32_t* conf_deg;
     int32_t* conf;
@@ -584,7 +586,8 @@ __global__ void k_b_blocks(const BFrame* __restrict__ frames, const BState* __re
 // undecided candidates and empty conflict lists.
 __global__ void k_b_merge_zero(const BFrame* __restrict__ frames, const BState* __restrict__ states, int B,
                                const int32_t* __restrict__ off, int32_t* __restrict__ cand_rank,
-                               uint8_t* __restrict__ cand_state, int32_t* __restrict__ conf_deg) {
+                               uint8_t* __restrict__ cand_state, int32_t* __restrict__ conf_deg,
+                               uint8_t* __restrict__ removed_r) {
     for (int bb = blockIdx.x; bb < off[B]; bb += gridDim.x) {
         const int f = locate(off, B, bb);
         const int a = (bb - off[f]) * kMT + threadIdx.x;
@@ -593,19 +596,29 @@ __global__ void k_b_merge_zero(const BFrame* __restrict__ frames, const BState* 
             cand_rank[i] = 0;
             cand_state[i] = kUndecided;
             conf_deg[i] = 0;
+            removed_r[i] = 0;  // rank a (ranks and candidates span the same range)
         }
     }
 }
 
+// rank_cand inverts cand_rank; each candidate's seed position is copied to
+// its rank's row of Xr, so the conflict search reads contiguous rows.
+template <int Dp>
 __global__ void k_b_rank_invert(const BFrame* __restrict__ frames, const BState* __restrict__ states, int B,
                                 const int32_t* __restrict__ off, const int32_t* __restrict__ cand_rank,
-                                int32_t* __restrict__ rank_cand) {
+                                const int32_t* __restrict__ cand, const float* __restrict__ X,
+                                int32_t* __restrict__ rank_cand, float* __restrict__ Xr) {
     for (int bb = blockIdx.x; bb < off[B]; bb += gridDim.x) {
         const int f = locate(off, B, bb);
         const int a = (bb - off[f]) * kMT + threadIdx.x;
         if (a < states[f].dc.n_cand) {
             const int64_t base = frames[f].pix0;
-            rank_cand[base + cand_rank[base + a]] = a;
+            const int r = cand_rank[base + a];
+            rank_cand[base + r] = a;
+            const float4* src = reinterpret_cast<const float4*>(X + (int64_t)cand[base + a] * Dp);
+            float4* dst = reinterpret_cast<float4*>(Xr + (base + r) * Dp);
+#pragma unroll
+            for (int q = 0; q < Dp / 4; ++q) dst[q] = src[q];
         }
     }
 }
@@ -669,7 +682,8 @@ template <int Dp>
 __global__ void __launch_bounds__(kMT)
 k_b_merge_old(const BFrame* __restrict__ frames, const BState* __restrict__ states, int B,
               const int32_t* __restrict__ off, const float* __restrict__ X, const int32_t* __restrict__ cand,
-              const float* __restrict__ modes, float thr_f, double thr, uint8_t* __restrict__ cand_state) {
+              const float* __restrict__ modes, float thr_f, double thr, uint8_t* __restrict__ cand_state,
+              const int32_t* __restrict__ cand_rank, uint8_t* __restrict__ removed_r) {
     __shared__ __align__(16) float tile[kVT * Dp];
     const int S = off[B + 1];
     for (int bb = blockIdx.x; bb < off[B]; bb += gridDim.x) {
@@ -695,7 +709,10 @@ k_b_merge_old(const BFrame* __restrict__ frames, const BState* __restrict__ stat
                         break;
                     }
         }
-        if (a < k && removed) cand_state[base + a] = kRemoved;
+        if (a < k && removed) {
+            cand_state[base + a] = kRemoved;
+            removed_r[base + cand_rank[base + a]] = 1;
+        }
         __syncthreads();
     }
 }
@@ -703,16 +720,19 @@ k_b_merge_old(const BFrame* __restrict__ frames, const BState* __restrict__ stat
 template <int Dp>
 __global__ void __launch_bounds__(kMT)
 k_b_merge_pairs(const BFrame* __restrict__ frames, const BState* __restrict__ states, int B,
-                const int32_t* __restrict__ off, const float* __restrict__ X, const int32_t* __restrict__ cand,
-                const int32_t* __restrict__ rank_cand, const uint8_t* __restrict__ cand_state, float thr_f,
-                double thr, int32_t* __restrict__ conf_deg, int32_t* __restrict__ conf) {
+                const int32_t* __restrict__ off, const float* __restrict__ Xr, const uint8_t* __restrict__ removed_r,
+                const int32_t* __restrict__ rank_cand, float thr_f, double thr, int32_t* __restrict__ conf_deg,
+                int32_t* __restrict__ conf) {
     // Candidates are visited in rank order: thread t of a block takes rank
     // r0 + t and compares it with every higher-priority candidate (rank < its
     // own) in the block's slice of ranks, so neighbouring lanes stop at
-    // neighbouring ranks and only the k(k-1)/2 ordered pairs are tested.
+    // neighbouring ranks and only the k(k-1)/2 ordered pairs are tested. The
+    // positions come from Xr (rank order), so a tile is one contiguous block
+    // of rows, read as float4.
+    constexpr int kQ = kVT * Dp / 4;  // float4 per tile
     __shared__ __align__(16) float tile[kVT * Dp];
     __shared__ int32_t s_idx[kVT];
-    __shared__ uint8_t s_state[kVT];
+    __shared__ uint8_t s_rem[kVT];
     const int S = off[B + 1];
     for (int bb = blockIdx.x; bb < off[B]; bb += gridDim.x) {
         const int f = locate(off, B, bb);
@@ -721,29 +741,26 @@ k_b_merge_pairs(const BFrame* __restrict__ frames, const BState* __restrict__ st
         const int k = states[f].dc.n_cand;
         const int r0 = (lb / S) * kMT;
         const int r = r0 + threadIdx.x;
-        const int a = r < k ? rank_cand[base + r] : -1;
-        const bool act = a >= 0 && cand_state[base + a] == kUndecided;
+        const bool act = r < k && !removed_r[base + r];
+        const int a = act ? rank_cand[base + r] : -1;
         const int lo = (int)((int64_t)sl * k / S);
         const int hi = min((int)((int64_t)(sl + 1) * k / S), r0 + kMT - 1);
         float x[Dp];
-        if (act) ldv<Dp>(x, X + (int64_t)cand[base + a] * Dp);
+        if (act) ldv<Dp>(x, Xr + (base + r) * Dp);
         for (int t0 = lo; t0 < hi; t0 += kVT) {
             const int cnt = min(kVT, hi - t0);
             __syncthreads();
-            for (int q = threadIdx.x; q < cnt * Dp; q += kMT) {
-                const int j = q / Dp, kk = q - j * Dp;
-                tile[q] = X[(int64_t)cand[base + rank_cand[base + t0 + j]] * Dp + kk];
-            }
+            const float4* src = reinterpret_cast<const float4*>(Xr + (base + t0) * Dp);
+            for (int q = threadIdx.x; q < cnt * (Dp / 4) && q < kQ; q += kMT) reinterpret_cast<float4*>(tile)[q] = src[q];
             for (int j = threadIdx.x; j < cnt; j += kMT) {
-                const int cj = rank_cand[base + t0 + j];
-                s_idx[j] = cj;
-                s_state[j] = cand_state[base + cj];
+                s_idx[j] = rank_cand[base + t0 + j];
+                s_rem[j] = removed_r[base + t0 + j];
             }
             __syncthreads();
             if (act) {
                 const int jend = min(cnt, r - t0);
                 for (int j = 0; j < jend; ++j) {
-                    if (s_state[j] == kRemoved) continue;
+                    if (s_rem[j]) continue;
                     if (cos_at_least<Dp>(x, tile + j * Dp, thr_f, thr)) {
                         const int slot = atomicAdd(&conf_deg[base + a], 1);
                         if (slot < kMergeCap) conf[(base + a) * kMergeCap + slot] = s_idx[j];
@@ -1104,18 +1121,19 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, B, kSelDoneCands, kMT, 4 * b->num_sms, b->blk_split);
     LAUNCHED("k_b_blocks");
     k_b_merge_zero<<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_off, b->cand_rank, b->cand_state,
-                                     b->conf_deg);
+                                     b->conf_deg, b->removed_r);
     LAUNCHED("k_b_merge_zero");
     k_b_rank<<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_split, b->cand, b->support, b->seed_order,
                                b->cand_rank);
     LAUNCHED("k_b_rank");
-    k_b_rank_invert<<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_off, b->cand_rank, b->rank_cand);
+    k_b_rank_invert<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_off, b->cand_rank, b->cand, b->X,
+                                          b->rank_cand, b->Xr);
     LAUNCHED("k_b_rank_invert");
     k_b_merge_old<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_split, b->X, b->cand, b->modes, mf,
-                                        b->cfg.merge_cos, b->cand_state);
+                                        b->cfg.merge_cos, b->cand_state, b->cand_rank, b->removed_r);
     LAUNCHED("k_b_merge_old");
-    k_b_merge_pairs<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_split, b->X, b->cand, b->rank_cand,
-                                          b->cand_state, mf, b->cfg.merge_cos, b->conf_deg, b->conf);
+    k_b_merge_pairs<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_split, b->Xr, b->removed_r,
+                                          b->rank_cand, mf, b->cfg.merge_cos, b->conf_deg, b->conf);
     LAUNCHED("k_b_merge_pairs");
     for (int sw = 0; sw < 8; ++sw) {
         k_b_merge_resolve<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_off, b->X, b->cand, b->cand_rank,
@@ -1344,7 +1362,8 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
         n * Dp * 4, n * 4, n, n * Dp * 4, n * 4, n * 4, n, n * 4, n * 4, n * 4,
         n * (Dp + 1) * 8, n * Dp * 4, n * 4, n * 4, n * 4, n, n * 4, n * kMergeCap * 4,
         (size_t)B * b->nblk_max * 4 + 4, b->tc ? (size_t)b->total_pk_rows * 128 * (Dp / 16) : 0, sizeof(int32_t*) * B,
-        tcl ? (size_t)b->total_pk_rows * 128 : 0, tcl ? n * sizeof(int2) : 0, sizeof(int32_t) * (B + 1) + 16};
+        tcl ? (size_t)b->total_pk_rows * 128 : 0, tcl ? n * sizeof(int2) : 0, sizeof(int32_t) * (B + 1) + 16,
+        n * Dp * 4, n};
     const int NS = (int)(sizeof(sizes) / sizeof(sizes[0]));
     size_t offs[32], tot = 0;
     for (int i = 0; i < NS; ++i) {
@@ -1393,6 +1412,8 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
     b->lsc.fix = tcl ? (int2*)(w + offs[26]) : nullptr;
     b->lsc.off = (int32_t*)(w + offs[27]);
     b->lsc.fix_count = b->lsc.off + (B + 1);
+    b->Xr = (float*)(w + offs[28]);
+    b->removed_r = (uint8_t*)(w + offs[29]);
     ms_status s = cuda_check(cudaMallocHost((void**)&b->h_states, sizeof(BState) * B), "cudaMallocHost");
     if (s == MS_OK) s = cuda_check(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "cudaStreamCreate");
     if (s == MS_OK)

@@ -204,8 +204,8 @@ Layout plan(int64_t np, int Dp, int target_items, bool bf16) {
         ((n + 1023) / 1024 + 1) * sizeof(int32_t),  // 20 block_tmp
         sizeof(DevCounters),              // 21 dc
         bf16 ? (n + 127) / 128 * 128 * 128 * (Dp / 16) : 0,  // 22 Pk (one array per 16 dimensions)
-        bf16 && Dp == 16 ? (n + 127) / 128 * 128 * 128 : 0,  // 23 Mk (labelling on the tensor cores: d <= 16)
-        bf16 && Dp == 16 ? n * sizeof(int2) + 16 : 0,         // 24 label_fix + count
+        bf16 ? (n + 127) / 128 * 128 * 128 * (Dp / 16) : 0,  // 23 Mk (labelling on the tensor cores)
+        bf16 ? n * sizeof(int2) + 16 : 0,                     // 24 label_fix + count
     };
     size_t t = 0;
     for (int i = 0; i < 25; ++i) {
@@ -337,8 +337,8 @@ ms_status ctx_alloc(const ms_config* cfg, int64_t max_pixels, cudaStream_t strea
     ctx->block_tmp = (int32_t*)(b + L.off[20]);
     ctx->dc = (DevCounters*)(b + L.off[21]);
     ctx->Pk = cfg->precision == MS_BF16 ? (void*)(b + L.off[22]) : nullptr;
-    ctx->Mk = cfg->precision == MS_BF16 && ctx->Dp == 16 ? (void*)(b + L.off[23]) : nullptr;
-    ctx->label_fix = cfg->precision == MS_BF16 && ctx->Dp == 16 ? (int2*)(b + L.off[24]) : nullptr;
+    ctx->Mk = cfg->precision == MS_BF16 ? (void*)(b + L.off[23]) : nullptr;
+    ctx->label_fix = cfg->precision == MS_BF16 ? (int2*)(b + L.off[24]) : nullptr;
     ctx->round_log_cap = 64;
     ctx->round_log = new (std::nothrow) int64_t[ctx->round_log_cap * 4];
     if (!ctx->round_log) {

@@ -67,6 +67,7 @@ struct ms_batch {
     CUtensorMap pmap;
     CUtensorMap pmap1;        // d = 32: dimensions 16..31 (the second Pk array)
     CUtensorMap mmap;
+    CUtensorMap mmap1;        // d = 32: the modes' dimensions 16..31 (the second Mk array)
     ms::LabelTcScratch lsc;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -1146,10 +1147,11 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     k_b_merge_append<Dp><<<B, kIT, 0, s>>>(b->frames, b->states, b->X, b->cand, b->rank_cand, b->cand_state,
                                            b->modes);
     LAUNCHED("k_b_merge_append");
-    if (b->Mk) {  // BF16 form, d <= 16: the pixels against the new modes on the tensor cores
+    if (b->Mk) {  // BF16 form: the pixels against the new modes on the tensor cores
         k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, B, kSelDonePixels, 128, 0, b->blk_off);
         LAUNCHED("k_b_blocks");
-        ms_status cs = launch_cover_tc_batch(b->pmap, b->mmap, b->Mk, b->frames, b->states, B, (int)b->max_pk_rows,
+        ms_status cs = launch_cover_tc_batch(b->pmap, b->mmap, b->pmap1, b->mmap1, b->Mk, b->total_pk_rows, Dp,
+                                             b->frames, b->states, B, (int)b->max_pk_rows,
                                              b->modes, b->P32, b->pix, b->d, b->cfg.bandwidth_cos, b->covered,
                                              b->blk_off, b->lsc, b->num_sms, b->misc + 1, s);
         if (cs != MS_OK) return cs;
@@ -1201,8 +1203,9 @@ ms_status enqueue_setup(ms_batch* b, cudaStream_t s) {
 
 template <int Dp>
 ms_status enqueue_label(ms_batch* b, cudaStream_t s) {
-    if (b->Mk)  // BF16 form, d <= 16: the tensor-core kernel, same labels (exact FP64 argmax)
-        return launch_label_tc_batch(b->pmap, b->mmap, b->Mk, b->frames, b->states, b->B, (int)b->max_pk_rows,
+    if (b->Mk)  // BF16 form: the tensor-core kernel, same labels (exact FP64 argmax)
+        return launch_label_tc_batch(b->pmap, b->mmap, b->pmap1, b->mmap1, b->Mk, b->total_pk_rows, Dp, b->frames,
+                                     b->states, b->B, (int)b->max_pk_rows,
                                      b->modes, b->P32, b->pix, b->d, b->label_ptrs, b->lsc, b->num_sms, b->misc + 1,
                                      s);
     k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, b->B, kSelAllPixels, kPT, 0, b->blk_off);
@@ -1355,14 +1358,14 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
     b->max_pk_rows = (b->max_np + 127) / 128 * 128;
     b->nblk_max = (b->max_np + kIT - 1) / kIT;
     const int Dp = b->Dp;
-    const bool tcl = b->tc && Dp == 16;  // labelling on the tensor cores (d <= 16)
+    const bool tcl = b->tc;  // labelling and coverage on the tensor cores
     const size_t n = (size_t)b->total_px;
     const size_t sizes[] = {
         sizeof(BFrame) * B, sizeof(BState) * B, sizeof(int32_t) * ((B + 1) * 4 + (B + 2) * 2), 64,
         n * Dp * 4, n * 4, n, n * Dp * 4, n * 4, n * 4, n, n * 4, n * 4, n * 4,
         n * (Dp + 1) * 8, n * Dp * 4, n * 4, n * 4, n * 4, n, n * 4, n * kMergeCap * 4,
         (size_t)B * b->nblk_max * 4 + 4, b->tc ? (size_t)b->total_pk_rows * 128 * (Dp / 16) : 0, sizeof(int32_t*) * B,
-        tcl ? (size_t)b->total_pk_rows * 128 : 0, tcl ? n * sizeof(int2) : 0, sizeof(int32_t) * (B + 1) + 16,
+        tcl ? (size_t)b->total_pk_rows * 128 * (Dp / 16) : 0, tcl ? n * sizeof(int2) : 0, sizeof(int32_t) * (B + 1) + 16,
         n * Dp * 4, n};
     const int NS = (int)(sizeof(sizes) / sizeof(sizes[0]));
     size_t offs[32], tot = 0;
@@ -1430,6 +1433,9 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
         s = encode_pk_map(Dp == 32 ? (uint8_t*)b->Pk + (size_t)b->total_pk_rows * 128 : b->Pk, (int)b->total_pk_rows,
                           &b->pmap1);
     if (s == MS_OK && tcl) s = encode_pk_map(b->Mk, (int)b->total_pk_rows, &b->mmap);
+    if (s == MS_OK && tcl) b->mmap1 = b->mmap;
+    if (s == MS_OK && tcl && Dp == 32)
+        s = encode_pk_map((uint8_t*)b->Mk + (size_t)b->total_pk_rows * 128, (int)b->total_pk_rows, &b->mmap1);
     if (s == MS_OK && tcl) s = label_tc_setup();
     if (s == MS_OK) s = rebuild_graph(b);
     if (s != MS_OK) {

@@ -78,23 +78,30 @@ struct LabelTcScratch {
 };
 
 ms_status label_tc_setup();
-ms_status launch_label_tc_single(const CUtensorMap& pmap, void* Mk, int64_t n_pad, const float* modes, int K, int n,
-                                 const float* P32, const int32_t* pix, const float* emb, int d, int32_t* labels,
-                                 LabelTcScratch sc, int grid, int* status, cudaStream_t st);
+// Labelling on the tensor cores (BF16 form, Dp = 16 or 32): exact FP64-argmax
+// labels, near-ties re-decided as the FP32 form decides them. pmap1: the
+// pixels' dimensions 16-31 (Dp = 32); Mk holds the modes' split rows, for
+// Dp = 32 followed by a second array of n_pad (mk_rows) rows.
+ms_status launch_label_tc_single(const CUtensorMap& pmap, const CUtensorMap& pmap1, void* Mk, int64_t n_pad, int Dp,
+                                 const float* modes, int K, int n, const float* P32, const int32_t* pix,
+                                 const float* emb, int d, int32_t* labels, LabelTcScratch sc, int grid, int* status,
+                                 cudaStream_t st);
 // Coverage against one frame's new modes [k0, k1) on the tensor cores (BF16
-// form, d <= 16): exact decisions, the near-threshold pixels re-decided as the
-// FP32 form decides them.
-ms_status launch_cover_tc_single(const CUtensorMap& pmap, void* Mk, int64_t n_pad, const float* modes, int k0,
-                                 int k1, int n, const float* P32, const int32_t* pix, const float* emb, int d,
-                                 double c, uint8_t* covered, int* n_uncovered, LabelTcScratch sc, int grid,
-                                 int* status, cudaStream_t st);
+// form): exact decisions, the near-threshold pixels re-decided as the FP32
+// form decides them.
+ms_status launch_cover_tc_single(const CUtensorMap& pmap, const CUtensorMap& pmap1, void* Mk, int64_t n_pad, int Dp,
+                                 const float* modes, int k0, int k1, int n, const float* P32, const int32_t* pix,
+                                 const float* emb, int d, double c, uint8_t* covered, int* n_uncovered,
+                                 LabelTcScratch sc, int grid, int* status, cudaStream_t st);
 // The same for the frames of a batch whose round ended (tile_off: their pixel
 // tiles, from k_b_blocks with 128 pixels per block).
-ms_status launch_cover_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, void* Mk, const BFrame* frames,
+ms_status launch_cover_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, const CUtensorMap& pmap1,
+                                const CUtensorMap& mmap1, void* Mk, int64_t mk_rows, int Dp, const BFrame* frames,
                                 BState* states, int B, int max_pk_rows, const float* modes, const float* P32,
                                 const int32_t* pix, int d, double c, uint8_t* covered, const int32_t* tile_off,
                                 LabelTcScratch sc, int grid, int* status, cudaStream_t st);
-ms_status launch_label_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, void* Mk, const BFrame* frames,
+ms_status launch_label_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, const CUtensorMap& pmap1,
+                                const CUtensorMap& mmap1, void* Mk, int64_t mk_rows, int Dp, const BFrame* frames,
                                 const BState* states, int B, int max_pk_rows, const float* modes, const float* P32,
                                 const int32_t* pix, int d, int32_t* const* labels, LabelTcScratch sc, int grid,
                                 int* status, cudaStream_t st);

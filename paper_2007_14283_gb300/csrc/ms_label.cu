@@ -78,9 +78,9 @@ ms_status launch_label(ms_ctx* ctx, int32_t* d_labels) {
     if (ctx->Mk) {
         // BF16 form: the tensor-core kernel, same labels (exact FP64 argmax)
         LabelTcScratch sc{ctx->label_fix, (int*)(ctx->label_fix + ctx->n), nullptr};
-        const ms_status s = launch_label_tc_single(ctx->pmap, ctx->Mk, ctx->n_pad, ctx->modes, ctx->n_kept,
-                                                   (int)ctx->n, ctx->P32, ctx->pix, ctx->emb, ctx->d, d_labels, sc,
-                                                   ctx->num_sms, &ctx->dc->status, ctx->stream);
+        const ms_status s = launch_label_tc_single(ctx->pmap, ctx->pmap1, ctx->Mk, ctx->n_pad, ctx->Dp, ctx->modes,
+                                                   ctx->n_kept, (int)ctx->n, ctx->P32, ctx->pix, ctx->emb, ctx->d,
+                                                   d_labels, sc, ctx->num_sms, &ctx->dc->status, ctx->stream);
         ctx->launches += ctx->n_kept > 1 ? 3 : 2;
         return s;
     }

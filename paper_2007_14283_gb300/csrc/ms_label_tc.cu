@@ -1,23 +1,23 @@
 // Labelling, BF16 tensor-core form (the labelling step of Algorithm 2): every
 // foreground vector takes the mode of highest cosine, lowest index on ties.
 //
-// The pixel-by-mode score matrix is a GEMM with K = d = 16. A work item is one
-// tile of 128 pixels (the GEMM's M rows) against every 128-mode tile of its
-// frame (N columns); the scores live only in TMEM:
-//     S = Ph.Mh + Ph.Mm + Pm.Mh          (3 tcgen05 MMAs, FP32 accumulate)
+// The pixel-by-mode score matrix is a GEMM with K = d = 16 (or 32, as two
+// 16-dimensional halves with their own pixel and mode tiles). A work item is
+// one tile of 128 pixels (the GEMM's M rows) against every 128-mode tile of
+// its frame (N columns); the scores live only in TMEM:
+//     S = Ph.Mh + Ph.Mm + Pm.Mh          (3 tcgen05 MMAs per half, FP32 accumulate)
 // with p = Ph + Pm + Pl and m = Mh + Mm + Ml the exact BF16 splits of the FP32
-// vectors. The dropped terms are at most 3 * 2^-18 for unit vectors and the
-// tensor cores' FP32 accumulation of 48 exact products adds at most 48 * 2^-23,
-// so |S - p.m| <= kEpsTc. Sixteen warps read S from TMEM, one pixel per lane
-// and 32 mode columns per warp, and keep the best and second-best score of
-// each pixel. A pixel whose best leads its second by more than 2 * kEpsTc has
-// the exact FP64 argmax as its winner; the others (near-ties) are queued and
-// re-decided by k_label_fix exactly as the FP32 form decides them: FP32 scores
-// over all modes, then FP64 among those within 2 * kEpsF32 of the best.
+// vectors, so |S - p.m| <= LbDim<D>::kEps (the bound is derived there).
+// Sixteen warps read S from TMEM, one pixel per lane and 32 mode columns per
+// warp, and keep the best and second-best score of each pixel. A pixel whose
+// best leads its second by more than 2 * kEps has the exact FP64 argmax as its
+// winner; the others (near-ties) are queued and re-decided by k_label_fix
+// exactly as the FP32 form decides them: FP32 scores over all modes, then
+// FP64 among those within 2 * kEpsF32 of the best.
 //
 // Warp roles (576 threads, one CTA per SM): warps 0-15 read S (warp w reaches
 // TMEM lanes 32 * (w % 4) + 0..31); warp 16 issues TMA loads (the item's pixel
-// tile, double-buffered, and mode tiles into an 8-stage ring); warp 17 owns the
+// tile, double-buffered, and mode tiles into a 4- or 8-stage ring); warp 17 owns the
 // 512 TMEM columns (four S buffers of 128) and issues the MMAs from a converged
 // warp, one elected lane issuing. Waits are bounded as in the shift kernel.
 #include <cudaTypedefs.h>
@@ -35,19 +35,34 @@ constexpr int kLEpi = 16;                   // score-reading warps
 constexpr int kLWarpTma = kLEpi;
 constexpr int kLWarpMma = kLEpi + 1;
 constexpr int kLThreads = (kLEpi + 2) * 32;  // 576
-constexpr int kLStages = 8;                 // mode-tile ring
 constexpr int kLSBufs = 4;                  // S buffers, 128 TMEM columns each
 constexpr int kLTile = 128 * 128;           // bytes of a 128-row operand tile
 constexpr uint32_t kLTmemCols = 512;
-constexpr float kEpsTc = 2.5e-5f;
 
-constexpr int kLOffA = 0;                                // 2 pixel tiles
-constexpr int kLOffB = 2 * kLTile;                       // kLStages mode tiles
-constexpr int kLOffX = kLOffB + kLStages * kLTile;       // exchange: [4][128] x (b1, i1, b2)
-constexpr int kLOffBar = kLOffX + 4 * 128 * 12;
-constexpr int kLNumBars = 2 * 2 + 2 * kLStages + 2 * kLSBufs + 2;
-constexpr int kLSmemBytes = kLOffBar + kLNumBars * 8 + 16 + 1024;
-static_assert(kLSmemBytes <= 227 * 1024, "shared memory budget");
+// Layout and score bound for embedding dimension D (16, or 32 as two halves).
+// Bound of |S - p.m| for unit vectors: per component the three products leave
+// out ph.ml + pm.(mm + ml) + pl.m. Each round-to-nearest BF16 residual is at
+// most 2^-8 of the value it splits (8 significant bits), so the three terms
+// are at most 2^-16 (1 + 2^-8) |p_k||m_k| each: at most 4.64e-5 over a unit
+// pair (a search over the split's rounding cases reaches about 2 * 2^-16 =
+// 3.0e-5). The tensor cores add the 3 * D exact products in FP32 in an
+// unspecified order; with partial sums below 1.01 an addition loses at most
+// 2^-22 even if it truncates both addends and the result: 48 * 2^-22 =
+// 1.14e-5 (D = 16) or 96 * 2^-22 = 2.29e-5 (D = 32). Hence kEps.
+template <int D>
+struct LbDim {
+    static constexpr int kHalves = D / 16;
+    static constexpr int kStages = D == 16 ? 8 : 4;                        // mode-tile ring
+    static constexpr int kOffA = 0;                                        // 2 pixel tiles per half
+    static constexpr int kOffB = 2 * kHalves * kLTile;                     // kStages mode tiles per half
+    static constexpr int kOffX = kOffB + kStages * kHalves * kLTile;       // exchange: [4][128] x (b1, i1, b2)
+    static constexpr int kOffBar = kOffX + 4 * 128 * 12;
+    static constexpr int kNumBars = 2 * 2 + 2 * kStages + 2 * kLSBufs + 2;
+    static constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 16 + 1024;
+    static constexpr float kEps = D == 16 ? 6e-5f : 7e-5f;
+    static_assert(D == 16 || D == 32, "embedding dimension 16 or 32");
+    static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
+};
 
 // What an item covers.
 struct LbItem {
@@ -138,19 +153,25 @@ struct LbOut {
 // kCover = true: coverage of the OSOP stop rule against the modes [k0, K):
 // an uncovered pixel whose best score clears c by kEpsTc is covered; one
 // within kEpsTc of c is queued for the FP32 form's exact test.
-template <class Map, bool kCover>
+// pmap / mmap: the pixel and mode split rows (dimensions 0-15); pmap1 /
+// mmap1: dimensions 16-31 (D = 32 only).
+template <class Map, bool kCover, int kD>
 __global__ void __launch_bounds__(kLThreads, 1)
-k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap mmap, Map map, LbOut out,
+k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap mmap,
+           const __grid_constant__ CUtensorMap pmap1, const __grid_constant__ CUtensorMap mmap1, Map map, LbOut out,
            int* status) {
+    using L = LbDim<kD>;
+    constexpr int kHalves = L::kHalves, kLStages = L::kStages;
+    constexpr float kEpsTc = L::kEps;
     if (!map.init()) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* Ab = smem + kLOffA;
-    uint8_t* Bst = smem + kLOffB;
-    float* xb1 = (float*)(smem + kLOffX);          // [4][128]
+    uint8_t* Ab = smem + L::kOffA;
+    uint8_t* Bst = smem + L::kOffB;
+    float* xb1 = (float*)(smem + L::kOffX);        // [4][128]
     int* xi1 = (int*)(xb1 + 4 * 128);              // [4][128]
     float* xb2 = (float*)(xi1 + 4 * 128);          // [4][128]
-    uint64_t* bars = (uint64_t*)(smem + kLOffBar);
+    uint64_t* bars = (uint64_t*)(smem + L::kOffBar);
     uint64_t* a_full = bars;                       // [2]
     uint64_t* a_empty = a_full + 2;                // [2]
     uint64_t* b_full = a_empty + 2;                // [kLStages]
@@ -158,7 +179,7 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
     uint64_t* s_full = b_empty + kLStages;         // [kLSBufs]
     uint64_t* s_empty = s_full + kLSBufs;          // [kLSBufs]
     uint64_t* aux = s_empty + kLSBufs;             // [2] drain
-    uint32_t* tmem_slot = (uint32_t*)(bars + kLNumBars);
+    uint32_t* tmem_slot = (uint32_t*)(bars + L::kNumBars);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -183,6 +204,10 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
     if (warp == kLWarpTma && lane == 0) {
         tma_prefetch_desc(&pmap);
         tma_prefetch_desc(&mmap);
+        if (kHalves > 1) {
+            tma_prefetch_desc(&pmap1);
+            tma_prefetch_desc(&mmap1);
+        }
     }
     if (warp == kLWarpMma) {
         tmem_alloc(tmem_slot, kLTmemCols);
@@ -205,8 +230,10 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
             const int ab = ia & 1;
             if (ia >= 2 && !(ok = lwarp_wait(&a_empty[ab], ((ia >> 1) - 1) & 1, abort))) break;
             if (lane == 0) {
-                mbar_arrive_expect_tx(&a_full[ab], kLTile);
-                tma_load_2d(Ab + ab * kLTile, &pmap, 0, ii.pk_row0 + ii.pt * 128, &a_full[ab]);
+                mbar_arrive_expect_tx(&a_full[ab], kHalves * kLTile);
+                tma_load_2d(Ab + ab * kHalves * kLTile, &pmap, 0, ii.pk_row0 + ii.pt * 128, &a_full[ab]);
+                if (kHalves > 1)
+                    tma_load_2d(Ab + (ab * kHalves + 1) * kLTile, &pmap1, 0, ii.pk_row0 + ii.pt * 128, &a_full[ab]);
             }
             __syncwarp();
             ++ia;
@@ -214,8 +241,11 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
                 const int s = g % kLStages;
                 if (g >= kLStages && !(ok = lwarp_wait(&b_empty[s], ((g / kLStages) - 1) & 1, abort))) break;
                 if (lane == 0) {
-                    mbar_arrive_expect_tx(&b_full[s], kLTile);
-                    tma_load_2d(Bst + s * kLTile, &mmap, 0, ii.pk_row0 + ii.k0 + mt * 128, &b_full[s]);
+                    mbar_arrive_expect_tx(&b_full[s], kHalves * kLTile);
+                    tma_load_2d(Bst + s * kHalves * kLTile, &mmap, 0, ii.pk_row0 + ii.k0 + mt * 128, &b_full[s]);
+                    if (kHalves > 1)
+                        tma_load_2d(Bst + (s * kHalves + 1) * kLTile, &mmap1, 0, ii.pk_row0 + ii.k0 + mt * 128,
+                                    &b_full[s]);
                 }
                 __syncwarp();
             }
@@ -238,17 +268,21 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
             if (nmt <= 0) continue;
             const int ab = ia & 1;
             if (!(ok = lwarp_wait(&a_full[ab], (ia >> 1) & 1, abort))) break;
-            const uint64_t a = dA + (uint64_t)ab * kT;
+            const uint64_t a = dA + (uint64_t)ab * kHalves * kT;
             for (int mt = 0; mt < nmt; ++mt, ++g) {
                 const int s = g % kLStages, b = g % kLSBufs;
                 if (!(ok = lwarp_wait(&b_full[s], (g / kLStages) & 1, abort))) break;
                 if (g >= kLSBufs && !(ok = lwarp_wait(&s_empty[b], ((g / kLSBufs) - 1) & 1, abort))) break;
                 tc_fence_after();
                 const uint32_t tS = tmem + b * 128;
-                const uint64_t bb = dB + (uint64_t)s * kT;
-                mma_bf16_warp(tS, a, bb, id, 0);          // Ph . Mh
-                mma_bf16_warp(tS, a, bb + 2, id, 1);      // Ph . Mm
-                mma_bf16_warp(tS, a + 2, bb, id, 1);      // Pm . Mh
+#pragma unroll
+                for (int hf = 0; hf < kHalves; ++hf) {
+                    const uint64_t ah = a + (uint64_t)hf * kT;
+                    const uint64_t bh = dB + (uint64_t)(s * kHalves + hf) * kT;
+                    mma_bf16_warp(tS, ah, bh, id, hf == 0 ? 0u : 1u);  // Ph . Mh
+                    mma_bf16_warp(tS, ah, bh + 2, id, 1);              // Ph . Mm
+                    mma_bf16_warp(tS, ah + 2, bh, id, 1);              // Pm . Mh
+                }
                 mma_commit_warp(&s_full[b]);
                 mma_commit_warp(&b_empty[s]);
             }
@@ -387,6 +421,7 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
 // does. FP32 scores over all modes (lanes stride the modes), the best of
 // them, then the FP64 cosine of the raw embedding for every mode within
 // 2 * kEpsF32 of that best; the largest wins, the lowest index on ties.
+template <int Dp>
 __global__ void k_label_fix(const int2* __restrict__ fix, const int* __restrict__ fix_count,
                             const float* __restrict__ P32, const float* __restrict__ modes,
                             const BFrame* __restrict__ frames, const BState* __restrict__ states,
@@ -402,20 +437,20 @@ __global__ void k_label_fix(const int2* __restrict__ fix, const int* __restrict_
         const int K = states ? states[f].dc.n_kept : K1;
         const float* emb = frames ? frames[f].emb : emb1;
         int32_t* lab = labels ? labels[f] : labels1;
-        const float* p = P32 + (base + i) * 16;
-        const float* M = modes + base * 16;
-        float pv[16];
+        const float* p = P32 + (base + i) * Dp;
+        const float* M = modes + base * Dp;
+        float pv[Dp];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) pv[k] = p[k];
+        for (int k = 0; k < Dp; ++k) pv[k] = p[k];
         float b1 = -INFINITY;
-        for (int j = lane; j < K; j += 32) b1 = fmaxf(b1, dot_seq<16>(pv, M + (int64_t)j * 16));
+        for (int j = lane; j < K; j += 32) b1 = fmaxf(b1, dot_seq<Dp>(pv, M + (int64_t)j * Dp));
         for (int o = 16; o > 0; o >>= 1) b1 = fmaxf(b1, __shfl_xor_sync(0xffffffffu, b1, o));
         const float* em = emb + (int64_t)pix[base + i] * d;
         double bc = -INFINITY;
         int best = K;
         for (int j = lane; j < K; j += 32) {
-            const float* m = M + (int64_t)j * 16;
-            if (dot_seq<16>(pv, m) < b1 - 2.f * kEpsF32) continue;
+            const float* m = M + (int64_t)j * Dp;
+            if (dot_seq<Dp>(pv, m) < b1 - 2.f * kEpsF32) continue;
             const double cs = cos64(em, m, d);
             if (cs > bc) {
                 bc = cs;
@@ -440,11 +475,12 @@ __global__ void k_label_fix(const int2* __restrict__ fix, const int* __restrict_
 // (so a mode is read from L2 once per 64 pixels instead of once per pixel).
 // Scores, thresholds and the FP64 tie-break are those of k_label_fix.
 constexpr int kFixPix = 64, kFixQ = 4, kFixTile = 128;
+template <int Dp>
 __global__ void __launch_bounds__(kFixPix * kFixQ)
 k_label_fix_tiled(const int2* __restrict__ fix, const int* __restrict__ fix_count, const float* __restrict__ P32,
                   const float* __restrict__ M, const int32_t* __restrict__ pix, const float* __restrict__ emb, int K,
                   int d, int32_t* __restrict__ labels) {
-    __shared__ __align__(16) float tile[kFixTile * 16];
+    __shared__ __align__(16) float tile[kFixTile * Dp];
     __shared__ float rb[kFixQ][kFixPix];
     __shared__ double rc[kFixQ][kFixPix];
     __shared__ int ri[kFixQ][kFixPix];
@@ -454,18 +490,18 @@ k_label_fix_tiled(const int2* __restrict__ fix, const int* __restrict__ fix_coun
         const int e = g0 + pl;
         const bool live = e < cnt;
         const int i = live ? fix[e].y : 0;
-        float pv[16];
+        float pv[Dp];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) pv[k] = live ? P32[(int64_t)i * 16 + k] : 0.f;
+        for (int k = 0; k < Dp; ++k) pv[k] = live ? P32[(int64_t)i * Dp + k] : 0.f;
         // pass 1: best FP32 score
         float b1 = -INFINITY;
         for (int j0 = 0; j0 < K; j0 += kFixTile) {
             const int nt = min(kFixTile, K - j0);
             __syncthreads();
-            for (int t = threadIdx.x; t < nt * 4; t += blockDim.x)
-                reinterpret_cast<float4*>(tile)[t] = reinterpret_cast<const float4*>(M + (int64_t)j0 * 16)[t];
+            for (int t = threadIdx.x; t < nt * (Dp / 4); t += blockDim.x)
+                reinterpret_cast<float4*>(tile)[t] = reinterpret_cast<const float4*>(M + (int64_t)j0 * Dp)[t];
             __syncthreads();
-            for (int j = q; j < nt; j += kFixQ) b1 = fmaxf(b1, dot_seq<16>(pv, tile + j * 16));
+            for (int j = q; j < nt; j += kFixQ) b1 = fmaxf(b1, dot_seq<Dp>(pv, tile + j * Dp));
         }
         rb[q][pl] = b1;
         __syncthreads();
@@ -477,13 +513,13 @@ k_label_fix_tiled(const int2* __restrict__ fix, const int* __restrict__ fix_coun
         for (int j0 = 0; j0 < K; j0 += kFixTile) {
             const int nt = min(kFixTile, K - j0);
             __syncthreads();
-            for (int t = threadIdx.x; t < nt * 4; t += blockDim.x)
-                reinterpret_cast<float4*>(tile)[t] = reinterpret_cast<const float4*>(M + (int64_t)j0 * 16)[t];
+            for (int t = threadIdx.x; t < nt * (Dp / 4); t += blockDim.x)
+                reinterpret_cast<float4*>(tile)[t] = reinterpret_cast<const float4*>(M + (int64_t)j0 * Dp)[t];
             __syncthreads();
             if (!live) continue;
             for (int j = q; j < nt; j += kFixQ) {
-                if (dot_seq<16>(pv, tile + j * 16) < b1 - 2.f * kEpsF32) continue;
-                const double cs = cos64(em, M + (int64_t)(j0 + j) * 16, d);
+                if (dot_seq<Dp>(pv, tile + j * Dp) < b1 - 2.f * kEpsF32) continue;
+                const double cs = cos64(em, M + (int64_t)(j0 + j) * Dp, d);
                 if (cs > bc) {  // j rises within a thread: '>' keeps the lowest index
                     bc = cs;
                     best = j0 + j;
@@ -504,28 +540,42 @@ k_label_fix_tiled(const int2* __restrict__ fix, const int* __restrict__ fix_coun
     }
 }
 
-// Modes as BF16 split rows at the frame's Pk row offsets (padding rows hold
-// the ones only; their columns are masked out by the score readers).
-__global__ void k_pack_modes_single(const float* __restrict__ modes, int K, int K_pad, uint4* __restrict__ Mk) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= K_pad) return;
-    pack_split_row(r < K ? modes + (int64_t)r * 16 : nullptr, Mk + (int64_t)r * 8);
+// Mode row `mode` (Dp floats, or nullptr for a padding row) as BF16 split rows
+// at row r of Mk: dimensions 0-15, and for Dp = 32 dimensions 16-31 in the
+// second array, half_rows rows further (no ones there).
+template <int Dp>
+__device__ __forceinline__ void pack_mode(const float* mode, uint4* Mk, int64_t r, int64_t half_rows) {
+    pack_split_row(mode, Mk + r * 8);
+    if (Dp == 32) pack_split_row(mode ? mode + 16 : nullptr, Mk + (half_rows + r) * 8, false);
 }
 
+// Modes as BF16 split rows at the frame's Pk row offsets (padding rows hold
+// the ones only; their columns are masked out by the score readers).
+template <int Dp>
+__global__ void k_pack_modes_single(const float* __restrict__ modes, int K, int K_pad, uint4* __restrict__ Mk,
+                                    int64_t half_rows) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= K_pad) return;
+    pack_mode<Dp>(r < K ? modes + (int64_t)r * Dp : nullptr, Mk, r, half_rows);
+}
+
+template <int Dp>
 __global__ void k_pack_modes_batch(const BFrame* __restrict__ frames, const BState* __restrict__ states,
-                                   const float* __restrict__ modes, uint4* __restrict__ Mk) {
+                                   const float* __restrict__ modes, uint4* __restrict__ Mk, int64_t half_rows) {
     const BFrame& fr = frames[blockIdx.y];
     const int K = states[blockIdx.y].dc.n_kept;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= (K + 127) / 128 * 128) return;
-    pack_split_row(r < K ? modes + (fr.pix0 + r) * 16 : nullptr, Mk + (int64_t)(fr.pk_row0 + r) * 8);
+    pack_mode<Dp>(r < K ? modes + (fr.pix0 + r) * Dp : nullptr, Mk, fr.pk_row0 + r, half_rows);
 }
 
 // Modes [k0, k1) of one frame as BF16 split rows at their Mk rows.
-__global__ void k_pack_modes_range(const float* __restrict__ modes, int k0, int k1, uint4* __restrict__ Mk) {
+template <int Dp>
+__global__ void k_pack_modes_range(const float* __restrict__ modes, int k0, int k1, uint4* __restrict__ Mk,
+                                   int64_t half_rows) {
     const int r = k0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= k1) return;
-    pack_split_row(modes + (int64_t)r * 16, Mk + (int64_t)r * 8);
+    pack_mode<Dp>(modes + (int64_t)r * Dp, Mk, r, half_rows);
 }
 
 // Coverage of the queued pixels (tensor-core score within kEpsTc of c),
@@ -533,6 +583,7 @@ __global__ void k_pack_modes_range(const float* __restrict__ modes, int k0, int 
 // the new modes; a mode covers the pixel when its FP32 score clears c by
 // kEpsF32, or is within kEpsF32 of c and the FP64 cosine of the raw embedding
 // reaches c.
+template <int Dp>
 __global__ void k_cover_fix(const int2* __restrict__ fix, const int* __restrict__ fix_count,
                             const float* __restrict__ P32, const float* __restrict__ modes, int k0, int k1,
                             const int32_t* __restrict__ pix, const float* __restrict__ emb, int d, float c_f, double c,
@@ -542,14 +593,14 @@ __global__ void k_cover_fix(const int2* __restrict__ fix, const int* __restrict_
     const int cnt = *fix_count;
     for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < cnt; e += gridDim.x * wpb) {
         const int i = fix[e].y;
-        float pv[16];
+        float pv[Dp];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) pv[k] = P32[(int64_t)i * 16 + k];
+        for (int k = 0; k < Dp; ++k) pv[k] = P32[(int64_t)i * Dp + k];
         const float* em = emb + (int64_t)pix[i] * d;
         bool cov = false;
         for (int j = k0 + lane; j < k1 && !cov; j += 32) {
-            const float* m = modes + (int64_t)j * 16;
-            const float sc = dot_seq<16>(pv, m);
+            const float* m = modes + (int64_t)j * Dp;
+            const float sc = dot_seq<Dp>(pv, m);
             cov = sc >= c_f + kEpsF32 || (sc >= c_f - kEpsF32 && cos64(em, m, d) >= c);
         }
         if (__any_sync(0xffffffffu, cov) && lane == 0) {
@@ -561,19 +612,22 @@ __global__ void k_cover_fix(const int2* __restrict__ fix, const int* __restrict_
 
 // The batch form of k_pack_modes_range: every frame whose round ended packs
 // its new modes [k0, n_kept) at its Mk rows; clears the recheck queue.
+template <int Dp>
 __global__ void k_pack_modes_new_batch(const BFrame* __restrict__ frames, const BState* __restrict__ states,
-                                       const float* __restrict__ modes, uint4* __restrict__ Mk, int* fix_count) {
+                                       const float* __restrict__ modes, uint4* __restrict__ Mk, int64_t half_rows,
+                                       int* fix_count) {
     const BFrame& fr = frames[blockIdx.y];
     const BState& st = states[blockIdx.y];
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *fix_count = 0;
     if (st.phase != kRoundDone) return;
     const int r = st.k0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= st.dc.n_kept) return;
-    pack_split_row(modes + (fr.pix0 + r) * 16, Mk + (int64_t)(fr.pk_row0 + r) * 8);
+    pack_mode<Dp>(modes + (fr.pix0 + r) * Dp, Mk, fr.pk_row0 + r, half_rows);
 }
 
 // k_cover_fix for the batch: queued (frame, foreground index) pairs, each
 // against its frame's new modes.
+template <int Dp>
 __global__ void k_cover_fix_batch(const int2* __restrict__ fix, const int* __restrict__ fix_count,
                                   const float* __restrict__ P32, const float* __restrict__ modes,
                                   const BFrame* __restrict__ frames, BState* states, const int32_t* __restrict__ pix,
@@ -587,14 +641,14 @@ __global__ void k_cover_fix_batch(const int2* __restrict__ fix, const int* __res
         const BFrame& fr = frames[f];
         const int64_t base = fr.pix0;
         const int k0 = states[f].k0, k1 = states[f].dc.n_kept;
-        float pv[16];
+        float pv[Dp];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) pv[k] = P32[(base + i) * 16 + k];
+        for (int k = 0; k < Dp; ++k) pv[k] = P32[(base + i) * Dp + k];
         const float* em = fr.emb + (int64_t)pix[base + i] * d;
         bool cov = false;
         for (int j = k0 + lane; j < k1 && !cov; j += 32) {
-            const float* m = modes + (base + j) * 16;
-            const float sc = dot_seq<16>(pv, m);
+            const float* m = modes + (base + j) * Dp;
+            const float sc = dot_seq<Dp>(pv, m);
             cov = sc >= c_f + kEpsF32 || (sc >= c_f - kEpsF32 && cos64(em, m, d) >= c);
         }
         if (__any_sync(0xffffffffu, cov) && lane == 0) {
@@ -617,103 +671,163 @@ __global__ void k_label_items(const BFrame* __restrict__ frames, int B, int32_t*
     *fix_count = 0;
 }
 
-}  // namespace
-
-ms_status label_tc_setup() {
-    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbSingle, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kLSmemBytes));
-    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbSingle, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kLSmemBytes));
-    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbBatch, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kLSmemBytes));
-    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbBatchCover, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kLSmemBytes));
+template <int D>
+ms_status label_tc_setup_dim() {
+    constexpr int smem = LbDim<D>::kSmemBytes;
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbSingle, false, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbSingle, true, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbBatch, false, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbBatchCover, true, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem));
     return MS_OK;
 }
 
-ms_status launch_cover_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, void* Mk, const BFrame* frames,
-                                BState* states, int B, int max_pk_rows, const float* modes, const float* P32,
-                                const int32_t* pix, int d, double c, uint8_t* covered, const int32_t* tile_off,
-                                LabelTcScratch sc, int grid, int* status, cudaStream_t st) {
+template <int Dp>
+ms_status cover_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, const CUtensorMap& pmap1,
+                         const CUtensorMap& mmap1, void* Mk, int64_t mk_rows, const BFrame* frames, BState* states,
+                         int B, int max_pk_rows, const float* modes, const float* P32, const int32_t* pix, int d,
+                         double c, uint8_t* covered, const int32_t* tile_off, LabelTcScratch sc, int grid, int* status,
+                         cudaStream_t st) {
     const dim3 gp((unsigned)((max_pk_rows + 255) / 256), (unsigned)B);
-    k_pack_modes_new_batch<<<gp, 256, 0, st>>>(frames, states, modes, (uint4*)Mk, sc.fix_count);
+    k_pack_modes_new_batch<Dp><<<gp, 256, 0, st>>>(frames, states, modes, (uint4*)Mk, mk_rows, sc.fix_count);
     MS_LAUNCH("k_pack_modes_new_batch");
     const float c_f = (float)c;
     LbBatchCover map{frames, states, tile_off, B, 0};
     LbOut out{nullptr, nullptr, frames, pix, sc.fix, sc.fix_count, covered, nullptr, c_f, states};
-    k_label_tc<LbBatchCover, true><<<grid, kLThreads, kLSmemBytes, st>>>(pmap, mmap, map, out, status);
+    k_label_tc<LbBatchCover, true, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(pmap, mmap, pmap1, mmap1, map,
+                                                                                       out, status);
     MS_LAUNCH("k_label_tc(cover, batch)");
-    k_cover_fix_batch<<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, P32, modes, frames, states, pix, d, c_f, c,
-                                            covered);
+    k_cover_fix_batch<Dp><<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, P32, modes, frames, states, pix, d, c_f, c,
+                                                covered);
     MS_LAUNCH("k_cover_fix_batch");
     return MS_OK;
 }
 
-ms_status launch_cover_tc_single(const CUtensorMap& pmap, void* Mk, int64_t n_pad, const float* modes, int k0,
-                                 int k1, int n, const float* P32, const int32_t* pix, const float* emb, int d,
-                                 double c, uint8_t* covered, int* n_uncovered, LabelTcScratch sc, int grid,
-                                 int* status, cudaStream_t st) {
-    if (n == 0 || k1 <= k0) return MS_OK;
+template <int Dp>
+ms_status cover_tc_single(const CUtensorMap& pmap, const CUtensorMap& pmap1, void* Mk, int64_t n_pad,
+                          const float* modes, int k0, int k1, int n, const float* P32, const int32_t* pix,
+                          const float* emb, int d, double c, uint8_t* covered, int* n_uncovered, LabelTcScratch sc,
+                          int grid, int* status, cudaStream_t st) {
     MS_CUDA(cudaMemsetAsync(sc.fix_count, 0, sizeof(int), st));
-    k_pack_modes_range<<<(k1 - k0 + 255) / 256, 256, 0, st>>>(modes, k0, k1, (uint4*)Mk);
+    k_pack_modes_range<Dp><<<(k1 - k0 + 255) / 256, 256, 0, st>>>(modes, k0, k1, (uint4*)Mk, n_pad);
     MS_LAUNCH("k_pack_modes_range");
-    CUtensorMap mmap;
+    CUtensorMap mmap, mmap1;
     ms_status s = encode_pk_map(Mk, (int)n_pad, &mmap);
     if (s != MS_OK) return s;
+    mmap1 = mmap;
+    if (Dp == 32 && (s = encode_pk_map((uint8_t*)Mk + n_pad * 128, (int)n_pad, &mmap1)) != MS_OK) return s;
     LbSingle map{n, k1};
     map.k0 = k0;
     const float c_f = (float)c;
     LbOut out{nullptr, nullptr, nullptr, pix, sc.fix, sc.fix_count, covered, n_uncovered, c_f, nullptr};
-    k_label_tc<LbSingle, true><<<grid, kLThreads, kLSmemBytes, st>>>(pmap, mmap, map, out, status);
+    k_label_tc<LbSingle, true, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(pmap, mmap, pmap1, mmap1, map, out,
+                                                                                   status);
     MS_LAUNCH("k_label_tc(cover)");
-    k_cover_fix<<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, P32, modes, k0, k1, pix, emb, d, c_f, c, covered,
-                                      n_uncovered);
+    k_cover_fix<Dp><<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, P32, modes, k0, k1, pix, emb, d, c_f, c, covered,
+                                          n_uncovered);
     MS_LAUNCH("k_cover_fix");
     return MS_OK;
 }
 
-ms_status launch_label_tc_single(const CUtensorMap& pmap, void* Mk, int64_t n_pad, const float* modes, int K, int n,
-                                 const float* P32, const int32_t* pix, const float* emb, int d, int32_t* labels,
-                                 LabelTcScratch sc, int grid, int* status, cudaStream_t st) {
-    if (n == 0) return MS_OK;
+template <int Dp>
+ms_status label_tc_single(const CUtensorMap& pmap, const CUtensorMap& pmap1, void* Mk, int64_t n_pad,
+                          const float* modes, int K, int n, const float* P32, const int32_t* pix, const float* emb,
+                          int d, int32_t* labels, LabelTcScratch sc, int grid, int* status, cudaStream_t st) {
     MS_CUDA(cudaMemsetAsync(sc.fix_count, 0, sizeof(int), st));
     if (K > 0) {
         const int K_pad = (K + 127) / 128 * 128;
-        k_pack_modes_single<<<(K_pad + 255) / 256, 256, 0, st>>>(modes, K, K_pad, (uint4*)Mk);
+        k_pack_modes_single<Dp><<<(K_pad + 255) / 256, 256, 0, st>>>(modes, K, K_pad, (uint4*)Mk, n_pad);
         MS_LAUNCH("k_pack_modes_single");
     }
-    CUtensorMap mmap;
+    CUtensorMap mmap, mmap1;
     ms_status s = encode_pk_map(Mk, (int)n_pad, &mmap);
     if (s != MS_OK) return s;
+    mmap1 = mmap;
+    if (Dp == 32 && (s = encode_pk_map((uint8_t*)Mk + n_pad * 128, (int)n_pad, &mmap1)) != MS_OK) return s;
     LbSingle map{n, K};
     LbOut out{nullptr, labels, nullptr, pix, sc.fix, sc.fix_count, nullptr, nullptr, 0.f, nullptr};
-    k_label_tc<LbSingle, false><<<grid, kLThreads, kLSmemBytes, st>>>(pmap, mmap, map, out, status);
+    k_label_tc<LbSingle, false, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(pmap, mmap, pmap1, mmap1, map,
+                                                                                    out, status);
     MS_LAUNCH("k_label_tc");
     if (K > 1) {
-        k_label_fix_tiled<<<2 * grid, kFixPix * kFixQ, 0, st>>>(sc.fix, sc.fix_count, P32, modes, pix, emb, K, d,
-                                                              labels);
+        k_label_fix_tiled<Dp><<<2 * grid, kFixPix * kFixQ, 0, st>>>(sc.fix, sc.fix_count, P32, modes, pix, emb, K, d,
+                                                                    labels);
         MS_LAUNCH("k_label_fix_tiled");
     }
     return MS_OK;
 }
 
-ms_status launch_label_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, void* Mk, const BFrame* frames,
-                                const BState* states, int B, int max_pk_rows, const float* modes, const float* P32,
-                                const int32_t* pix, int d, int32_t* const* labels, LabelTcScratch sc, int grid,
-                                int* status, cudaStream_t st) {
+template <int Dp>
+ms_status label_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, const CUtensorMap& pmap1,
+                         const CUtensorMap& mmap1, void* Mk, int64_t mk_rows, const BFrame* frames,
+                         const BState* states, int B, int max_pk_rows, const float* modes, const float* P32,
+                         const int32_t* pix, int d, int32_t* const* labels, LabelTcScratch sc, int grid, int* status,
+                         cudaStream_t st) {
     const dim3 gp((unsigned)((max_pk_rows + 255) / 256), (unsigned)B);
-    k_pack_modes_batch<<<gp, 256, 0, st>>>(frames, states, modes, (uint4*)Mk);
+    k_pack_modes_batch<Dp><<<gp, 256, 0, st>>>(frames, states, modes, (uint4*)Mk, mk_rows);
     MS_LAUNCH("k_pack_modes_batch");
     k_label_items<<<1, 32, 0, st>>>(frames, B, sc.off, sc.fix_count);
     MS_LAUNCH("k_label_items");
     LbBatch map{frames, states, sc.off, B, 0};
     LbOut out{labels, nullptr, frames, pix, sc.fix, sc.fix_count, nullptr, nullptr, 0.f, nullptr};
-    k_label_tc<LbBatch, false><<<grid, kLThreads, kLSmemBytes, st>>>(pmap, mmap, map, out, status);
+    k_label_tc<LbBatch, false, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(pmap, mmap, pmap1, mmap1, map,
+                                                                                   out, status);
     MS_LAUNCH("k_label_tc(batch)");
-    k_label_fix<<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, P32, modes, frames, states, pix, nullptr, 0, d, labels,
-                                      nullptr);
+    k_label_fix<Dp><<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, P32, modes, frames, states, pix, nullptr, 0, d, labels,
+                                          nullptr);
     MS_LAUNCH("k_label_fix(batch)");
     return MS_OK;
+}
+
+}  // namespace
+
+ms_status label_tc_setup() {
+    ms_status s = label_tc_setup_dim<16>();
+    return s == MS_OK ? label_tc_setup_dim<32>() : s;
+}
+
+ms_status launch_cover_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, const CUtensorMap& pmap1,
+                                const CUtensorMap& mmap1, void* Mk, int64_t mk_rows, int Dp, const BFrame* frames,
+                                BState* states, int B, int max_pk_rows, const float* modes, const float* P32,
+                                const int32_t* pix, int d, double c, uint8_t* covered, const int32_t* tile_off,
+                                LabelTcScratch sc, int grid, int* status, cudaStream_t st) {
+    return Dp == 32 ? cover_tc_batch<32>(pmap, mmap, pmap1, mmap1, Mk, mk_rows, frames, states, B, max_pk_rows, modes,
+                                         P32, pix, d, c, covered, tile_off, sc, grid, status, st)
+                    : cover_tc_batch<16>(pmap, mmap, pmap1, mmap1, Mk, mk_rows, frames, states, B, max_pk_rows, modes,
+                                         P32, pix, d, c, covered, tile_off, sc, grid, status, st);
+}
+
+ms_status launch_cover_tc_single(const CUtensorMap& pmap, const CUtensorMap& pmap1, void* Mk, int64_t n_pad, int Dp,
+                                 const float* modes, int k0, int k1, int n, const float* P32, const int32_t* pix,
+                                 const float* emb, int d, double c, uint8_t* covered, int* n_uncovered,
+                                 LabelTcScratch sc, int grid, int* status, cudaStream_t st) {
+    if (n == 0 || k1 <= k0) return MS_OK;
+    return Dp == 32 ? cover_tc_single<32>(pmap, pmap1, Mk, n_pad, modes, k0, k1, n, P32, pix, emb, d, c, covered,
+                                          n_uncovered, sc, grid, status, st)
+                    : cover_tc_single<16>(pmap, pmap1, Mk, n_pad, modes, k0, k1, n, P32, pix, emb, d, c, covered,
+                                          n_uncovered, sc, grid, status, st);
+}
+
+ms_status launch_label_tc_single(const CUtensorMap& pmap, const CUtensorMap& pmap1, void* Mk, int64_t n_pad, int Dp,
+                                 const float* modes, int K, int n, const float* P32, const int32_t* pix,
+                                 const float* emb, int d, int32_t* labels, LabelTcScratch sc, int grid, int* status,
+                                 cudaStream_t st) {
+    if (n == 0) return MS_OK;
+    return Dp == 32 ? label_tc_single<32>(pmap, pmap1, Mk, n_pad, modes, K, n, P32, pix, emb, d, labels, sc, grid,
+                                          status, st)
+                    : label_tc_single<16>(pmap, pmap1, Mk, n_pad, modes, K, n, P32, pix, emb, d, labels, sc, grid,
+                                          status, st);
+}
+
+ms_status launch_label_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, const CUtensorMap& pmap1,
+                                const CUtensorMap& mmap1, void* Mk, int64_t mk_rows, int Dp, const BFrame* frames,
+                                const BState* states, int B, int max_pk_rows, const float* modes, const float* P32,
+                                const int32_t* pix, int d, int32_t* const* labels, LabelTcScratch sc, int grid,
+                                int* status, cudaStream_t st) {
+    return Dp == 32 ? label_tc_batch<32>(pmap, mmap, pmap1, mmap1, Mk, mk_rows, frames, states, B, max_pk_rows, modes,
+                                         P32, pix, d, labels, sc, grid, status, st)
+                    : label_tc_batch<16>(pmap, mmap, pmap1, mmap1, Mk, mk_rows, frames, states, B, max_pk_rows, modes,
+                                         P32, pix, d, labels, sc, grid, status, st);
 }
 
 }  // namespace ms

@@ -469,9 +469,10 @@ ms_status launch_merge_append(ms_ctx* ctx, int32_t k) {
 
 ms_status launch_cover(ms_ctx* ctx, int32_t k0, int32_t k1) {
     if (k1 <= k0 || ctx->n == 0) return MS_OK;
-    if (ctx->Mk) {  // BF16 form, d <= 16: the tensor cores score the pixels against the new modes
+    if (ctx->Mk) {  // BF16 form: the tensor cores score the pixels against the new modes
         LabelTcScratch sc{ctx->label_fix, (int*)(ctx->label_fix + ctx->n), nullptr};
-        const ms_status s = launch_cover_tc_single(ctx->pmap, ctx->Mk, ctx->n_pad, ctx->modes, k0, k1, (int)ctx->n,
+        const ms_status s = launch_cover_tc_single(ctx->pmap, ctx->pmap1, ctx->Mk, ctx->n_pad, ctx->Dp, ctx->modes,
+                                                   k0, k1, (int)ctx->n,
                                                    ctx->P32, ctx->pix, ctx->emb, ctx->d, ctx->cfg.bandwidth_cos,
                                                    ctx->covered, &ctx->dc->n_uncovered, sc, ctx->num_sms,
                                                    &ctx->dc->status, ctx->stream);

@@ -2,11 +2,13 @@
 //
 // One work item = 128 seeds x a chunk of 128-pixel tiles. Per pixel tile:
 //   GEMM1  S' = Xh.Ph + Xh.Pm + Xl.Ph - c       (4 tcgen05 MMAs, FP32 in TMEM)
-//          x = Xh + Xl and p = Ph + Pm + Pl are exact BF16 splits of the FP32
-//          vectors and -c is split into three BF16 terms against a ones
-//          column, so S' = x.p - c up to the dropped terms (<= 3 * 2^-18 =
-//          1.2e-5 for unit vectors) and the tensor cores' FP32 accumulation
-//          (measured <= 6e-6 against an exact reconstruction).
+//          x ~ Xh + Xl and p = Ph + Pm + Pl are round-to-nearest BF16 splits
+//          of the FP32 vectors (p's exact) and -c is split into three BF16
+//          terms against a ones column, so S' = x.p - c up to the dropped
+//          terms (at most 3.04 * 2^-16 = 4.64e-5 for unit vectors: a BF16
+//          residual is at most 2^-8 of what it splits) and the tensor cores'
+//          FP32 accumulation (at most 51 * 2^-22 = 1.2e-5 even for an adder
+//          that truncates; measured <= 6e-6): 5.9e-5 < kBand.
 //   mask   a pair is in the window when S' >= 0 (sign bit clear). Pairs with
 //          |S'| < kBand = 2^-14 are re-decided with the same sequential FP32
 //          dot product as the FP32 form, against the pixel's exact FP32 value

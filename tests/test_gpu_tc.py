@@ -70,6 +70,22 @@ def _run(ms, emb, mask=None, **cfg):
     return res.labels.cpu().numpy(), res.modes.cpu().numpy(), res.stats
 
 
+def assert_labels_are_fp64_argmax(emb, mask, labels, modes):
+    """Every foreground label is the FP64 argmax of the raw embedding's cosine
+    over the given modes (lowest index on ties); pixels whose top two differ by
+    less than 1e-12 accept either."""
+    fg = np.ones(emb.shape[0], bool) if mask is None else mask.astype(bool)
+    E = emb[fg].astype(np.float64)
+    M = modes.astype(np.float64)
+    C = (E @ M.T) / np.linalg.norm(E, axis=1)[:, None] / np.linalg.norm(M, axis=1)[None, :]
+    best = np.argmax(C, axis=1)
+    top = np.sort(C, axis=1)[:, -2:] if C.shape[1] > 1 else np.concatenate([C, C - 1], 1)
+    clear = top[:, 1] - top[:, 0] > 1e-12
+    got = labels[fg]
+    assert np.array_equal(got[clear], best[clear]), int((got[clear] != best[clear]).sum())
+    assert np.all(C[np.arange(len(got)), got] >= top[:, 1] - 1e-12)
+
+
 def test_bf16_c1_separable_exact(ms_lib):
     f = synth.frame_c1_separable(seed=0)
     ref = oracle.run(f.emb)
@@ -135,7 +151,8 @@ def test_tile_shape_out_of_range_is_rejected(ms_lib):
 # ---------------------------------------------------------------- d = 32
 # The tensor-core form for 17 <= d <= 32: two 16-dimensional halves, each with
 # its own BF16 split operand tiles (seven GEMM1 products per tile, two Y
-# blocks in GEMM2), the same FP32 re-decision band, and FP32 labelling.
+# blocks in GEMM2), the same FP32 re-decision band; labelling and coverage
+# score both halves on the tensor cores (six products per mode tile).
 
 
 @pytest.mark.parametrize("d", [32, 18])
@@ -153,6 +170,9 @@ def test_bf16_d32_equals_fp32_form_and_oracle(ms_lib, d):
     assert mode_errors(b[1], ref.modes).max() <= 1e-5
     assert matched_agreement(ref.labels, b[0]) >= 0.999
     assert (b[0][f.mask == 0] == -1).all()
+    # the tensor-core labelling (both 16-dimensional halves for d > 16) gives
+    # the exact FP64 argmax over its own modes
+    assert_labels_are_fp64_argmax(f.emb, f.mask, b[0], b[1])
 
 
 @pytest.mark.parametrize("shape", [2, 4, 6])

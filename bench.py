@@ -830,6 +830,22 @@ def e2e_leg(args, runner, ws):
             "device_step_ms_after": ev0.elapsed_time(ev1), "clocks": clk}
 
 
+def phase_leg(runner):
+    """One untimed extra step with the phase timers on (profiling level 2):
+    where a step's time goes inside the graph, by phase (ncu does not look
+    inside conditional graph bodies). Restores the shift timers alone."""
+    import torch
+    ms = runner.ms
+    ms.ms_batch_profile(runner.batch, 2)
+    ms.ms_batch_run(runner.batch)
+    torch.cuda.synchronize()
+    out = ms.ms_batch_phase_ms(runner.batch)
+    ms.ms_batch_profile(runner.batch, 1)
+    tot = sum(out.values())
+    return {"ms": out, "share": {k: v / tot for k, v in out.items()} if tot > 0 else None,
+            "note": "one extra untimed step with one-thread global-timer kernels between the graph's phases"}
+
+
 def run_ours(args, rank, ws, local):
     import torch
 
@@ -854,6 +870,7 @@ def run_ours(args, rank, ws, local):
                          "ms_per_frame": sum(step_ms) / max(1, tot["frames"]),
                          "roofline_frac": roofline["frac"]}}
     e2e = e2e_leg(args, main, ws) if args.e2e_steps > 0 else None
+    phases = phase_leg(main) if main.batched and not args.eager else None
 
     for other in [f for f in args.compare.split(",") if f and f != args.form]:
         r = Runner(ms, other, frames[: args.compare_frames], dev)
@@ -939,7 +956,7 @@ def run_ours(args, rank, ws, local):
                            "autotune": main.tuning,
                            "fp32_rechecked_pair_fraction": tot.get("band_pairs", 0) /
                            max(1.0, float(tot["seed_iters"]) * N_FG)},
-                "roofline": roofline, "forms": forms, "smooth_kernel": vmf, "kernel_variants": kvar, "d32": d32,
+                "roofline": roofline, "batch_phases": phases, "forms": forms, "smooth_kernel": vmf, "kernel_variants": kvar, "d32": d32,
                 "video": video,
                 "parity_vs_oracle": parity,
                 "cpu_baseline": cpu,

@@ -408,7 +408,9 @@ MS_API void ms_video_destroy(ms_video* v);
  * kernels that had work, from the GPU global timer read by one-thread
  * kernels placed before and after each shift launch; includes one launch gap
  * each). ms_batch_profile(b, 1) rebuilds the graph with those timer kernels
- * (0 removes them); it synchronises the stream. ms_batch_modes copies frame f's K kept modes, float32
+ * (0 removes them); ms_batch_profile(b, 2) adds one-thread timer kernels
+ * between the phases of the graph as well (see ms_batch_phase_ms); it
+ * synchronises the stream. ms_batch_modes copies frame f's K kept modes, float32
  * [K, dim], to h_out (cap >= K; h_out NULL only reports K). ms_batch_destroy
  * synchronises the stream and frees everything. */
 typedef struct ms_batch ms_batch;
@@ -435,6 +437,16 @@ MS_API ms_status ms_batch_stats(const ms_batch* b, int32_t frame, ms_stats* out)
  * MS_ERR_STATE if a frame is still unfinished after `passes`. */
 MS_API ms_status ms_batch_run_eager(ms_batch* b, int32_t passes);
 MS_API ms_status ms_batch_profile(ms_batch* b, int32_t enable);
+/* Measurement only (no counterpart in the paper): with profiling level 2, the
+ * time of the last synchronised run split by phase, in ms, from the GPU
+ * global timer: out[0] set-up (compaction, normalisation, packing); summed
+ * over the loop's passes out[1] relaunch of the loop body, seed selection and
+ * work plan, out[2] the shift, out[3] its finalisation and early-stop check,
+ * out[4] the merge chain, out[5] coverage, out[6] the schedule and loop
+ * condition; out[7] labelling. Each phase includes the launch gaps inside
+ * it. Writes min(cap, 8) values (zeros below level 2) and *n_out = 8.
+ * MS_ERR_INVALID_ARG on NULL b or out with cap > 0. */
+MS_API ms_status ms_batch_phase_ms(const ms_batch* b, double* out, int32_t cap, int32_t* n_out);
 MS_API ms_status ms_batch_modes(const ms_batch* b, int32_t frame, float* h_out, int32_t cap,
                                 int32_t* n_modes_out);
 MS_API void ms_batch_destroy(ms_batch* b);

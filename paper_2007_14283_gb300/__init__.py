@@ -98,6 +98,7 @@ _SIGNATURES = {
     "ms_batch_run_host": (_i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "ms_batch_stats": (_i32, [_vp, _i32, ctypes.POINTER(ms_stats)]),
     "ms_batch_profile": (_i32, [_vp, _i32]),
+    "ms_batch_phase_ms": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), _i32, _pi32]),
     "ms_batch_run_eager": (_i32, [_vp, _i32]),
     "ms_batch_configure": (_i32, [_vp, _i32, _i32, _i32]),
     "ms_batch_autotune": (_i32, [_vp, _i32, ctypes.POINTER(ms_tune_result), _i32, _pi32]),
@@ -520,8 +521,20 @@ def ms_batch_autotune(b: Batch, reps: int = 3) -> list:
             for r in res[:n.value]]
 
 
-def ms_batch_profile(b: Batch, enable: bool = True):
-    _check(load().ms_batch_profile(b.handle, 1 if enable else 0))
+def ms_batch_profile(b: Batch, enable=True):
+    """enable: False/0 off, True/1 shift timers, 2 shift and phase timers."""
+    _check(load().ms_batch_profile(b.handle, int(enable)))
+
+
+MS_BATCH_PHASES = ("setup", "seed_plan", "shift", "finalize_check", "merge", "cover", "schedule", "label")
+
+
+def ms_batch_phase_ms(b: Batch) -> dict:
+    """Per-phase time of the last synchronised run (profiling level 2), ms."""
+    out = (ctypes.c_double * len(MS_BATCH_PHASES))()
+    n = ctypes.c_int32()
+    _check(load().ms_batch_phase_ms(b.handle, out, len(MS_BATCH_PHASES), ctypes.byref(n)))
+    return {k: out[i] for i, k in enumerate(MS_BATCH_PHASES)}
 
 
 def ms_batch_modes(b: Batch, frame: int):

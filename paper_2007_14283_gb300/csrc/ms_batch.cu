@@ -40,7 +40,8 @@ struct ms_batch {
     ms::BPlan plan;
     int32_t* blk_off;         // [B + 2] block work list of the current merge/cover/label kernel
     int32_t* blk_split;       // [B + 2] block work list with the inner loop split (slices at [B + 1])
-    int32_t* misc;            // [0] passes, [1] status, u64 at [2] band pairs, [4] tick, [6] shift ns, [8] shift launches
+    int32_t* misc;            // [0] passes, [1] status, u64 at [2] band pairs, [4] tick, [6] shift ns, [8] shift
+                              // launches, [14] last phase tick, [16..31] eight phase sums (ns)
     float* P32;
     int32_t* pix;
     uint8_t* covered;
@@ -77,7 +78,8 @@ struct ms_batch {
     int tc_shape;             // warp arrangement of the tensor-core shift kernel (ms_config.tc_shape)
     int64_t fixed_launches;   // set-up and labelling kernels
     bool prof;                // body brackets the shift launch with timer ticks
-    int32_t h_misc[16];       // host copy of misc after the last synchronised run
+    bool prof_phases;         // ... and every phase of the graph with phase ticks (k_b_phase)
+    int32_t h_misc[32];       // host copy of misc after the last synchronised run
     std::vector<ms::BFrame> hf;   // host copy of the frame table (device pointers of every frame)
     std::vector<int32_t*> h_labels;  // device label buffers
 };
@@ -95,6 +97,11 @@ constexpr int kPT = 256;    // pixel threads (cover, label)
 constexpr int kDefaultMaxPasses = 200000;  // loop guard: far above any real run (rounds x iterations)
 
 enum BlockSel { kSelDoneSeeds = 0, kSelDoneCands = 1, kSelDonePixels = 2, kSelAllPixels = 3 };
+// Phase sums of profiling level 2 (ms_batch_phase_ms): set-up; per pass the
+// loop's relaunch gap with seed selection and the work plan, the shift, its
+// finalisation and early-stop check, the merge chain, coverage, the schedule
+// with the loop condition; then labelling.
+enum Phase { kPhSetup = 0, kPhSeed, kPhShift, kPhFinalize, kPhMerge, kPhCover, kPhSchedule, kPhLabel, kPhases };
 
 // ------------------------------------------------------------ device math
 __device__ uint64_t d_splitmix64(uint64_t x) {
@@ -1006,6 +1013,18 @@ __global__ void k_b_tick(int* misc, const int32_t* __restrict__ item_total, int 
     }
 }
 
+// Phase timer (profiling level 2): adds the global-timer time since the last
+// phase tick to phase sum `slot` (u64 misc words 8..15); slot < 0 only starts
+// the clock. Ticks sit between the phases in stream order, so a phase's sum
+// includes the launch gaps inside it.
+__global__ void k_b_phase(int* misc, int slot) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    unsigned long long* m = reinterpret_cast<unsigned long long*>(misc);
+    if (slot >= 0) m[8 + slot] += t - m[7];
+    m[7] = t;
+}
+
 __global__ void k_b_cond(const BState* __restrict__ states, int B, int* misc, int max_passes,
                          cudaGraphConditionalHandle h) {
     if (threadIdx.x != 0) return;
@@ -1088,6 +1107,10 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     k_b_plan<<<1, kIT, 0, s>>>(b->frames, b->states, B, b->plan, b->target_mult * grid_shift,
                                b->split ? 0 : 2 * grid_shift, b->tc ? 1 : 0, grid_shift);
     LAUNCHED("k_b_plan");
+    if (b->prof_phases) {
+        k_b_phase<<<1, 1, 0, s>>>(b->misc, kPhSeed);
+        LAUNCHED("k_b_phase");
+    }
     if (b->prof) {
         k_b_tick<<<1, 1, 0, s>>>(b->misc, b->plan.item_off + B, 0);
         LAUNCHED("k_b_tick");
@@ -1107,11 +1130,19 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
         k_b_tick<<<1, 1, 0, s>>>(b->misc, b->plan.item_off + B, 1);
         LAUNCHED("k_b_tick");
     }
+    if (b->prof_phases) {
+        k_b_phase<<<1, 1, 0, s>>>(b->misc, kPhShift);
+        LAUNCHED("k_b_phase");
+    }
     k_b_finalize<Dp><<<G, 256, 0, s>>>(b->frames, b->states, B, b->plan, b->act[0], b->act[1], b->acc, b->X,
                                        b->sstate, b->support, b->cfg.tol);
     LAUNCHED("k_b_finalize");
     k_b_check<<<(B + 255) / 256, 256, 0, s>>>(b->states, B, gamma, b->cfg.max_iter);
     LAUNCHED("k_b_check");
+    if (b->prof_phases) {
+        k_b_phase<<<1, 1, 0, s>>>(b->misc, kPhFinalize);
+        LAUNCHED("k_b_phase");
+    }
     // merge chain for the frames whose round ended
     k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, B, kSelDoneSeeds, 256, 0, b->blk_off);
     LAUNCHED("k_b_blocks");
@@ -1147,6 +1178,10 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     k_b_merge_append<Dp><<<B, kIT, 0, s>>>(b->frames, b->states, b->X, b->cand, b->rank_cand, b->cand_state,
                                            b->modes);
     LAUNCHED("k_b_merge_append");
+    if (b->prof_phases) {
+        k_b_phase<<<1, 1, 0, s>>>(b->misc, kPhMerge);
+        LAUNCHED("k_b_phase");
+    }
     if (b->Mk) {  // BF16 form: the pixels against the new modes on the tensor cores
         k_b_blocks<<<1, 32, 0, s>>>(b->frames, b->states, B, kSelDonePixels, 128, 0, b->blk_off);
         LAUNCHED("k_b_blocks");
@@ -1163,6 +1198,10 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
                                         b->modes, (float)b->cfg.bandwidth_cos, b->cfg.bandwidth_cos);
         LAUNCHED("k_b_cover");
     }
+    if (b->prof_phases) {
+        k_b_phase<<<1, 1, 0, s>>>(b->misc, kPhCover);
+        LAUNCHED("k_b_phase");
+    }
     k_b_schedule<<<(B + 255) / 256, 256, 0, s>>>(b->states, B, b->cfg.P_target, L, b->cfg.H, b->cfg.max_rounds,
                                                  b->cfg.all_seeds);
     LAUNCHED("k_b_schedule");
@@ -1170,6 +1209,10 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
         k_b_cond<<<1, 32, 0, s>>>(b->states, B, b->misc,
                                   b->cfg.batch_max_passes > 0 ? b->cfg.batch_max_passes : kDefaultMaxPasses, h);
         LAUNCHED("k_b_cond");
+    }
+    if (b->prof_phases) {
+        k_b_phase<<<1, 1, 0, s>>>(b->misc, kPhSchedule);
+        LAUNCHED("k_b_phase");
     }
 #undef LAUNCHED
     *nlaunch = nl;
@@ -1181,7 +1224,11 @@ ms_status enqueue_setup(ms_batch* b, cudaStream_t s) {
     const int B = b->B;
     MS_CUDA(cudaMemsetAsync(b->covered, 0, (size_t)b->total_px, s));
     MS_CUDA(cudaMemsetAsync(b->acc, 0, sizeof(unsigned long long) * (size_t)b->total_px * (Dp + 1), s));
-    MS_CUDA(cudaMemsetAsync(b->misc, 0, 64, s));
+    MS_CUDA(cudaMemsetAsync(b->misc, 0, sizeof(b->h_misc), s));
+    if (b->prof_phases) {
+        k_b_phase<<<1, 1, 0, s>>>(b->misc, -1);
+        MS_LAUNCH("k_b_phase");
+    }
     const dim3 gc((unsigned)b->nblk_max, (unsigned)B);
     k_b_count<<<gc, kIT, 0, s>>>(b->frames, (int)b->nblk_max, b->block_tmp);
     MS_LAUNCH("k_b_count");
@@ -1198,6 +1245,18 @@ ms_status enqueue_setup(ms_batch* b, cudaStream_t s) {
     const dim3 gl((unsigned)((b->max_np + 255) / 256 < 1024 ? (b->max_np + 255) / 256 : 1024), (unsigned)B);
     k_b_labels_clear<<<gl, 256, 0, s>>>(b->frames, b->label_ptrs);
     MS_LAUNCH("k_b_labels_clear");
+    if (b->prof_phases) {
+        k_b_phase<<<1, 1, 0, s>>>(b->misc, kPhSetup);
+        MS_LAUNCH("k_b_phase");
+    }
+    return MS_OK;
+}
+
+// The labelling phase's closing tick (profiling level 2).
+ms_status enqueue_label_tick(ms_batch* b, cudaStream_t s) {
+    if (!b->prof_phases) return MS_OK;
+    k_b_phase<<<1, 1, 0, s>>>(b->misc, kPhLabel);
+    MS_LAUNCH("k_b_phase");
     return MS_OK;
 }
 
@@ -1254,12 +1313,13 @@ ms_status build_graph(ms_batch* b) {
     if (st2 != MS_OK) return st2;
     MS_CUDA(cudaStreamBeginCaptureToGraph(s, g, &cnode, nullptr, 1, cudaStreamCaptureModeRelaxed));
     st = enqueue_label<Dp>(b, s);
+    if (st == MS_OK) st = enqueue_label_tick(b, s);
     st2 = cuda_check(cudaStreamEndCapture(s, &tmp), "end capture (labels)");
     if (st != MS_OK) return st;
     if (st2 != MS_OK) return st2;
     MS_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
     b->body_launches = nl;
-    b->fixed_launches = (b->tc ? 5 : 4) + (b->Mk ? 4 : 2);  // set-up, then labelling
+    b->fixed_launches = (b->tc ? 5 : 4) + (b->Mk ? 4 : 2) + (b->prof_phases ? 3 : 0);  // set-up, then labelling
     return MS_OK;
 }
 
@@ -1273,6 +1333,7 @@ ms_status enqueue_eager(ms_batch* b, int passes) {
         st = enqueue_body<Dp>(b, b->stream, cudaGraphConditionalHandle{}, false, &nl);
     }
     if (st == MS_OK) st = enqueue_label<Dp>(b, b->stream);
+    if (st == MS_OK) st = enqueue_label_tick(b, b->stream);
     return st;
 }
 
@@ -1361,7 +1422,7 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
     const bool tcl = b->tc;  // labelling and coverage on the tensor cores
     const size_t n = (size_t)b->total_px;
     const size_t sizes[] = {
-        sizeof(BFrame) * B, sizeof(BState) * B, sizeof(int32_t) * ((B + 1) * 4 + (B + 2) * 2), 64,
+        sizeof(BFrame) * B, sizeof(BState) * B, sizeof(int32_t) * ((B + 1) * 4 + (B + 2) * 2), sizeof(b->h_misc),
         n * Dp * 4, n * 4, n, n * Dp * 4, n * 4, n * 4, n, n * 4, n * 4, n * 4,
         n * (Dp + 1) * 8, n * Dp * 4, n * 4, n * 4, n * 4, n, n * 4, n * kMergeCap * 4,
         (size_t)B * b->nblk_max * 4 + 4, b->tc ? (size_t)b->total_pk_rows * 128 * (Dp / 16) : 0, sizeof(int32_t*) * B,
@@ -1605,11 +1666,21 @@ extern "C" ms_status ms_batch_stats(const ms_batch* b, int32_t frame, ms_stats* 
 }
 
 extern "C" ms_status ms_batch_profile(ms_batch* b, int32_t enable) {
-    if (!b) return set_error(MS_ERR_INVALID_ARG, "batch is NULL");
-    if ((enable != 0) == b->prof) return MS_OK;
+    if (!b || enable < 0 || enable > 2) return set_error(MS_ERR_INVALID_ARG, "bad arguments");
+    if ((enable != 0) == b->prof && (enable == 2) == b->prof_phases) return MS_OK;
     MS_CUDA(cudaStreamSynchronize(b->stream));
     b->prof = enable != 0;
+    b->prof_phases = enable == 2;
     return rebuild_graph(b);
+}
+
+extern "C" ms_status ms_batch_phase_ms(const ms_batch* b, double* out, int32_t cap, int32_t* n_out) {
+    if (!b || cap < 0 || (cap > 0 && !out)) return set_error(MS_ERR_INVALID_ARG, "bad arguments");
+    const unsigned long long* m = reinterpret_cast<const unsigned long long*>(b->h_misc);
+    const int n = cap < kPhases ? cap : kPhases;
+    for (int i = 0; i < n; ++i) out[i] = b->prof_phases ? (double)m[8 + i] * 1e-6 : 0.0;
+    if (n_out) *n_out = kPhases;
+    return MS_OK;
 }
 
 extern "C" ms_status ms_batch_modes(const ms_batch* b, int32_t frame, float* h_out, int32_t cap,

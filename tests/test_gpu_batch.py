@@ -184,6 +184,40 @@ def test_batch_host_buffers_and_profile(ms_lib):
         b.close()
 
 
+def test_batch_phase_timers(ms_lib):
+    """Profiling level 2 adds phase timers between the graph's phases: the
+    labels and counters do not change, every phase sum is positive, and the
+    phases account for the run's time (within the launch gaps around them)."""
+    import time
+
+    import torch
+    fs = synth.batch_c4(seed=12, B=3, n_lo=1000, n_hi=5000)
+    embs, masks = _to_dev([(f.emb, f.mask) for f in fs])
+    b = _batch(ms_lib, embs, masks, precision=ms_lib.MS_BF16)
+    try:
+        ref = [t.cpu().clone() for t in b.labels]
+        st0 = ms_lib.ms_batch_stats(b, -1)
+        assert all(v == 0.0 for v in ms_lib.ms_batch_phase_ms(b).values())
+        ms_lib.ms_batch_profile(b, 2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ms_lib.ms_batch_run(b)
+        wall_ms = 1e3 * (time.perf_counter() - t0)
+        for a, c in zip(ref, b.labels):
+            assert torch.equal(a, c.cpu())
+        st = ms_lib.ms_batch_stats(b, -1)
+        assert st["seed_iters"] == st0["seed_iters"] and st["n_modes"] == st0["n_modes"]
+        ph = ms_lib.ms_batch_phase_ms(b)
+        assert set(ph) == set(ms_lib.MS_BATCH_PHASES)
+        assert all(v > 0.0 for v in ph.values()), ph
+        assert 0.5 * wall_ms <= sum(ph.values()) <= wall_ms, (ph, wall_ms)
+        assert ph["shift"] >= 0.9 * st["shift_ms"]  # the phase spans the shift timers' own span
+        with pytest.raises(ms_lib.MsError):
+            ms_lib.ms_batch_profile(b, 3)
+    finally:
+        b.close()
+
+
 def test_batch_eager_launches_equal_graph(ms_lib):
     import torch
     fs = synth.batch_c4(seed=11, B=3, n_lo=800, n_hi=6000)

@@ -64,11 +64,13 @@ struct ms_batch {
     int32_t* block_tmp;       // [B, nblk_max]
     void* Pk;
     void* Mk;                 // kept modes as BF16 split rows at the frames' Pk offsets (labelling)
+    void* Ck;                 // merge candidates (rank order) as BF16 split rows at the frames' Pk offsets
     int32_t** label_ptrs;     // device array of B label buffers
     CUtensorMap pmap;
     CUtensorMap pmap1;        // d = 32: dimensions 16..31 (the second Pk array)
     CUtensorMap mmap;
     CUtensorMap mmap1;        // d = 32: the modes' dimensions 16..31 (the second Mk array)
+    CUtensorMap cmap, cmap1;  // Ck, and its second array (d = 32)
     ms::LabelTcScratch lsc;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -1161,12 +1163,21 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     k_b_rank_invert<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_off, b->cand_rank, b->cand, b->X,
                                           b->rank_cand, b->Xr);
     LAUNCHED("k_b_rank_invert");
-    k_b_merge_old<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_split, b->X, b->cand, b->modes, mf,
-                                        b->cfg.merge_cos, b->cand_state, b->cand_rank, b->removed_r);
-    LAUNCHED("k_b_merge_old");
-    k_b_merge_pairs<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_split, b->Xr, b->removed_r,
-                                          b->rank_cand, mf, b->cfg.merge_cos, b->conf_deg, b->conf);
-    LAUNCHED("k_b_merge_pairs");
+    if (b->Ck) {  // BF16 form: both contractions of the merge on the tensor cores
+        ms_status ms2 = launch_merge_tc_batch(b->cmap, b->cmap1, b->mmap, b->mmap1, b->Ck, b->total_pk_rows, Dp,
+                                              b->frames, b->states, B, (int)b->max_pk_rows, b->Xr, b->modes,
+                                              b->rank_cand, b->cand_state, b->removed_r, b->conf_deg, b->conf, mf,
+                                              b->cfg.merge_cos, b->blk_off, b->lsc, b->num_sms, b->misc + 1, s);
+        if (ms2 != MS_OK) return ms2;
+        nl += 4;
+    } else {
+        k_b_merge_old<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_split, b->X, b->cand, b->modes, mf,
+                                            b->cfg.merge_cos, b->cand_state, b->cand_rank, b->removed_r);
+        LAUNCHED("k_b_merge_old");
+        k_b_merge_pairs<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_split, b->Xr, b->removed_r,
+                                              b->rank_cand, mf, b->cfg.merge_cos, b->conf_deg, b->conf);
+        LAUNCHED("k_b_merge_pairs");
+    }
     for (int sw = 0; sw < 8; ++sw) {
         k_b_merge_resolve<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_off, b->X, b->cand, b->cand_rank,
                                                 b->cand_state, b->conf_deg, b->conf, mf, b->cfg.merge_cos, sw == 7);
@@ -1427,7 +1438,7 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
         n * (Dp + 1) * 8, n * Dp * 4, n * 4, n * 4, n * 4, n, n * 4, n * kMergeCap * 4,
         (size_t)B * b->nblk_max * 4 + 4, b->tc ? (size_t)b->total_pk_rows * 128 * (Dp / 16) : 0, sizeof(int32_t*) * B,
         tcl ? (size_t)b->total_pk_rows * 128 * (Dp / 16) : 0, tcl ? n * sizeof(int2) : 0, sizeof(int32_t) * (B + 1) + 16,
-        n * Dp * 4, n};
+        n * Dp * 4, n, tcl ? (size_t)b->total_pk_rows * 128 * (Dp / 16) : 0};
     const int NS = (int)(sizeof(sizes) / sizeof(sizes[0]));
     size_t offs[32], tot = 0;
     for (int i = 0; i < NS; ++i) {
@@ -1478,6 +1489,7 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
     b->lsc.fix_count = b->lsc.off + (B + 1);
     b->Xr = (float*)(w + offs[28]);
     b->removed_r = (uint8_t*)(w + offs[29]);
+    b->Ck = tcl ? (void*)(w + offs[30]) : nullptr;
     ms_status s = cuda_check(cudaMallocHost((void**)&b->h_states, sizeof(BState) * B), "cudaMallocHost");
     if (s == MS_OK) s = cuda_check(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "cudaStreamCreate");
     if (s == MS_OK)
@@ -1497,6 +1509,10 @@ extern "C" ms_status ms_batch_create(const ms_config* cfg, int32_t B, const floa
     if (s == MS_OK && tcl) b->mmap1 = b->mmap;
     if (s == MS_OK && tcl && Dp == 32)
         s = encode_pk_map((uint8_t*)b->Mk + (size_t)b->total_pk_rows * 128, (int)b->total_pk_rows, &b->mmap1);
+    if (s == MS_OK && tcl) s = encode_pk_map(b->Ck, (int)b->total_pk_rows, &b->cmap);
+    if (s == MS_OK && tcl) b->cmap1 = b->cmap;
+    if (s == MS_OK && tcl && Dp == 32)
+        s = encode_pk_map((uint8_t*)b->Ck + (size_t)b->total_pk_rows * 128, (int)b->total_pk_rows, &b->cmap1);
     if (s == MS_OK && tcl) s = label_tc_setup();
     if (s == MS_OK) s = rebuild_graph(b);
     if (s != MS_OK) {

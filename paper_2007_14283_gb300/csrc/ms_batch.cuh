@@ -100,6 +100,18 @@ ms_status launch_cover_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap
                                 BState* states, int B, int max_pk_rows, const float* modes, const float* P32,
                                 const int32_t* pix, int d, double c, uint8_t* covered, const int32_t* tile_off,
                                 LabelTcScratch sc, int grid, int* status, cudaStream_t st);
+// The merge's two contractions on the tensor cores for the frames whose round
+// ended (tile_off: their candidates in blocks of 128): the candidates in rank
+// order (Xr, packed into Ck) against their earlier modes (Mk), then against
+// one another; exact decisions (merge_cos), the near-threshold pairs decided
+// by the FP32-then-FP64 test. Sets removed_r / cand_state and fills the
+// conflict lists as k_b_merge_old and k_b_merge_pairs do.
+ms_status launch_merge_tc_batch(const CUtensorMap& cmap, const CUtensorMap& cmap1, const CUtensorMap& mmap,
+                                const CUtensorMap& mmap1, void* Ck, int64_t rows, int Dp, const BFrame* frames,
+                                BState* states, int B, int max_pk_rows, const float* Xr, const float* modes,
+                                const int32_t* rank_cand, uint8_t* cand_state, uint8_t* removed_r, int32_t* conf_deg,
+                                int32_t* conf, float thr_f, double thr, const int32_t* tile_off, LabelTcScratch sc,
+                                int grid, int* status, cudaStream_t st);
 ms_status launch_label_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, const CUtensorMap& pmap1,
                                 const CUtensorMap& mmap1, void* Mk, int64_t mk_rows, int Dp, const BFrame* frames,
                                 const BState* states, int B, int max_pk_rows, const float* modes, const float* P32,

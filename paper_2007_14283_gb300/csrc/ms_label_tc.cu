@@ -121,6 +121,44 @@ struct LbBatchCover {
     }
 };
 
+// The merge of the frames whose round ended (off from k_b_blocks with 128
+// candidates per block): row tile t of a frame's k candidates, in rank order
+// (Ck rows), against its modes kept in earlier rounds (Mk, LbBatchOld) or
+// against the candidates ranked up to the tile's end (Ck, LbBatchPairs).
+struct LbBatchOld {
+    const BFrame* frames;
+    const BState* states;
+    const int32_t* off;
+    int B;
+    int total_;
+    __device__ __forceinline__ bool init() {
+        total_ = off[B];
+        return total_ > 0;
+    }
+    __device__ __forceinline__ int total() const { return total_; }
+    __device__ __forceinline__ LbItem item(int i) const {
+        const int f = locate(off, B, i);
+        return LbItem{f, frames[f].pk_row0, i - off[f], states[f].dc.n_cand, states[f].dc.n_kept, 0};
+    }
+};
+struct LbBatchPairs {
+    const BFrame* frames;
+    const BState* states;
+    const int32_t* off;
+    int B;
+    int total_;
+    __device__ __forceinline__ bool init() {
+        total_ = off[B];
+        return total_ > 0;
+    }
+    __device__ __forceinline__ int total() const { return total_; }
+    __device__ __forceinline__ LbItem item(int i) const {
+        const int f = locate(off, B, i);
+        const int t = i - off[f], k = states[f].dc.n_cand;
+        return LbItem{f, frames[f].pk_row0, t, k, min(k, (t + 1) * 128), 0};
+    }
+};
+
 __device__ __forceinline__ bool lwarp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
     return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort));
 }
@@ -145,17 +183,43 @@ struct LbOut {
     // form) or the frames' states (batch form), and c
     uint8_t* covered;
     int* n_uncovered;
-    float c_f;
+    float c_f;             // coverage: c; merge: merge_cos rounded to FP32
     BState* states;
+    // merge (rows are candidates in rank order): their FP32 positions, the
+    // removed-by-an-earlier-mode flags by rank, rank -> candidate, the
+    // candidates' states and conflict lists, and merge_cos
+    const float* Xr;
+    uint8_t* removed_r;
+    const int32_t* rank_cand;
+    uint8_t* cand_state;
+    int32_t* conf_deg;
+    int32_t* conf;
+    double thr;
 };
 
-// kCover = false: labelling (best and second-best mode of every pixel).
-// kCover = true: coverage of the OSOP stop rule against the modes [k0, K):
+// What k_label_tc's score readers do with a row's scores.
+enum LbMode {
+    kLbLabel = 0,   // best and second-best column (labelling)
+    kLbCover = 1,   // best column against c (OSOP coverage)
+    kLbOld = 2,     // best column against merge_cos (candidates against earlier modes)
+    kLbPairs = 3,   // every column ranked above the row at or above merge_cos (conflict lists)
+};
+
+// kMode = kLbLabel: labelling (best and second-best mode of every pixel).
+// kMode = kLbCover: coverage of the OSOP stop rule against the modes [k0, K):
 // an uncovered pixel whose best score clears c by kEpsTc is covered; one
 // within kEpsTc of c is queued for the FP32 form's exact test.
+// kMode = kLbOld, kLbPairs: the merge's two contractions, rows being the
+// candidates in rank order. A score farther than kDelta = kEpsTc + 2e-6 from
+// merge_cos decides the pair as the exact test does (kEpsTc bounds the split
+// score, 2e-6 the gap between x.m and the FP64 cosine of near-unit FP32
+// vectors); nearer ones take the exact test itself (cos_at_least). kLbOld:
+// a candidate within merge_cos of an earlier mode is removed; near ones are
+// queued for k_merge_old_fix. kLbPairs: every candidate ranked above the row
+// that is not removed and within merge_cos joins the row's conflict list.
 // pmap / mmap: the pixel and mode split rows (dimensions 0-15); pmap1 /
 // mmap1: dimensions 16-31 (D = 32 only).
-template <class Map, bool kCover, int kD>
+template <class Map, int kMode, int kD>
 __global__ void __launch_bounds__(kLThreads, 1)
 k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap mmap,
            const __grid_constant__ CUtensorMap pmap1, const __grid_constant__ CUtensorMap mmap1, Map map, LbOut out,
@@ -163,6 +227,8 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
     using L = LbDim<kD>;
     constexpr int kHalves = L::kHalves, kLStages = L::kStages;
     constexpr float kEpsTc = L::kEps;
+    constexpr float kDelta = L::kEps + 2e-6f;
+    constexpr bool kCover = kMode == kLbCover || kMode == kLbOld;  // best column against a threshold
     if (!map.init()) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -304,10 +370,17 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
         for (int item = blockIdx.x; item < items; item += gridDim.x) {
             const LbItem ii = map.item(item);
             const int nmt = (ii.K - ii.k0 + 127) / 128;
-            if (kCover && nmt <= 0) continue;
+            if (kMode != kLbLabel && nmt <= 0) continue;
             bool ok = true;
             float b1 = -INFINITY, b2 = -INFINITY;
             int i1 = -1;
+            // merge rows: the candidate's rank, its frame's row base, and
+            // whether it takes part (a candidate removed by an earlier mode
+            // needs no conflict list)
+            const int mi = ii.pt * 128 + r;
+            const int64_t mbase = (kMode == kLbPairs && out.frames) ? out.frames[ii.frame].pix0 : 0;
+            const bool mrow = kMode == kLbPairs && mi < ii.n && !out.removed_r[mbase + mi];
+            int ma = -1;  // the row's candidate index, read when first needed
             for (int mt = 0; mt < nmt; ++mt, ++g) {
                 const int b = g % kLSBufs;
                 if (!(ok = lwarp_wait(&s_full[b], (g / kLSBufs) & 1, abort))) break;
@@ -329,6 +402,41 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
                 for (int j = 1; j < 32; ++j) m = fmaxf(m, __uint_as_float(v[j]));
                 if (kCover) {
                     b1 = fmaxf(b1, m);
+                    continue;
+                }
+                if constexpr (kMode == kLbPairs) {
+                    const float lo = out.c_f - kDelta, hi = out.c_f + kDelta;
+                    if (__any_sync(0xffffffffu, mrow && m >= lo) && mrow && m >= lo) {
+                        uint32_t near = 0, sure = 0;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float sc = __uint_as_float(v[j]);
+                            near |= (uint32_t)(sc >= lo && col0 + j < mi) << j;
+                            sure |= (uint32_t)(sc >= hi) << j;
+                        }
+                        float xr[kD];
+                        bool have_x = false;
+                        while (near) {
+                            const int j = __ffs(near) - 1;
+                            near &= near - 1;
+                            const int col = col0 + j;
+                            if (out.removed_r[mbase + col]) continue;
+                            bool hit = (sure >> j) & 1u;
+                            if (!hit) {
+                                if (!have_x) {
+#pragma unroll
+                                    for (int k = 0; k < kD; ++k) xr[k] = out.Xr[(mbase + mi) * kD + k];
+                                    have_x = true;
+                                }
+                                hit = cos_at_least<kD>(xr, out.Xr + (mbase + col) * kD, out.c_f, out.thr);
+                            }
+                            if (hit) {
+                                if (ma < 0) ma = out.rank_cand[mbase + mi];
+                                const int slot = atomicAdd(&out.conf_deg[mbase + ma], 1);
+                                if (slot < kMergeCap) out.conf[(mbase + ma) * kMergeCap + slot] = out.rank_cand[mbase + col];
+                            }
+                        }
+                    }
                     continue;
                 }
                 // A column can change the best two only if it beats the
@@ -364,7 +472,20 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
                 : "r"(ok ? 0u : 1u), "n"(kLEpi * 32)
                 : "memory");
             if (any_bad) break;
-            if (kCover && h == 0) {
+            if (kMode == kLbOld && h == 0) {
+                const float B1 = fmaxf(fmaxf(xb1[r], xb1[128 + r]), fmaxf(xb1[256 + r], xb1[384 + r]));
+                const int i = ii.pt * 128 + r;
+                const int64_t base = out.frames[ii.frame].pix0;
+                if (i < ii.n && !out.removed_r[base + i]) {
+                    if (B1 >= out.c_f + kDelta) {
+                        out.removed_r[base + i] = 1;
+                        out.cand_state[base + out.rank_cand[base + i]] = kRemoved;
+                    } else if (B1 >= out.c_f - kDelta) {
+                        const int slot = atomicAdd(out.fix_count, 1);
+                        out.fix[slot] = make_int2(ii.frame, i);
+                    }
+                }
+            } else if (kMode == kLbCover && h == 0) {
                 const float B1 = fmaxf(fmaxf(xb1[r], xb1[128 + r]), fmaxf(xb1[256 + r], xb1[384 + r]));
                 const int i = ii.pt * 128 + r;
                 const int64_t base = out.frames ? out.frames[ii.frame].pix0 : 0;
@@ -381,7 +502,7 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
                 const unsigned nb = __ballot_sync(0xffffffffu, newly);
                 if (lane == 0 && nb)
                     atomicSub(out.states ? &out.states[ii.frame].dc.n_uncovered : out.n_uncovered, __popc(nb));
-            } else if (!kCover && h == 0) {
+            } else if (kMode == kLbLabel && h == 0) {
                 float B1 = xb1[r], B2 = xb2[r];
                 int I1 = xi1[r];
 #pragma unroll
@@ -658,6 +779,50 @@ __global__ void k_cover_fix_batch(const int2* __restrict__ fix, const int* __res
     }
 }
 
+// The candidates of every frame whose round ended, in rank order (Xr), as
+// BF16 split rows at the frame's Pk row offsets; clears the recheck queue.
+template <int Dp>
+__global__ void k_pack_cands_batch(const BFrame* __restrict__ frames, const BState* __restrict__ states,
+                                   const float* __restrict__ Xr, uint4* __restrict__ Ck, int64_t half_rows,
+                                   int* fix_count) {
+    const BFrame& fr = frames[blockIdx.y];
+    const BState& st = states[blockIdx.y];
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *fix_count = 0;
+    if (st.phase != kRoundDone) return;
+    const int k = st.dc.n_cand;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (k + 127) / 128 * 128) return;
+    pack_mode<Dp>(r < k ? Xr + (fr.pix0 + r) * Dp : nullptr, Ck, fr.pk_row0 + r, half_rows);
+}
+
+// Candidates queued by the tensor-core test against earlier modes (score
+// within kDelta of merge_cos), decided exactly as k_b_merge_old decides: one
+// warp per candidate, lanes over the frame's earlier modes.
+template <int Dp>
+__global__ void k_merge_old_fix_batch(const int2* __restrict__ fix, const int* __restrict__ fix_count,
+                                      const float* __restrict__ Xr, const float* __restrict__ modes,
+                                      const BFrame* __restrict__ frames, const BState* __restrict__ states,
+                                      const int32_t* __restrict__ rank_cand, float thr_f, double thr,
+                                      uint8_t* __restrict__ cand_state, uint8_t* __restrict__ removed_r) {
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int cnt = *fix_count;
+    for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < cnt; e += gridDim.x * wpb) {
+        const int2 fi = fix[e];
+        const int64_t base = frames[fi.x].pix0;
+        const int K = states[fi.x].dc.n_kept;
+        float x[Dp];
+#pragma unroll
+        for (int k = 0; k < Dp; ++k) x[k] = Xr[(base + fi.y) * Dp + k];
+        bool hit = false;
+        for (int j = lane; j < K && !hit; j += 32) hit = cos_at_least<Dp>(x, modes + (base + j) * Dp, thr_f, thr);
+        if (__any_sync(0xffffffffu, hit) && lane == 0) {
+            removed_r[base + fi.y] = 1;
+            cand_state[base + rank_cand[base + fi.y]] = kRemoved;
+        }
+    }
+}
+
 // Per-frame offsets of the label items (128-pixel tiles); clears the queue.
 __global__ void k_label_items(const BFrame* __restrict__ frames, int B, int32_t* __restrict__ off,
                               int* __restrict__ fix_count) {
@@ -674,11 +839,51 @@ __global__ void k_label_items(const BFrame* __restrict__ frames, int B, int32_t*
 template <int D>
 ms_status label_tc_setup_dim() {
     constexpr int smem = LbDim<D>::kSmemBytes;
-    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbSingle, false, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbSingle, true, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbBatch, false, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbBatchCover, true, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbSingle, kLbLabel, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbSingle, kLbCover, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbBatch, kLbLabel, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbBatchCover, kLbCover, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem));
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbBatchOld, kLbOld, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem));
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbBatchPairs, kLbPairs, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem));
+    return MS_OK;
+}
+
+template <int Dp>
+ms_status merge_tc_batch(const CUtensorMap& cmap, const CUtensorMap& cmap1, const CUtensorMap& mmap,
+                         const CUtensorMap& mmap1, void* Ck, int64_t rows, const BFrame* frames, BState* states, int B,
+                         int max_pk_rows, const float* Xr, const float* modes, const int32_t* rank_cand,
+                         uint8_t* cand_state, uint8_t* removed_r, int32_t* conf_deg, int32_t* conf, float thr_f,
+                         double thr, const int32_t* tile_off, LabelTcScratch sc, int grid, int* status,
+                         cudaStream_t st) {
+    const dim3 gp((unsigned)((max_pk_rows + 255) / 256), (unsigned)B);
+    k_pack_cands_batch<Dp><<<gp, 256, 0, st>>>(frames, states, Xr, (uint4*)Ck, rows, sc.fix_count);
+    MS_LAUNCH("k_pack_cands_batch");
+    LbOut out{};
+    out.frames = frames;
+    out.fix = sc.fix;
+    out.fix_count = sc.fix_count;
+    out.c_f = thr_f;
+    out.Xr = Xr;
+    out.removed_r = removed_r;
+    out.rank_cand = rank_cand;
+    out.cand_state = cand_state;
+    out.conf_deg = conf_deg;
+    out.conf = conf;
+    out.thr = thr;
+    LbBatchOld om{frames, states, tile_off, B, 0};
+    k_label_tc<LbBatchOld, kLbOld, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(cmap, mmap, cmap1, mmap1, om,
+                                                                                     out, status);
+    MS_LAUNCH("k_label_tc(merge, earlier modes)");
+    k_merge_old_fix_batch<Dp><<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, Xr, modes, frames, states, rank_cand, thr_f,
+                                                    thr, cand_state, removed_r);
+    MS_LAUNCH("k_merge_old_fix_batch");
+    LbBatchPairs pm{frames, states, tile_off, B, 0};
+    k_label_tc<LbBatchPairs, kLbPairs, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(cmap, cmap, cmap1, cmap1,
+                                                                                         pm, out, status);
+    MS_LAUNCH("k_label_tc(merge, conflicts)");
     return MS_OK;
 }
 
@@ -694,7 +899,7 @@ ms_status cover_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, const
     const float c_f = (float)c;
     LbBatchCover map{frames, states, tile_off, B, 0};
     LbOut out{nullptr, nullptr, frames, pix, sc.fix, sc.fix_count, covered, nullptr, c_f, states};
-    k_label_tc<LbBatchCover, true, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(pmap, mmap, pmap1, mmap1, map,
+    k_label_tc<LbBatchCover, kLbCover, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(pmap, mmap, pmap1, mmap1, map,
                                                                                        out, status);
     MS_LAUNCH("k_label_tc(cover, batch)");
     k_cover_fix_batch<Dp><<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, P32, modes, frames, states, pix, d, c_f, c,
@@ -720,7 +925,7 @@ ms_status cover_tc_single(const CUtensorMap& pmap, const CUtensorMap& pmap1, voi
     map.k0 = k0;
     const float c_f = (float)c;
     LbOut out{nullptr, nullptr, nullptr, pix, sc.fix, sc.fix_count, covered, n_uncovered, c_f, nullptr};
-    k_label_tc<LbSingle, true, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(pmap, mmap, pmap1, mmap1, map, out,
+    k_label_tc<LbSingle, kLbCover, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(pmap, mmap, pmap1, mmap1, map, out,
                                                                                    status);
     MS_LAUNCH("k_label_tc(cover)");
     k_cover_fix<Dp><<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, P32, modes, k0, k1, pix, emb, d, c_f, c, covered,
@@ -746,7 +951,7 @@ ms_status label_tc_single(const CUtensorMap& pmap, const CUtensorMap& pmap1, voi
     if (Dp == 32 && (s = encode_pk_map((uint8_t*)Mk + n_pad * 128, (int)n_pad, &mmap1)) != MS_OK) return s;
     LbSingle map{n, K};
     LbOut out{nullptr, labels, nullptr, pix, sc.fix, sc.fix_count, nullptr, nullptr, 0.f, nullptr};
-    k_label_tc<LbSingle, false, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(pmap, mmap, pmap1, mmap1, map,
+    k_label_tc<LbSingle, kLbLabel, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(pmap, mmap, pmap1, mmap1, map,
                                                                                     out, status);
     MS_LAUNCH("k_label_tc");
     if (K > 1) {
@@ -770,7 +975,7 @@ ms_status label_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, const
     MS_LAUNCH("k_label_items");
     LbBatch map{frames, states, sc.off, B, 0};
     LbOut out{labels, nullptr, frames, pix, sc.fix, sc.fix_count, nullptr, nullptr, 0.f, nullptr};
-    k_label_tc<LbBatch, false, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(pmap, mmap, pmap1, mmap1, map,
+    k_label_tc<LbBatch, kLbLabel, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(pmap, mmap, pmap1, mmap1, map,
                                                                                    out, status);
     MS_LAUNCH("k_label_tc(batch)");
     k_label_fix<Dp><<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, P32, modes, frames, states, pix, nullptr, 0, d, labels,
@@ -784,6 +989,20 @@ ms_status label_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, const
 ms_status label_tc_setup() {
     ms_status s = label_tc_setup_dim<16>();
     return s == MS_OK ? label_tc_setup_dim<32>() : s;
+}
+
+ms_status launch_merge_tc_batch(const CUtensorMap& cmap, const CUtensorMap& cmap1, const CUtensorMap& mmap,
+                                const CUtensorMap& mmap1, void* Ck, int64_t rows, int Dp, const BFrame* frames,
+                                BState* states, int B, int max_pk_rows, const float* Xr, const float* modes,
+                                const int32_t* rank_cand, uint8_t* cand_state, uint8_t* removed_r, int32_t* conf_deg,
+                                int32_t* conf, float thr_f, double thr, const int32_t* tile_off, LabelTcScratch sc,
+                                int grid, int* status, cudaStream_t st) {
+    return Dp == 32 ? merge_tc_batch<32>(cmap, cmap1, mmap, mmap1, Ck, rows, frames, states, B, max_pk_rows, Xr, modes,
+                                         rank_cand, cand_state, removed_r, conf_deg, conf, thr_f, thr, tile_off, sc,
+                                         grid, status, st)
+                    : merge_tc_batch<16>(cmap, cmap1, mmap, mmap1, Ck, rows, frames, states, B, max_pk_rows, Xr, modes,
+                                         rank_cand, cand_state, removed_r, conf_deg, conf, thr_f, thr, tile_off, sc,
+                                         grid, status, st);
 }
 
 ms_status launch_cover_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, const CUtensorMap& pmap1,

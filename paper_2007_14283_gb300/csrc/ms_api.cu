@@ -170,7 +170,7 @@ ms_status validate(const ms_config* c) {
 constexpr size_t kAlign = 256;
 
 struct Layout {
-    size_t off[26];
+    size_t off[29];
     size_t total;
 
 };
@@ -206,9 +206,12 @@ Layout plan(int64_t np, int Dp, int target_items, bool bf16) {
         bf16 ? (n + 127) / 128 * 128 * 128 * (Dp / 16) : 0,  // 22 Pk (one array per 16 dimensions)
         bf16 ? (n + 127) / 128 * 128 * 128 * (Dp / 16) : 0,  // 23 Mk (labelling on the tensor cores)
         bf16 ? n * sizeof(int2) + 16 : 0,                     // 24 label_fix + count
+        bf16 ? n * Dp * sizeof(float) : 0,                    // 25 Xr (merge candidates in rank order)
+        bf16 ? n : 0,                                         // 26 removed_r
+        bf16 ? (n + 127) / 128 * 128 * 128 * (Dp / 16) : 0,  // 27 Ck (their BF16 split rows)
     };
     size_t t = 0;
-    for (int i = 0; i < 25; ++i) {
+    for (int i = 0; i < 28; ++i) {
         L.off[i] = t;
         t += align_up(sizes[i]);
     }
@@ -339,6 +342,9 @@ ms_status ctx_alloc(const ms_config* cfg, int64_t max_pixels, cudaStream_t strea
     ctx->Pk = cfg->precision == MS_BF16 ? (void*)(b + L.off[22]) : nullptr;
     ctx->Mk = cfg->precision == MS_BF16 ? (void*)(b + L.off[23]) : nullptr;
     ctx->label_fix = cfg->precision == MS_BF16 ? (int2*)(b + L.off[24]) : nullptr;
+    ctx->Xr = cfg->precision == MS_BF16 ? (float*)(b + L.off[25]) : nullptr;
+    ctx->removed_r = cfg->precision == MS_BF16 ? (uint8_t*)(b + L.off[26]) : nullptr;
+    ctx->Ck = cfg->precision == MS_BF16 ? (void*)(b + L.off[27]) : nullptr;
     ctx->round_log_cap = 64;
     ctx->round_log = new (std::nothrow) int64_t[ctx->round_log_cap * 4];
     if (!ctx->round_log) {

@@ -786,8 +786,9 @@ template <int Dp>
 __global__ void __launch_bounds__(kMT)
 k_b_merge_resolve(const BFrame* __restrict__ frames, BState* states, int B, const int32_t* __restrict__ off,
                   const float* __restrict__ X, const int32_t* __restrict__ cand,
-                  const int32_t* __restrict__ cand_rank, uint8_t* cand_state, const int32_t* __restrict__ conf_deg,
-                  const int32_t* __restrict__ conf, float thr_f, double thr, int count_left) {
+                  const int32_t* __restrict__ cand_rank, const int32_t* __restrict__ rank_cand, uint8_t* cand_state,
+                  const int32_t* __restrict__ conf_deg, const int32_t* __restrict__ conf, float thr_f, double thr,
+                  int count_left) {
     for (int bb = blockIdx.x; bb < off[B]; bb += gridDim.x) {
         const int f = locate(off, B, bb);
         const int lb = bb - off[f];
@@ -806,11 +807,13 @@ k_b_merge_resolve(const BFrame* __restrict__ frames, BState* states, int B, cons
                 if (s == kUndecided) all_removed = false;
             }
         } else {
+            // more conflicts than were stored: test the candidates ranked
+            // above this one again, in rank order
             float x[Dp];
             ldv<Dp>(x, X + (int64_t)cand[base + a] * Dp);
             const int ra = cand_rank[base + a];
-            for (int b2 = 0; b2 < k; ++b2) {
-                if (cand_rank[base + b2] >= ra) continue;
+            for (int rb = 0; rb < ra; ++rb) {
+                const int b2 = rank_cand[base + rb];
                 const uint8_t s = st[b2];
                 if (s == kRemoved) continue;
                 if (!cos_at_least<Dp>(x, X + (int64_t)cand[base + b2] * Dp, thr_f, thr)) continue;
@@ -1180,7 +1183,8 @@ ms_status enqueue_body(ms_batch* b, cudaStream_t s, cudaGraphConditionalHandle h
     }
     for (int sw = 0; sw < 8; ++sw) {
         k_b_merge_resolve<Dp><<<G, kMT, 0, s>>>(b->frames, b->states, B, b->blk_off, b->X, b->cand, b->cand_rank,
-                                                b->cand_state, b->conf_deg, b->conf, mf, b->cfg.merge_cos, sw == 7);
+                                                b->rank_cand, b->cand_state, b->conf_deg, b->conf, mf,
+                                                b->cfg.merge_cos, sw == 7);
         LAUNCHED("k_b_merge_resolve");
     }
     k_b_merge_sequential<Dp><<<B, 32, 0, s>>>(b->frames, b->states, b->X, b->cand, b->rank_cand, b->cand_state, mf,

@@ -112,6 +112,12 @@ ms_status launch_merge_tc_batch(const CUtensorMap& cmap, const CUtensorMap& cmap
                                 const int32_t* rank_cand, uint8_t* cand_state, uint8_t* removed_r, int32_t* conf_deg,
                                 int32_t* conf, float thr_f, double thr, const int32_t* tile_off, LabelTcScratch sc,
                                 int grid, int* status, cudaStream_t st);
+// The same for one frame: k candidates (Xr, packed into Ck) against its K_old
+// earlier modes (Mk), then against one another.
+ms_status launch_merge_tc_single(void* Ck, void* Mk, int64_t n_pad, int Dp, int k, int K_old, const float* Xr,
+                                 const float* modes, const int32_t* rank_cand, uint8_t* cand_state, uint8_t* removed_r,
+                                 int32_t* conf_deg, int32_t* conf, float thr_f, double thr, LabelTcScratch sc,
+                                 int grid, int* status, cudaStream_t st);
 ms_status launch_label_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, const CUtensorMap& pmap1,
                                 const CUtensorMap& mmap1, void* Mk, int64_t mk_rows, int Dp, const BFrame* frames,
                                 const BState* states, int B, int max_pk_rows, const float* modes, const float* P32,

@@ -142,6 +142,9 @@ struct ms_ctx {
     int tc_grid;         // persistent grid of the tensor-core shift kernel
     void* Mk;            // [n_pad, 64] bf16 split rows of the kept modes (labelling)
     int2* label_fix;     // [n] near-tie queue of the tensor-core labelling, then its count
+    float* Xr;           // BF16 form: [n, Dp] merge candidates' positions in rank order
+    uint8_t* removed_r;  // BF16 form: [n] candidates removed by an earlier mode, by rank
+    void* Ck;            // BF16 form: [n_pad, 64] bf16 split rows of Xr (a second array for Dp = 32)
     // measurement
     bool prof;
     cudaEvent_t ev[64];  // start/end pairs around shift launches of one batch

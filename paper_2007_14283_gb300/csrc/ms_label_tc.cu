@@ -159,6 +159,17 @@ struct LbBatchPairs {
     }
 };
 
+// The same for one frame (row base 0): k candidates against K earlier modes,
+// or against one another (pairs).
+struct LbSingleMerge {
+    int k, K, pairs;
+    __device__ __forceinline__ bool init() { return k > 0; }
+    __device__ __forceinline__ int total() const { return (k + 127) / 128; }
+    __device__ __forceinline__ LbItem item(int i) const {
+        return LbItem{0, 0, i, k, pairs ? min(k, (i + 1) * 128) : K, 0};
+    }
+};
+
 __device__ __forceinline__ bool lwarp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
     return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort));
 }
@@ -475,7 +486,7 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
             if (kMode == kLbOld && h == 0) {
                 const float B1 = fmaxf(fmaxf(xb1[r], xb1[128 + r]), fmaxf(xb1[256 + r], xb1[384 + r]));
                 const int i = ii.pt * 128 + r;
-                const int64_t base = out.frames[ii.frame].pix0;
+                const int64_t base = out.frames ? out.frames[ii.frame].pix0 : 0;
                 if (i < ii.n && !out.removed_r[base + i]) {
                     if (B1 >= out.c_f + kDelta) {
                         out.removed_r[base + i] = 1;
@@ -798,10 +809,11 @@ __global__ void k_pack_cands_batch(const BFrame* __restrict__ frames, const BSta
 // Candidates queued by the tensor-core test against earlier modes (score
 // within kDelta of merge_cos), decided exactly as k_b_merge_old decides: one
 // warp per candidate, lanes over the frame's earlier modes.
+// One frame: frames and states are nullptr, the frame's earlier modes are K1.
 template <int Dp>
 __global__ void k_merge_old_fix_batch(const int2* __restrict__ fix, const int* __restrict__ fix_count,
                                       const float* __restrict__ Xr, const float* __restrict__ modes,
-                                      const BFrame* __restrict__ frames, const BState* __restrict__ states,
+                                      const BFrame* __restrict__ frames, const BState* __restrict__ states, int K1,
                                       const int32_t* __restrict__ rank_cand, float thr_f, double thr,
                                       uint8_t* __restrict__ cand_state, uint8_t* __restrict__ removed_r) {
     const int lane = threadIdx.x & 31;
@@ -809,8 +821,8 @@ __global__ void k_merge_old_fix_batch(const int2* __restrict__ fix, const int* _
     const int cnt = *fix_count;
     for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < cnt; e += gridDim.x * wpb) {
         const int2 fi = fix[e];
-        const int64_t base = frames[fi.x].pix0;
-        const int K = states[fi.x].dc.n_kept;
+        const int64_t base = frames ? frames[fi.x].pix0 : 0;
+        const int K = states ? states[fi.x].dc.n_kept : K1;
         float x[Dp];
 #pragma unroll
         for (int k = 0; k < Dp; ++k) x[k] = Xr[(base + fi.y) * Dp + k];
@@ -821,6 +833,15 @@ __global__ void k_merge_old_fix_batch(const int2* __restrict__ fix, const int* _
             cand_state[base + rank_cand[base + fi.y]] = kRemoved;
         }
     }
+}
+
+// One frame's k candidates (rank order, Xr) as BF16 split rows [0, kp).
+template <int Dp>
+__global__ void k_pack_cands_single(const float* __restrict__ Xr, int k, int kp, uint4* __restrict__ Ck,
+                                    int64_t half_rows) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= kp) return;
+    pack_mode<Dp>(r < k ? Xr + (int64_t)r * Dp : nullptr, Ck, r, half_rows);
 }
 
 // Per-frame offsets of the label items (128-pixel tiles); clears the queue.
@@ -848,6 +869,54 @@ ms_status label_tc_setup_dim() {
                                  smem));
     MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbBatchPairs, kLbPairs, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem));
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbSingleMerge, kLbOld, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem));
+    MS_CUDA(cudaFuncSetAttribute(k_label_tc<LbSingleMerge, kLbPairs, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem));
+    return MS_OK;
+}
+
+template <int Dp>
+ms_status merge_tc_single(void* Ck, void* Mk, int64_t n_pad, int k, int K_old, const float* Xr, const float* modes,
+                          const int32_t* rank_cand, uint8_t* cand_state, uint8_t* removed_r, int32_t* conf_deg,
+                          int32_t* conf, float thr_f, double thr, LabelTcScratch sc, int grid, int* status,
+                          cudaStream_t st) {
+    MS_CUDA(cudaMemsetAsync(sc.fix_count, 0, sizeof(int), st));
+    const int kp = (k + 127) / 128 * 128;
+    k_pack_cands_single<Dp><<<(kp + 255) / 256, 256, 0, st>>>(Xr, k, kp, (uint4*)Ck, n_pad);
+    MS_LAUNCH("k_pack_cands_single");
+    CUtensorMap cmap, cmap1, mmap, mmap1;
+    ms_status s = encode_pk_map(Ck, (int)n_pad, &cmap);
+    if (s == MS_OK) s = encode_pk_map(Mk, (int)n_pad, &mmap);
+    if (s != MS_OK) return s;
+    cmap1 = cmap;
+    mmap1 = mmap;
+    if (Dp == 32 && (s = encode_pk_map((uint8_t*)Ck + n_pad * 128, (int)n_pad, &cmap1)) != MS_OK) return s;
+    if (Dp == 32 && (s = encode_pk_map((uint8_t*)Mk + n_pad * 128, (int)n_pad, &mmap1)) != MS_OK) return s;
+    LbOut out{};
+    out.fix = sc.fix;
+    out.fix_count = sc.fix_count;
+    out.c_f = thr_f;
+    out.Xr = Xr;
+    out.removed_r = removed_r;
+    out.rank_cand = rank_cand;
+    out.cand_state = cand_state;
+    out.conf_deg = conf_deg;
+    out.conf = conf;
+    out.thr = thr;
+    if (K_old > 0) {
+        LbSingleMerge om{k, K_old, 0};
+        k_label_tc<LbSingleMerge, kLbOld, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(cmap, mmap, cmap1, mmap1,
+                                                                                            om, out, status);
+        MS_LAUNCH("k_label_tc(merge, earlier modes)");
+        k_merge_old_fix_batch<Dp><<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, Xr, modes, nullptr, nullptr, K_old,
+                                                        rank_cand, thr_f, thr, cand_state, removed_r);
+        MS_LAUNCH("k_merge_old_fix");
+    }
+    LbSingleMerge pm{k, 0, 1};
+    k_label_tc<LbSingleMerge, kLbPairs, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(cmap, cmap, cmap1, cmap1,
+                                                                                          pm, out, status);
+    MS_LAUNCH("k_label_tc(merge, conflicts)");
     return MS_OK;
 }
 
@@ -877,8 +946,8 @@ ms_status merge_tc_batch(const CUtensorMap& cmap, const CUtensorMap& cmap1, cons
     k_label_tc<LbBatchOld, kLbOld, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(cmap, mmap, cmap1, mmap1, om,
                                                                                      out, status);
     MS_LAUNCH("k_label_tc(merge, earlier modes)");
-    k_merge_old_fix_batch<Dp><<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, Xr, modes, frames, states, rank_cand, thr_f,
-                                                    thr, cand_state, removed_r);
+    k_merge_old_fix_batch<Dp><<<grid, 256, 0, st>>>(sc.fix, sc.fix_count, Xr, modes, frames, states, 0, rank_cand,
+                                                    thr_f, thr, cand_state, removed_r);
     MS_LAUNCH("k_merge_old_fix_batch");
     LbBatchPairs pm{frames, states, tile_off, B, 0};
     k_label_tc<LbBatchPairs, kLbPairs, Dp><<<grid, kLThreads, LbDim<Dp>::kSmemBytes, st>>>(cmap, cmap, cmap1, cmap1,
@@ -1003,6 +1072,17 @@ ms_status launch_merge_tc_batch(const CUtensorMap& cmap, const CUtensorMap& cmap
                     : merge_tc_batch<16>(cmap, cmap1, mmap, mmap1, Ck, rows, frames, states, B, max_pk_rows, Xr, modes,
                                          rank_cand, cand_state, removed_r, conf_deg, conf, thr_f, thr, tile_off, sc,
                                          grid, status, st);
+}
+
+ms_status launch_merge_tc_single(void* Ck, void* Mk, int64_t n_pad, int Dp, int k, int K_old, const float* Xr,
+                                 const float* modes, const int32_t* rank_cand, uint8_t* cand_state, uint8_t* removed_r,
+                                 int32_t* conf_deg, int32_t* conf, float thr_f, double thr, LabelTcScratch sc,
+                                 int grid, int* status, cudaStream_t st) {
+    if (k <= 0) return MS_OK;
+    return Dp == 32 ? merge_tc_single<32>(Ck, Mk, n_pad, k, K_old, Xr, modes, rank_cand, cand_state, removed_r,
+                                          conf_deg, conf, thr_f, thr, sc, grid, status, st)
+                    : merge_tc_single<16>(Ck, Mk, n_pad, k, K_old, Xr, modes, rank_cand, cand_state, removed_r,
+                                          conf_deg, conf, thr_f, thr, sc, grid, status, st);
 }
 
 ms_status launch_cover_tc_batch(const CUtensorMap& pmap, const CUtensorMap& mmap, const CUtensorMap& pmap1,

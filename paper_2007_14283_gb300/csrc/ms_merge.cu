@@ -68,6 +68,21 @@ __global__ void k_rank_invert(const int32_t* __restrict__ cand_rank, int k, int3
     if (a < k) rank_cand[cand_rank[a]] = a;
 }
 
+// k_rank_invert that also copies each candidate's position to its rank's row
+// of Xr (the BF16 form's tensor-core merge reads the candidates in rank order).
+template <int Dp>
+__global__ void k_rank_invert_xr(const int32_t* __restrict__ cand_rank, int k, const int32_t* __restrict__ cand,
+                                 const float* __restrict__ X, int32_t* __restrict__ rank_cand, float* __restrict__ Xr) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= k) return;
+    const int r = cand_rank[a];
+    rank_cand[r] = a;
+    const float4* src = reinterpret_cast<const float4*>(X + (int64_t)cand[a] * Dp);
+    float4* dst = reinterpret_cast<float4*>(Xr + (int64_t)r * Dp);
+#pragma unroll
+    for (int q = 0; q < Dp / 4; ++q) dst[q] = src[q];
+}
+
 template <int Dp>
 __device__ __forceinline__ void load_vec(float* dst, const float* src) {
 #pragma unroll
@@ -161,7 +176,7 @@ k_merge_pairs(const float* __restrict__ X, const int32_t* __restrict__ cand, int
 template <int Dp>
 __global__ void __launch_bounds__(kMT)
 k_merge_resolve(const float* __restrict__ X, const int32_t* __restrict__ cand, int k,
-                const int32_t* __restrict__ cand_rank, uint8_t* cand_state,
+                const int32_t* __restrict__ cand_rank, const int32_t* __restrict__ rank_cand, uint8_t* cand_state,
                 const int32_t* __restrict__ conf_deg, const int32_t* __restrict__ conf,
                 float thr_f, double thr, DevCounters* dc) {
     const int a = blockIdx.x * kMT + threadIdx.x;
@@ -180,11 +195,13 @@ k_merge_resolve(const float* __restrict__ X, const int32_t* __restrict__ cand, i
             if (s == kUndecided) all_removed = false;
         }
     } else {
+        // more conflicts than were stored: test the candidates ranked above
+        // this one again, in rank order
         float x[Dp];
         load_vec<Dp>(x, X + (int64_t)cand[a] * Dp);
         const int ra = cand_rank[a];
-        for (int b = 0; b < k; ++b) {
-            if (cand_rank[b] >= ra) continue;
+        for (int rb = 0; rb < ra; ++rb) {
+            const int b = rank_cand[rb];
             const uint8_t s = st[b];
             if (s == kRemoved) continue;
             if (!cos_at_least<Dp>(x, X + (int64_t)cand[b] * Dp, thr_f, thr)) continue;
@@ -385,6 +402,19 @@ ms_status merge_prepare_t(ms_ctx* ctx, int32_t k) {
     k_rank<<<dim3(g256, inner_slices((int)g256, k, ctx->num_sms)), 256, 0, ctx->stream>>>(
         ctx->cand, k, ctx->support, ctx->seed_order, ctx->cand_rank);
     MS_LAUNCH("k_rank");
+    if (ctx->Ck) {  // BF16 form: both contractions of the merge on the tensor cores
+        MS_CUDA(cudaMemsetAsync(ctx->removed_r, 0, (size_t)k, ctx->stream));
+        k_rank_invert_xr<Dp><<<g256, 256, 0, ctx->stream>>>(ctx->cand_rank, k, ctx->cand, ctx->X, ctx->rank_cand,
+                                                             ctx->Xr);
+        MS_LAUNCH("k_rank_invert_xr");
+        LabelTcScratch sc{ctx->label_fix, (int*)(ctx->label_fix + ctx->n), nullptr};
+        const ms_status s = launch_merge_tc_single(ctx->Ck, ctx->Mk, ctx->n_pad, Dp, k, ctx->n_kept, ctx->Xr,
+                                                   ctx->modes, ctx->rank_cand, ctx->cand_state, ctx->removed_r,
+                                                   ctx->conf_deg, ctx->conf, thr_f, thr, sc, ctx->num_sms,
+                                                   &ctx->dc->status, ctx->stream);
+        ctx->launches += 4 + (ctx->n_kept > 0 ? 2 : 0);
+        return s;
+    }
     k_rank_invert<<<g256, 256, 0, ctx->stream>>>(ctx->cand_rank, k, ctx->rank_cand);
     MS_LAUNCH("k_rank_invert");
     if (ctx->n_kept > 0) {
@@ -425,11 +455,11 @@ ms_status launch_merge_resolve(ms_ctx* ctx, int32_t k, int sweeps) {
         MS_CUDA(cudaMemsetAsync(&ctx->dc->undecided, 0, sizeof(int32_t), ctx->stream));
         if (ctx->Dp == 16)
             k_merge_resolve<16><<<gm, kMT, 0, ctx->stream>>>(ctx->X, ctx->cand, k, ctx->cand_rank,
-                                                             ctx->cand_state, ctx->conf_deg, ctx->conf,
+                                                             ctx->rank_cand, ctx->cand_state, ctx->conf_deg, ctx->conf,
                                                              thr_f, thr, ctx->dc);
         else
             k_merge_resolve<32><<<gm, kMT, 0, ctx->stream>>>(ctx->X, ctx->cand, k, ctx->cand_rank,
-                                                             ctx->cand_state, ctx->conf_deg, ctx->conf,
+                                                             ctx->rank_cand, ctx->cand_state, ctx->conf_deg, ctx->conf,
                                                              thr_f, thr, ctx->dc);
         MS_LAUNCH("k_merge_resolve");
         ctx->launches += 1;

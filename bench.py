@@ -925,6 +925,17 @@ def run_ours(args, rank, ws, local):
                     "value": 1.0 / (sdt1 / ssi1 * per_frame), "cores": 1,
                     "sample": f"{args.cpu_seeds // 8} seeds ({ssi1} seed-iterations, {sdt1:.1f} s) on one core, "
                               f"scaled likewise"}
+            # the small single-frame configuration (64 x 64, 4096 unit vectors, 8 vMF clusters), whole
+            import synth
+            c1 = synth.frame_c1(seed=0)
+            c1_runs = []
+            for _ in range(3):
+                t1 = time.perf_counter()
+                oracle.run(c1.emb)
+                c1_runs.append(time.perf_counter() - t1)
+            cpu["c1_frame"] = {"seconds_per_frame": statistics.median(c1_runs), "runs": 3, "cores": host_threads(),
+                               "sample": "one 64x64 frame (4096 pixels, d=16, 8 vMF clusters), every step of the "
+                                         "method in FP64; median of 3"}
             match, how, err, bg_ok = label_match(main.labels[0].cpu().numpy(), ref.labels, main.modes(0),
                                                  ref.modes)
             parity = {"frame": 0, "label_match": match, "method": how, "mode_err_max": err,

@@ -653,11 +653,17 @@ __global__ void k_b_collect(const BFrame* __restrict__ frames, BState* states, i
 
 // Rank in (support desc, seed order asc): block (candidate block, slice) adds
 // its partial count of candidates ahead (ranks start at 0, k_b_merge_zero).
+// A candidate is ahead of another exactly when its key support * 2^32 +
+// (2^32 - 1 - order) is larger (seed orders are distinct within a frame).
+__device__ __forceinline__ unsigned long long rank_key(int32_t support, int32_t order) {
+    return ((unsigned long long)(uint32_t)support << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)order);
+}
+
 __global__ void k_b_rank(const BFrame* __restrict__ frames, const BState* __restrict__ states, int B,
                          const int32_t* __restrict__ off, const int32_t* __restrict__ cand,
                          const int32_t* __restrict__ support, const int32_t* __restrict__ order,
                          int32_t* __restrict__ cand_rank) {
-    __shared__ int32_t s_sup[kMT], s_ord[kMT];
+    __shared__ unsigned long long s_key[kMT];
     const int S = off[B + 1];
     for (int bb = blockIdx.x; bb < off[B]; bb += gridDim.x) {
         const int f = locate(off, B, bb);
@@ -666,22 +672,15 @@ __global__ void k_b_rank(const BFrame* __restrict__ frames, const BState* __rest
         const int k = states[f].dc.n_cand;
         const int a = (lb / S) * kMT + threadIdx.x;
         const int lo = (int)((int64_t)sl * k / S), hi = (int)((int64_t)(sl + 1) * k / S);
-        int sa = 0, oa = 0;
-        if (a < k) {
-            sa = support[cand[base + a]];
-            oa = order[cand[base + a]];
-        }
+        const unsigned long long ka = a < k ? rank_key(support[cand[base + a]], order[cand[base + a]]) : 0ull;
         int r = 0;
         for (int t0 = lo; t0 < hi; t0 += kMT) {
             const int j = t0 + threadIdx.x;
             __syncthreads();
-            if (j < hi) {
-                s_sup[threadIdx.x] = support[cand[base + j]];
-                s_ord[threadIdx.x] = order[cand[base + j]];
-            }
+            if (j < hi) s_key[threadIdx.x] = rank_key(support[cand[base + j]], order[cand[base + j]]);
             __syncthreads();
             const int lim = min(kMT, hi - t0);
-            for (int q = 0; q < lim; ++q) r += (s_sup[q] > sa) || (s_sup[q] == sa && s_ord[q] < oa);
+            for (int q = 0; q < lim; ++q) r += s_key[q] > ka;
         }
         if (a < k && r) atomicAdd(&cand_rank[base + a], r);
         __syncthreads();

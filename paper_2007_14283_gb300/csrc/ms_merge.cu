@@ -36,28 +36,26 @@ __global__ void k_collect(const uint8_t* __restrict__ sstate, int m, int32_t* __
 
 // Rank of every candidate in (support desc, seed order asc): the count of
 // candidates ahead of it. Block (x, y) counts candidate block x against slice y
-// of all candidates and adds its partial count (ranks start at 0).
+// of all candidates and adds its partial count (ranks start at 0). A candidate
+// is ahead of another exactly when its key support * 2^32 + (2^32 - 1 - order)
+// is larger (seed orders are distinct within a frame).
+__device__ __forceinline__ unsigned long long rank_key(int32_t support, int32_t order) {
+    return ((unsigned long long)(uint32_t)support << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)order);
+}
+
 __global__ void k_rank(const int32_t* __restrict__ cand, int k, const int32_t* __restrict__ support,
                        const int32_t* __restrict__ order, int32_t* __restrict__ cand_rank) {
-    __shared__ int32_t s_sup[256], s_ord[256];
+    __shared__ unsigned long long s_key[256];
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    int sa = 0, oa = 0;
-    if (a < k) {
-        sa = support[cand[a]];
-        oa = order[cand[a]];
-    }
+    const unsigned long long ka = a < k ? rank_key(support[cand[a]], order[cand[a]]) : 0ull;
     const int lo = (int)((int64_t)blockIdx.y * k / gridDim.y), hi = (int)((int64_t)(blockIdx.y + 1) * k / gridDim.y);
     int r = 0;
     for (int base = lo; base < hi; base += 256) {
         const int b = base + threadIdx.x;
-        if (b < hi) {
-            s_sup[threadIdx.x] = support[cand[b]];
-            s_ord[threadIdx.x] = order[cand[b]];
-        }
+        if (b < hi) s_key[threadIdx.x] = rank_key(support[cand[b]], order[cand[b]]);
         __syncthreads();
         const int lim = min(256, hi - base);
-        for (int j = 0; j < lim; ++j)
-            r += (s_sup[j] > sa) || (s_sup[j] == sa && s_ord[j] < oa);
+        for (int j = 0; j < lim; ++j) r += s_key[j] > ka;
         __syncthreads();
     }
     if (a < k && r) atomicAdd(&cand_rank[a], r);

@@ -59,7 +59,8 @@ typedef int32_t ms_status;
 
 #define MS_FP32 0 /* plain FP32 SIMT similarity and sums */
 #define MS_BF16 1 /* BF16 tensor-core GEMMs with FP32 accumulation and an FP32 recheck band (the
-                     shift for any dim; labelling on the tensor cores for dim <= 16, else FP32) */
+                     shift, coverage, labelling and, in batches and single frames, the merge's
+                     two contractions; every decision equal to the FP32 form's) */
 
 #define MS_MAX_DIM 32
 
@@ -82,7 +83,8 @@ typedef struct ms_config {
     uint64_t frame_id;
     int32_t precision;    /* MS_FP32 or MS_BF16 */
     int32_t max_rounds;   /* guard on OSOP rounds; default 1000000 */
-    double eps_band;      /* BF16 recheck band half-width; 0 = the library's proven bound */
+    double eps_band;      /* reserved, 0: the BF16 recheck band is the library's derived bound
+                             (2^-14 around c; other values are ignored) */
     int32_t all_seeds;    /* 1 = Algorithm 1: every pixel seeds a single round, gamma = 1 */
     int32_t batch_split;  /* ms_batch_* only: 0 = each frame split into work items as on its own
                              (results bit-identical to ms_run on that frame); 1 = the batch's

@@ -396,21 +396,29 @@ k_label_tc(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUt
                 const int b = g % kLSBufs;
                 if (!(ok = lwarp_wait(&s_full[b], (g / kLSBufs) & 1, abort))) break;
                 tc_fence_after();
+                // A full slice of 32 columns gets its per-lane maximum from the
+                // TMEM load itself; the last, partial slice of an item masks its
+                // padding columns (scores of zero rows) and takes the maximum here.
                 uint32_t v[32];
-                tmem_ld32(tmem + b * 128 + lane_base + h * 32, v);
+                float m;
+                const int col0 = ii.k0 + mt * 128 + h * 32;
+                const bool partial = col0 + 32 > ii.K;  // warp-uniform
+                if (partial)
+                    tmem_ld32(tmem + b * 128 + lane_base + h * 32, v);
+                else
+                    tmem_ld32_max(tmem + b * 128 + lane_base + h * 32, v, &m);
                 tmem_ld_wait();
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&s_empty[b]);
-                const int col0 = ii.k0 + mt * 128 + h * 32;
-                if (col0 + 32 > ii.K) {
+                if (partial) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
                         if (col0 + j >= ii.K) v[j] = 0xFF800000u;  // -inf: past the last mode
-                }
-                float m = __uint_as_float(v[0]);
+                    m = __uint_as_float(v[0]);
 #pragma unroll
-                for (int j = 1; j < 32; ++j) m = fmaxf(m, __uint_as_float(v[j]));
+                    for (int j = 1; j < 32; ++j) m = fmaxf(m, __uint_as_float(v[j]));
+                }
                 if (kCover) {
                     b1 = fmaxf(b1, m);
                     continue;

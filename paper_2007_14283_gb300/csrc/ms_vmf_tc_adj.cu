@@ -4,7 +4,7 @@
 // For one step x -> x' = y/|y| with y_m = sum_i w_mi p_i and
 // w_mi = exp(kappa (x_m.p_i - 1)) (Eq. 2 with the exponential profile, the
 // dense update of Sec. 3.2.1), and with gy_m = (g_m - x'_m (x'_m.g_m))/|y_m|
-// from the upstream gradient g = dL/dx' (k_vmf_gy):
+// from the upstream gradient g = dL/dx' (formed by k_vmf_adj_link):
 //     a_mi  = gy_m . p_i,   ds_mi = kappa w_mi a_mi,
 //     pass A   dL/dx_m  = sum_i ds_mi p_i                 rows: seeds,  columns: pixels
 //     pass B   dL/dp_i += sum_m w_mi gy_m + ds_mi x_m      rows: pixels, columns: seeds

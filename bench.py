@@ -104,13 +104,22 @@ def barrier(ws):
 
 
 def reduce_over_ranks(v, ws, op):
+    """max or sum of a scalar over the ranks (a CPU tensor under gloo)."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def whole_job_rate(units, seconds, ws):
+    """Replicas' whole-job throughput: the units all ranks processed over the
+    slowest rank's time. Returns (rate, slowest time)."""
+    t = reduce_over_ranks(seconds, ws, "max")
+    return reduce_over_ranks(units, ws, "sum") / t, t
 
 
 class Clocks:
@@ -195,9 +204,16 @@ def shift_traffic_per_unit(kernel):
     return None
 
 
+def frame_seeds(rank, B):
+    """Seeds of the B frames a rank clusters; ranks' shards are disjoint."""
+    if not 0 <= B <= 1000:
+        raise ValueError("at most 1000 frames per rank keep the ranks' seeds disjoint")
+    return [rank * 1000 + i for i in range(B)]
+
+
 def c2_frames(rank, B):
     import synth
-    return [synth.frame_c2(seed=rank * 1000 + i) for i in range(B)]
+    return [synth.frame_c2(seed=s) for s in frame_seeds(rank, B)]
 
 
 def c2_seed_iters_per_frame():
@@ -812,7 +828,7 @@ def e2e_leg(args, runner, ws):
         one()
         walls.append(1e3 * (time.perf_counter() - w0))
     torch.cuda.synchronize()
-    t = reduce_over_ranks(time.perf_counter() - t0, ws, "max")
+    value, _ = whole_job_rate(args.e2e_steps * len(frames), time.perf_counter() - t0, ws)
     # one device-resident step right after, on the same clock state: the
     # difference to the host-buffer steps is the copies' share
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -822,7 +838,6 @@ def e2e_leg(args, runner, ws):
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    value = reduce_over_ranks(args.e2e_steps * len(frames), ws, "sum") / t
     assert torch.equal(h_labels[0], runner.labels[0].cpu()), "host-buffer run disagrees with the device run"
     api = "ms_batch_run_host" if runner.batched else "ms_run_host"
     return {"value": value, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -863,8 +878,7 @@ def run_ours(args, rank, ws, local):
     clocks.start()
     step_ms, tot = timed(main, args.steps, args.warmup, ws, flush, stream)
     clk = clocks.stop()
-    t_total = reduce_over_ranks(sum(step_ms) / 1e3, ws, "max")
-    value = reduce_over_ranks(tot["frames"], ws, "sum") / t_total
+    value, t_total = whole_job_rate(tot["frames"], sum(step_ms) / 1e3, ws)
     roofline = roofline_of(args.form, tot, step_ms, clk, n_sm)
     forms = {args.form: {"value": value, "frames_per_step": args.frames, "steps": args.steps,
                          "ms_per_frame": sum(step_ms) / max(1, tot["frames"]),
@@ -878,7 +892,7 @@ def run_ours(args, rank, ws, local):
         c_clocks.start()
         sm_, tt = timed(r, args.compare_steps, 1, ws, flush, stream)
         c_clk = c_clocks.stop()
-        v = reduce_over_ranks(tt["frames"], ws, "sum") / reduce_over_ranks(sum(sm_) / 1e3, ws, "max")
+        v, _ = whole_job_rate(tt["frames"], sum(sm_) / 1e3, ws)
         rf = roofline_of(other, tt, sm_, c_clk, n_sm)
         same = all(torch.equal(a, b) for a, b in zip(r.labels, main.labels)) if other.split("-")[0] == \
             args.form.split("-")[0] else None

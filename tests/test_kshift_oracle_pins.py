@@ -39,7 +39,7 @@ def test_gaussian_hand_worked_and_wide_bandwidth_limit():
     rng = np.random.default_rng(0)
     P = rng.standard_normal((50, 3))
     X, _, _ = K.step(rng.standard_normal((4, 3)), P, K.EUCLID, K.GAUSSIAN, 1e8)
-    assert np.allclose(X, P.mean(axis=0), atol=1e-12)
+    assert np.allclose(X, P.mean(axis=0), rtol=0, atol=1e-12)
 
 
 def test_symmetric_configuration_is_a_fixed_point():
@@ -47,7 +47,7 @@ def test_symmetric_configuration_is_a_fixed_point():
     P = np.array([[1.0, 0.0], [-1.0, 0.0], [0.0, 0.7], [0.0, -0.7]]) + np.array([3.0, -2.0])
     for kind in (K.FLAT, K.EPANECHNIKOV, K.GAUSSIAN):
         X, _, _ = K.step(np.array([[3.0, -2.0]]), P, K.EUCLID, kind, 1.5)
-        assert np.allclose(X, [[3.0, -2.0]], atol=1e-15), kind
+        assert np.allclose(X, [[3.0, -2.0]], rtol=0, atol=1e-15), kind
 
 
 def test_flat_cosine_equals_the_c_oracle_window_mean():
@@ -65,7 +65,7 @@ def test_flat_cosine_equals_the_c_oracle_window_mean():
             continue
         assert n[m] == cnt
         if cnt:
-            assert np.allclose(X[m], xn, atol=1e-12)
+            assert np.allclose(X[m], xn, rtol=0, atol=1e-12)
 
 
 # Shadow profiles: weights g = k are the derivative -k_s' of the profile
@@ -98,3 +98,33 @@ def test_euclidean_steps_ascend_the_shadow_density(kind):
 def test_empty_window_keeps_the_seed():
     X, s, n = K.step(np.array([[10.0, 10.0]]), np.array([[0.0, 0.0], [1.0, 0.0]]), K.EUCLID, K.FLAT, 1.0)
     assert np.array_equal(X, [[10.0, 10.0]]) and s[0] == 0 and n[0] == 0
+
+
+def test_flat_window_includes_its_boundary():
+    # Eq. 3's flat kernel counts t <= 1: from x = 0 with h = 1 the vector at
+    # distance exactly 1 is in the window (dyadic values, t = 1 exactly)
+    X, s, n = K.step(np.array([[0.0]]), np.array([[-0.5], [1.0], [1.5]]), K.EUCLID, K.FLAT, 1.0)
+    assert n[0] == 2 and X[0, 0] == 0.25
+
+
+def test_cosine_epanechnikov_hand_worked_2d():
+    # directions e1 and e2 given at lengths 2 and 3 (the cosine form
+    # normalises them), x = e1, h = 2: 1 - cos = 0 and 1, t = 0 and 1/4,
+    # w = 1 and 3/4, y = e1 + (3/4) e2, x' = (4, 3) / 5
+    P = np.array([[2.0, 0.0], [0.0, 3.0]])
+    X, s, n = K.step(np.array([[1.0, 0.0]]), P, K.COSINE, K.EPANECHNIKOV, 2.0)
+    assert np.allclose(X, [[0.8, 0.6]], rtol=0, atol=1e-15) and s[0] == pytest.approx(1.75, abs=1e-15)
+
+
+def test_run_takes_exactly_T_steps():
+    # Epanechnikov on 0 and 1 from 0.25 (h = 1): one step gives 7/22 (above);
+    # a second gives, with t = (7/22)^2 and (15/22)^2,
+    # x'' = w1 / (w0 + w1), w0 = 1 - 49/484, w1 = 1 - 225/484
+    P = np.array([[0.0], [1.0]])
+    x1, _ = K.run(P, np.array([[0.25]]), K.EUCLID, K.EPANECHNIKOV, 1.0, 1)
+    x2, _ = K.run(P, np.array([[0.25]]), K.EUCLID, K.EPANECHNIKOV, 1.0, 2)
+    assert x1[0, 0] == pytest.approx(7.0 / 22.0, abs=1e-15)
+    assert x2[0, 0] == pytest.approx((259.0 / 484.0) / (435.0 / 484.0 + 259.0 / 484.0), abs=1e-15)
+    # T = 0 returns the seeds, normalised for the cosine distance
+    x0, _ = K.run(np.array([[1.0, 0.0]]), np.array([[3.0, 4.0]]), K.COSINE, K.FLAT, 0.5, 0)
+    assert np.allclose(x0, [[0.6, 0.8]], rtol=0, atol=1e-15)

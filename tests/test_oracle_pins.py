@@ -63,8 +63,8 @@ def test_normalize_compacts_and_unit_norms():
     mask = (rng.uniform(size=50) < 0.5).astype(np.uint8)
     P, pn, idx = oracle.normalize(emb, mask)
     assert idx.tolist() == np.flatnonzero(mask).tolist()
-    assert np.allclose(np.linalg.norm(P, axis=1), 1.0, atol=1e-15)
-    assert np.allclose(pn, 1.0, atol=1e-15)
+    assert np.allclose(np.linalg.norm(P, axis=1), 1.0, rtol=0, atol=1e-15)
+    assert np.allclose(pn, 1.0, rtol=0, atol=1e-15)
     # direction preserved
     e = emb[idx].astype(np.float64)
     assert np.allclose(P * np.linalg.norm(e, axis=1, keepdims=True), e, rtol=1e-14, atol=1e-14)
@@ -96,7 +96,7 @@ def test_window_listed_by_hand_d2():
     xn, cnt, _ = oracle.shift_step(P, pn, [1.0, 0.0], c)
     assert cnt == 4
     s = P[[0, 1, 2, 3]].sum(axis=0)
-    assert np.allclose(xn, s / np.linalg.norm(s), atol=1e-15)
+    assert np.allclose(xn, s / np.linalg.norm(s), rtol=0, atol=1e-15)
 
 
 def test_window_boundary_is_inclusive_eq11():
@@ -128,7 +128,7 @@ def test_one_cluster_single_step_fixed_point():
     for s in (0, 17, 39):
         traj, counts, T = oracle.trajectory(P, np.linalg.norm(P, axis=1), P[s], 0.9)
         assert T == 2 and counts.tolist() == [40, 40]
-        assert np.allclose(traj[1], want, atol=1e-15)
+        assert np.allclose(traj[1], want, rtol=0, atol=1e-15)
         assert np.array_equal(traj[2], traj[1])
 
 
@@ -147,7 +147,7 @@ def test_objective_monotone_along_trajectories():
         traj, counts, T = oracle.trajectory(P, pn, P[s], 0.9)
         F = [_F(P, x, 0.9) for x in traj]
         assert all(F[i + 1] >= F[i] - 1e-12 for i in range(len(F) - 1))
-        assert np.allclose(np.linalg.norm(traj[1:], axis=1), 1.0, atol=1e-12)
+        assert np.allclose(np.linalg.norm(traj[1:], axis=1), 1.0, rtol=0, atol=1e-12)
 
 
 def test_round_early_stop_matches_trajectories():
@@ -187,7 +187,7 @@ def test_merge_order_and_threshold_by_hand():
     cand = _ring([0, 10, 30, 80])
     kept, src, _ = oracle.merge(cand, [5, 9, 1, 1], [0, 1, 2, 3], 0.9)
     assert src.tolist() == [1, 3]
-    assert np.allclose(kept, cand[[1, 3]])
+    assert np.array_equal(kept, cand[[1, 3]])
     # equal supports: earlier seed order wins
     kept, src, _ = oracle.merge(_ring([0, 5]), [4, 4], [7, 3], 0.9)
     assert src.tolist() == [1]
@@ -280,7 +280,7 @@ def test_paper_orthogonal_blob_design_modes_are_cluster_means():
     for k in range(10):
         members = r.labels == k
         s = P[members].sum(axis=0)
-        assert np.allclose(r.modes[k], s / np.linalg.norm(s), atol=1e-13)
+        assert np.allclose(r.modes[k], s / np.linalg.norm(s), rtol=0, atol=1e-13)
         assert r.support[k] == members.sum()
 
 
@@ -311,7 +311,7 @@ def test_fixed_points_on_fragmented_frame():
         assert np.abs(xn - r.modes[k]).max() <= 1e-12
         checked += 1
     assert checked > 0.95 * r.modes.shape[0]
-    assert np.allclose(np.linalg.norm(r.modes, axis=1), 1.0, atol=1e-12)
+    assert np.allclose(np.linalg.norm(r.modes, axis=1), 1.0, rtol=0, atol=1e-12)
     # kept modes are pairwise farther apart than the merge threshold
     G = r.modes @ r.modes.T
     np.fill_diagonal(G, -1)

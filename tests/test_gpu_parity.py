@@ -200,7 +200,8 @@ def test_single_pixel(ms_lib):
     emb = np.array([[0.3, -2.0] + [0.0] * 14], np.float32)
     labels, modes, st = _run_gpu(ms_lib, emb)
     assert labels.tolist() == [0] and modes.shape[0] == 1
-    assert np.allclose(modes[0], emb[0] / np.linalg.norm(emb[0]), atol=1e-7)
+    # normalised in FP32 at ingest and again by the shift: a few units in the last place
+    assert np.allclose(modes[0], emb[0] / np.linalg.norm(emb[0]), rtol=0, atol=5e-7)
 
 
 def test_deterministic_repeat(ms_lib):

@@ -31,7 +31,7 @@ def test_vmf_forward_matches_fp64(ms_lib, N, M, T):
     XT = ms_lib.ms_vmf_forward(P.cuda(), X0.cuda(), 20.0, T)
     ref = vmf_ref.vmf_forward(P.double(), X0.double(), 20.0, T)
     assert (XT.cpu().double() - ref).abs().max().item() <= 1e-5
-    assert torch.allclose(XT.norm(dim=1).cpu().double(), torch.ones(M, dtype=torch.float64), atol=1e-6)
+    assert torch.allclose(XT.norm(dim=1).cpu().double(), torch.ones(M, dtype=torch.float64), rtol=0, atol=1e-6)
 
 
 @pytest.mark.parametrize("N,M,T", [(4096, 64, 10), (3000, 37, 3)])
@@ -122,7 +122,7 @@ def test_vmf_bf16_forward_matches_fp64(ms_lib, N, M, T):
     XT = ms_lib.ms_vmf_forward(P.cuda(), X0.cuda(), 20.0, T, precision=ms_lib.MS_BF16)
     ref = vmf_ref.vmf_forward(P.double(), X0.double(), 20.0, T)
     assert (XT.cpu().double() - ref).abs().max().item() <= BF16_TOL
-    assert torch.allclose(XT.norm(dim=1).cpu().double(), torch.ones(M, dtype=torch.float64), atol=1e-6)
+    assert torch.allclose(XT.norm(dim=1).cpu().double(), torch.ones(M, dtype=torch.float64), rtol=0, atol=1e-6)
 
 
 def test_vmf_bf16_c5_full_config(ms_lib):

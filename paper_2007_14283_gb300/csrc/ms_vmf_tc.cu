@@ -392,11 +392,8 @@ VmfTcPlan vmf_tc_plan(int32_t M, int64_t N, int grid) {
 size_t vmf_tc_pk_bytes(int64_t N) { return (size_t)((N + 127) / 128 * 128) * 128; }
 
 ms_status vmf_tc_prepare(const float* P, int64_t N, void* Pk, CUtensorMap* map, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        MS_CUDA(cudaFuncSetAttribute(k_vmf_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kVSmemBytes));
-        attr = true;
-    }
+    // per call: the attribute belongs to the current device
+    MS_CUDA(cudaFuncSetAttribute(k_vmf_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kVSmemBytes));
     const int64_t rows = (N + 127) / 128 * 128;
     k_vmf_tc_pack<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P, N, rows, (uint4*)Pk);
     MS_LAUNCH("k_vmf_tc_pack");

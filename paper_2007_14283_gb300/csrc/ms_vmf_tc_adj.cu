@@ -558,12 +558,9 @@ size_t vmf_adj_bytes(int32_t M, int64_t N, int grid) {
 }
 
 ms_status vmf_adj_prepare(void* Pk, int64_t N, int32_t M, int grid, void* ws, VmfAdjWork* w) {
-    static bool attr = false;
-    if (!attr) {
-        MS_CUDA(cudaFuncSetAttribute(k_vmf_adj_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmemBytes));
-        MS_CUDA(cudaFuncSetAttribute(k_vmf_adj_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmemBytes));
-        attr = true;
-    }
+    // per call: the attribute belongs to the current device
+    MS_CUDA(cudaFuncSetAttribute(k_vmf_adj_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmemBytes));
+    MS_CUDA(cudaFuncSetAttribute(k_vmf_adj_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmemBytes));
     w->M = M;
     w->N = N;
     w->Mp = (M + 127) / 128 * 128;

@@ -123,11 +123,14 @@ typedef struct ms_stats {
     double shift_ms;       /* their summed CUDA-event time (profiling on) */
 } ms_stats;
 
-/* Fill *cfg with the paper's defaults (h = 0.1, gamma = 0.9, N_initial = 128,
- * L = 2, H = 8, P = 0.99) for dimension 16 and MS_FP32. */
+/* Fill *cfg with the paper's defaults for dimension 16 and MS_FP32: h = 0.1
+ * (Sec. 4.2 and 4.3), gamma = 0.9 (Sec. 3.2.3), N_initial = 128, L = 2 and
+ * H = 8 (Sec. 3.2.4), P = 0.99 (Eq. 19). Cannot fail. */
 MS_API void ms_config_default(ms_config* cfg);
 
-/* Message describing the last failure on the calling thread ("" if none). */
+/* Message describing the last failure on the calling thread ("" if none).
+ * No counterpart in the paper. Cannot fail; the string is thread-local and is
+ * overwritten by the thread's next failing call. */
 MS_API const char* ms_last_error(void);
 
 /* Testing hook for the allocation-failure path (no counterpart in the paper):
@@ -136,7 +139,10 @@ MS_API const char* ms_last_error(void);
  * calling it; nothing is left allocated. count <= 0 clears it. */
 MS_API void ms_inject_alloc_failure(int32_t count);
 
-/* Device bytes ms_create would allocate for n_pixels pixels with cfg. */
+/* Device bytes ms_create would allocate for n_pixels pixels with cfg (no
+ * counterpart in the paper; the layout is the one in ms_create). Allocates
+ * nothing. MS_ERR_INVALID_ARG for a bad cfg, a NULL bytes_out or n_pixels
+ * outside [0, 2^24). */
 MS_API ms_status ms_workspace_bytes(const ms_config* cfg, int64_t n_pixels, int64_t* bytes_out);
 
 /* Bind a frame (the vector set S of Algorithm 2) and allocate the workspace.
@@ -181,19 +187,28 @@ MS_API ms_status ms_merge_modes(ms_ctx* ctx, int32_t* n_modes_out, int64_t* n_un
 MS_API ms_status ms_label(ms_ctx* ctx, int32_t* d_labels_out, float* d_modes_out, int32_t cap,
                    int32_t* n_modes_out);
 
-/* Free the workspace. Accepts NULL. */
+/* Free the workspace (no counterpart in the paper). Synchronises the
+ * context's stream first. Accepts NULL; cannot fail. */
 MS_API void ms_destroy(ms_ctx* ctx);
 
-/* The whole method for the bound frame: OSOP rounds (seed, iterate, merge)
- * until every foreground pixel is covered or max_rounds, then ms_label. */
+/* The whole method for the bound frame (Algorithm 2): OSOP rounds (seed,
+ * iterate, merge) until every foreground pixel is covered or max_rounds, then
+ * ms_label. A round in which no seed converged is not an error here (its
+ * batch is consumed and the next round starts), nor is stopping at
+ * max_rounds (ms_stats.uncovered > 0 then). Errors: MS_ERR_INVALID_ARG for a
+ * NULL ctx, MS_ERR_STATE while a seed batch is pending, otherwise those of
+ * ms_seed_batch, ms_iterate, ms_merge_modes and ms_label. */
 MS_API ms_status ms_run(ms_ctx* ctx, int32_t* d_labels_out, float* d_modes_out, int32_t cap,
                  int32_t* n_modes_out);
 
-/* Record CUDA events around every shift-kernel launch on the context's
- * stream (enable = 1) so ms_stats reports its device time; off by default. */
+/* Measurement only (no counterpart in the paper): record CUDA events around
+ * every shift-kernel launch on the context's stream (enable = 1) so ms_stats
+ * reports its device time; off by default. MS_ERR_INVALID_ARG for a NULL ctx,
+ * MS_ERR_CUDA if the events cannot be created. */
 MS_API ms_status ms_profile(ms_ctx* ctx, int32_t enable);
 
-/* Counters of the context so far. */
+/* Counters of the context so far (no counterpart in the paper). Does not
+ * synchronise. MS_ERR_INVALID_ARG for a NULL argument. */
 MS_API ms_status ms_stats_get(const ms_ctx* ctx, ms_stats* out);
 
 /* OSOP state carried across frames of a video (Sec. 3.2.4; Sec. 4.3, Table 3):
@@ -203,13 +218,16 @@ MS_API ms_status ms_stats_get(const ms_ctx* ctx, ms_stats* out);
  * at the frame's end), and is bounded by the largest seed batch the frame drew
  * (no frame can use more seeds than it has uncovered pixels). ms_set_state
  * sets the frame's starting N; it returns MS_ERR_STATE once the frame's first
- * round has run. */
+ * round has run. MS_ERR_INVALID_ARG for a NULL argument or (ms_set_state)
+ * n_next < 1. */
 MS_API ms_status ms_get_state(const ms_ctx* ctx, int64_t* n_next_out);
 MS_API ms_status ms_set_state(ms_ctx* ctx, int64_t n_next);
 
-/* Copy an internal array to host memory for inspection (tests, debugging).
- * what: MS_INSPECT_* below. Writes min(cap, available) elements to h_out and
- * the available count to *count_out. Synchronises the stream. */
+/* Copy an internal array to host memory for inspection (tests, debugging;
+ * no counterpart in the paper). what: MS_INSPECT_* below. Writes min(cap,
+ * available) elements to h_out and the available count to *count_out.
+ * Synchronises the stream. MS_ERR_INVALID_ARG for a NULL ctx, a NULL h_out
+ * with cap > 0 or an unknown code; MS_ERR_CUDA if a copy fails. */
 #define MS_INSPECT_SEED_LOG 1  /* int32: foreground index of every seed in draw order */
 #define MS_INSPECT_MODES 2     /* float32 [K, dim]: kept modes in keep order */
 #define MS_INSPECT_SUPPORT 3   /* int32 [K]: window size of each kept mode */
@@ -219,13 +237,17 @@ MS_API ms_status ms_set_state(ms_ctx* ctx, int64_t n_next);
 MS_API ms_status ms_inspect(const ms_ctx* ctx, int32_t what, void* h_out, int64_t cap,
                      int64_t* count_out);
 
-/* The whole method on one frame held in HOST memory: copies h_emb and h_mask
+/* The whole method (Algorithm 2) on one frame held in HOST memory: copies h_emb and h_mask
  * to the device, runs ms_create + ms_run, and copies labels (and modes, when
  * h_modes is not NULL) back, all on `stream`; returns after the copies end.
  * h_emb: float32 [n_pixels, cfg->dim]; h_mask: uint8 [n_pixels] or NULL;
  * h_labels: int32 [n_pixels]; h_modes: float32 [cap, dim] or NULL. Pinned
  * host buffers make the copies asynchronous. Allocates and frees its own
- * device memory. stats_out (nullable) receives the run's counters. */
+ * device memory. stats_out (nullable) receives the run's counters. Errors:
+ * MS_ERR_INVALID_ARG for a bad cfg, n_pixels outside [0, 2^24) or a NULL
+ * h_emb or h_labels with n_pixels > 0; MS_ERR_OOM if the device buffer cannot
+ * be allocated; otherwise those of ms_create and ms_run (nothing is copied
+ * back after a failure). */
 MS_API ms_status ms_run_host(const ms_config* cfg, const float* h_emb, const uint8_t* h_mask,
                              int64_t n_pixels, void* stream, int32_t* h_labels, float* h_modes,
                              int32_t cap, int32_t* n_modes_out, ms_stats* stats_out);
@@ -304,7 +326,9 @@ MS_API ms_status ms_kernel_shift(const float* d_P, int64_t N, const float* d_X0,
  * h_S [128, n_pad] the raw accumulator Xh.Ph + Xh.Pm + Xl.Ph - c (c rounded
  * up to FP32; n_pad = n_pix rounded up to 128) and h_acc [128, 17] each seed's window
  * sums (units of 2^-36) and window size. 1 <= n_pix <= 4096. Allocates and
- * frees its own device memory; synchronises the device. */
+ * frees its own device memory; synchronises the device. MS_ERR_INVALID_ARG
+ * for NULL pointers or n_pix out of range, MS_ERR_TIMEOUT if a bounded wait
+ * inside the kernel gave up. */
 MS_API ms_status ms_tc_selftest(const float* d_X, const float* d_P, int32_t n_pix, double c, float* h_S,
                                 int64_t* h_acc);
 
@@ -454,7 +478,7 @@ MS_API ms_status ms_batch_modes(const ms_batch* b, int32_t frame, float* h_out, 
 MS_API void ms_batch_destroy(ms_batch* b);
 
 /* Work split and tile shape of a batch's shift launches (the autotuned
- * parameters): batch_split 0 gives every frame the single-frame split
+ * parameters; no counterpart in the paper): batch_split 0 gives every frame the single-frame split
  * (results equal ms_run's frame by frame; target_mult is then unused);
  * batch_split 1 shares target_mult x (shift grid) work items across the
  * iterating frames in proportion to their seed x pixel work (target_mult
@@ -467,7 +491,13 @@ MS_API void ms_batch_destroy(ms_batch* b);
  * (1, 4), (1, 8) on tc_shape 0; for a BF16 batch, phase 2 times tc_shapes
  * 1..7 on phase 1's fastest split. It keeps the fastest of all, runs it once
  * more so the batch's outputs come from it, and writes min(cap, 5 or 12)
- * results to `results` (host), in the order timed. */
+ * results to `results` (host), in the order timed. Both are for speed only
+ * (the paper fixes no work split): every tile shape gives the same results,
+ * and batch_split 0 equals ms_run frame by frame; batch_split 1 cuts each
+ * seed's window sums into other chunks, so its rounding may differ while it
+ * meets the same bar against the FP64 method. MS_ERR_INVALID_ARG for a NULL batch, batch_split not 0 or 1,
+ * target_mult outside 1..64, tc_shape outside 0..7, reps outside 1..100 or
+ * cap < 0; otherwise the errors of ms_batch_run with sync. */
 typedef struct ms_tune_result {
     int32_t batch_split;
     int32_t target_mult;

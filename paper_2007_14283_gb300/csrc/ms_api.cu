@@ -177,7 +177,7 @@ struct Layout {
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-Layout plan(int64_t np, int Dp, int target_items, bool bf16) {
+Layout plan(int64_t np, int Dp, bool bf16) {
     Layout L;
     const size_t n = (size_t)(np > 0 ? np : 1);
     const size_t sizes[] = {
@@ -282,8 +282,7 @@ ms_status ms_workspace_bytes(const ms_config* cfg, int64_t n_pixels, int64_t* by
     if (s != MS_OK) return s;
     if (!bytes_out || n_pixels < 0 || n_pixels >= (1LL << 24))
         return set_error(MS_ERR_INVALID_ARG, "n_pixels must be in [0, 2^24)");
-    const int grid = device_sms() * shift_blocks_per_sm();
-    *bytes_out = (int64_t)plan(n_pixels, padded_dim(cfg->dim), 2 * grid, cfg->precision == MS_BF16).total;
+    *bytes_out = (int64_t)plan(n_pixels, padded_dim(cfg->dim), cfg->precision == MS_BF16).total;
     return MS_OK;
 }
 
@@ -304,7 +303,7 @@ ms_status ctx_alloc(const ms_config* cfg, int64_t max_pixels, cudaStream_t strea
     ctx->num_sms = device_sms();
     ctx->shift_grid = ctx->num_sms * shift_blocks_per_sm();
     ctx->target_items = 2 * ctx->shift_grid;
-    const Layout L = plan(max_pixels, ctx->Dp, ctx->target_items, cfg->precision == MS_BF16);
+    const Layout L = plan(max_pixels, ctx->Dp, cfg->precision == MS_BF16);
     ctx->ws_bytes = L.total;
     cudaError_t e = workspace_malloc(&ctx->ws, L.total);
     if (e != cudaSuccess) {

@@ -35,6 +35,9 @@ MUTANTS = {
     "seeds_ignore_coverage": ("            if (covered[i]) continue;\n            covered[i] = 1;",
                               "            covered[i] = 1;"),
     "perm_offset_ignored": ("return (int64_t)((aj + (uint64_t)b) % (uint64_t)n);", "return (int64_t)(aj % (uint64_t)n);"),
+    "merge_keep_at_threshold": ("if (n_kept == 0 || best < merge_cos) {", "if (n_kept == 0 || best <= merge_cos) {"),
+    "schedule_double_at_edge": ("if ((double)N < L * nmin)", "if ((double)N <= L * nmin)"),
+    "schedule_shrink_at_edge": ("else if ((double)N > H * nmin)", "else if ((double)N >= H * nmin)"),
     "normalise_skipped": ("for (int32_t k = 0; k < dim; ++k) p[k] = (double)e[k] / nrm;",
                           "for (int32_t k = 0; k < dim; ++k) p[k] = (double)e[k];"),
 }

@@ -196,6 +196,17 @@ def test_merge_order_and_threshold_by_hand():
     assert kept.shape[0] == 2 and src.tolist() == [1]
 
 
+def test_merge_threshold_is_strict():
+    # a candidate is kept only when its cosine to every kept mode is below
+    # merge_cos: (1,1,1,1) and (1,1,1,-1) have cosine 2/4 = 1/2 exactly, so at
+    # merge_cos = 1/2 the second merges, and just above 1/2 it is kept
+    cand = np.array([[1.0, 1.0, 1.0, 1.0], [1.0, 1.0, 1.0, -1.0]])
+    _, src, _ = oracle.merge(cand, [2, 1], [0, 1], 0.5)
+    assert src.tolist() == [0]
+    _, src, _ = oracle.merge(cand, [2, 1], [0, 1], np.nextafter(0.5, 1.0))
+    assert src.tolist() == [0, 1]
+
+
 def test_cover_by_hand():
     P = _ring([0, 20, 40, 100])
     cov, left, _ = oracle.cover(P, np.ones(4), _ring([30]), np.zeros(4, np.uint8), c=math.cos(math.radians(12)))
@@ -265,6 +276,21 @@ def test_schedule_hand_worked_rows():
     assert len(rows) >= 10
     for N, I, unc, want in rows:
         assert oracle.next_n(int(N), int(I), int(unc)) == int(want), (N, I, unc)
+
+
+def test_schedule_bounds_are_strict():
+    # Eq. 21 doubles N only when it is below L N_min and subtracts N_min only
+    # when it is above H N_min: at N = L N_min (or H N_min) exactly, N stays.
+    # L is chosen as N / N_min where that product rounds back to N exactly.
+    I = 10
+    nm = oracle.nmin(I)
+    N = next(N for N in range(int(nm) + 2, int(nm) + 400) if (N / nm) * nm == N)
+    edge = N / nm
+    assert oracle.next_n(N, I, 10 ** 6, L=edge, H=1e9) == N
+    assert oracle.next_n(N, I, 10 ** 6, L=0.5, H=edge) == N
+    # one unit in the last place inside the band's edge, the rule acts
+    assert oracle.next_n(N, I, 10 ** 6, L=np.nextafter(edge, 2 * edge), H=1e9) == 2 * N
+    assert oracle.next_n(N, I, 10 ** 6, L=0.5, H=np.nextafter(edge, 0.0)) == N - math.ceil(nm)
 
 
 # ------------------------------------------------------- whole method

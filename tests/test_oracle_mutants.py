@@ -38,6 +38,24 @@ MUTANTS = {
     "merge_keep_at_threshold": ("if (n_kept == 0 || best < merge_cos) {", "if (n_kept == 0 || best <= merge_cos) {"),
     "schedule_double_at_edge": ("if ((double)N < L * nmin)", "if ((double)N <= L * nmin)"),
     "schedule_shrink_at_edge": ("else if ((double)N > H * nmin)", "else if ((double)N >= H * nmin)"),
+    "schedule_no_clamp": ("    if (nn > hi) nn = hi;\n", ""),
+    "background_zero": ("for (int64_t i = 0; i < n_pixels; ++i) labels[i] = -1;",
+                        "for (int64_t i = 0; i < n_pixels; ++i) labels[i] = 0;"),
+    "merge_least_similar": ("            if (cs > best) best = cs;\n        }\n        if (n_kept > 0) {",
+                            "            if (best == -INFINITY || cs < best) best = cs;\n        }\n        if (n_kept > 0) {"),
+    "perm_tie_upper_first": ("        if (lo >= 1 && lo <= n - 1 && gcd64(lo, n) == 1) { pick = lo; break; }\n"
+                             "        if (hi >= 1 && hi <= n - 1 && gcd64(hi, n) == 1) { pick = hi; break; }",
+                             "        if (hi >= 1 && hi <= n - 1 && gcd64(hi, n) == 1) { pick = hi; break; }\n"
+                             "        if (lo >= 1 && lo <= n - 1 && gcd64(lo, n) == 1) { pick = lo; break; }"),
+    "perm_golden_truncated": ("floor(0.6180339887 * (double)n + 0.5)", "floor(0.6180339887 * (double)n)"),
+    "seed_iters_count_idle_seeds": ("        si += active;", "        si += m;"),
+    "no_stop_when_none_moving": ("if ((double)nconv > gamma * (double)m || nmove == 0) break;",
+                                 "if ((double)nconv > gamma * (double)m) break;"),
+    "moving_seeds_offered": ("            if (sstate[s] != 1) {", "            if (sstate[s] == 2) {"),
+    "schedule_uses_round_modes": ("        N = or_next_n(N, n_kept, 1.0, cfg->P_target, L, cfg->H, uncovered);",
+                                  "        N = or_next_n(N, n_kept - k0, 1.0, cfg->P_target, L, cfg->H, uncovered);"),
+    "carry_unbounded": ("st.n_carry = n_free < max_draw ? n_free : max_draw;", "st.n_carry = n_free;"),
+    "all_seeds_keeps_gamma": ("const double gamma = cfg->all_seeds ? 1.0 : cfg->gamma;", "const double gamma = cfg->gamma;"),
     "normalise_skipped": ("for (int32_t k = 0; k < dim; ++k) p[k] = (double)e[k] / nrm;",
                           "for (int32_t k = 0; k < dim; ++k) p[k] = (double)e[k];"),
 }

@@ -56,6 +56,14 @@ def test_affine_permutation_is_bijection(n):
         assert p[0] == b
 
 
+def test_affine_step_tie_takes_the_lower_candidate():
+    # n = 16: round(0.618 * 16) = 10 shares the factor 2 with 16; at distance
+    # one both 9 and 11 are coprime, and the lower one is taken
+    assert oracle.perm_params(16)[0] == 9
+    # n = 10: 6 and 5 share a factor with 10, 7 does not
+    assert oracle.perm_params(10)[0] == 7
+
+
 # ------------------------------------------------------------ normalisation
 def test_normalize_compacts_and_unit_norms():
     rng = np.random.default_rng(0)
@@ -169,6 +177,9 @@ def test_round_early_stop_matches_trajectories():
         r = oracle.shift_round(P, pn, P[seeds], gamma=gamma)
         t_stop = next(t for t in range(1, 301) if (T <= t).sum() > gamma * m or (T <= t).sum() == m)
         assert r["sweeps"] == t_stop, gamma
+        # one seed-iteration per seed and sweep while it is active: a seed is
+        # shifted until it converges or the round stops
+        assert r["seed_iters"] == int(np.minimum(T, t_stop).sum()), gamma
         conv = r["state"] == 1
         assert np.array_equal(conv, T <= t_stop)
         assert np.array_equal(r["conv_iter"][conv], T[conv])
@@ -349,16 +360,22 @@ def test_osop_labels_equal_all_seeds_labels_when_separable():
     r_osop = oracle.run(f.emb)
     r_all = oracle.run(f.emb, all_seeds=1)
     assert r_all.stats["rounds"] == 1 and r_all.stats["seeds"] == 4096
+    # Algorithm 1 has no early stop: every seed is shifted to its mode
+    assert r_all.stats["dropped"] == 0 and r_all.stats["candidates"] == 4096
     assert r_osop.stats["seeds"] < 1000
     assert matched_agreement(r_all.labels, r_osop.labels) == 1.0
 
 
-def test_run_covers_every_pixel_and_schedule_follows_rule():
-    f = synth.frame_c1(seed=5)
-    r = oracle.run(f.emb)
+@pytest.mark.parametrize("separable,n_initial", [(False, 128), (True, 1)])
+def test_run_covers_every_pixel_and_schedule_follows_rule(separable, n_initial):
+    # Eq. 19-21 with I = every mode kept so far. The separable frame started
+    # from one seed keeps 1, 2, 4, 8 modes over its rounds: after round two,
+    # I = 2 doubles N where the single mode of that round alone would not.
+    f = synth.frame_c1_separable(seed=0) if separable else synth.frame_c1(seed=5)
+    r = oracle.run(f.emb, n_initial=n_initial)
     log = r.round_log
     assert log[-1, 3] == 0
-    assert log[0, 0] == 128
+    assert log[0, 0] == n_initial
     for i in range(1, log.shape[0]):
         want = oracle.next_n(log[i - 1, 0], log[i - 1, 2], log[i - 1, 3])
         assert log[i, 0] == want

@@ -56,6 +56,13 @@ MUTANTS = {
                                   "        N = or_next_n(N, n_kept - k0, 1.0, cfg->P_target, L, cfg->H, uncovered);"),
     "carry_unbounded": ("st.n_carry = n_free < max_draw ? n_free : max_draw;", "st.n_carry = n_free;"),
     "all_seeds_keeps_gamma": ("const double gamma = cfg->all_seeds ? 1.0 : cfg->gamma;", "const double gamma = cfg->gamma;"),
+    "mask_inverted": ("if (mask != NULL && mask[i] == 0) continue;", "if (mask != NULL && mask[i] != 0) continue;"),
+    "label_margin_stale_second": ("            if (cs > b1) {\n                b2 = b1;\n", "            if (cs > b1) {\n"),
+    "schedule_no_floor": ("    if (nn < 1) nn = 1;\n", ""),
+    "window_margin_ignored": ("            if (m < mm) mm = m;\n        }\n        if (cs >= c) {",
+                              "        }\n        if (cs >= c) {"),
+    "cover_margin_ignored": ("            double marg = fabs(best - c);\n            if (marg < mm) mm = marg;\n"
+                             "            if (best >= c) {", "            if (best >= c) {"),
     "normalise_skipped": ("for (int32_t k = 0; k < dim; ++k) p[k] = (double)e[k] / nrm;",
                           "for (int32_t k = 0; k < dim; ++k) p[k] = (double)e[k];"),
 }

@@ -101,8 +101,10 @@ def test_window_listed_by_hand_d2():
     P = _ring(ang)
     pn = np.ones(len(ang))
     c = math.cos(math.radians(25))
-    xn, cnt, _ = oracle.shift_step(P, pn, [1.0, 0.0], c)
+    xn, cnt, margin = oracle.shift_step(P, pn, [1.0, 0.0], c)
     assert cnt == 4
+    # the decision closest to the edge: the point at 24 degrees
+    assert margin == pytest.approx(math.cos(math.radians(24)) - c, rel=0, abs=1e-15)
     s = P[[0, 1, 2, 3]].sum(axis=0)
     assert np.allclose(xn, s / np.linalg.norm(s), rtol=0, atol=1e-15)
 
@@ -220,8 +222,10 @@ def test_merge_threshold_is_strict():
 
 def test_cover_by_hand():
     P = _ring([0, 20, 40, 100])
-    cov, left, _ = oracle.cover(P, np.ones(4), _ring([30]), np.zeros(4, np.uint8), c=math.cos(math.radians(12)))
+    cov, left, margin = oracle.cover(P, np.ones(4), _ring([30]), np.zeros(4, np.uint8), c=math.cos(math.radians(12)))
     assert cov.tolist() == [0, 1, 1, 0] and left == 2
+    # closest to the edge: the pixels 10 degrees from the mode
+    assert margin == pytest.approx(math.cos(math.radians(10)) - math.cos(math.radians(12)), rel=0, abs=1e-15)
     cov2, left2, _ = oracle.cover(P, np.ones(4), _ring([30]), np.array([1, 0, 0, 0], np.uint8),
                                   c=math.cos(math.radians(12)))
     assert cov2.tolist() == [1, 1, 1, 0] and left2 == 1
@@ -237,6 +241,9 @@ def test_label_argmax_ties_lowest_and_background():
     labels, margin = oracle.label(P, np.ones(4), np.array([0, 2, 3, 5]), modes, 6)
     assert labels.tolist() == [0, -1, 0, 1, -1, 1]
     assert margin[0] == 0.0  # exact tie between modes 0 and 2
+    # top-two margin when the best mode comes last: 1 - cos 45 degrees
+    _, margin = oracle.label(_ring([0]), np.ones(1), np.array([0]), _ring([90, 45, 0]), 1)
+    assert margin[0] == pytest.approx(1.0 - math.sqrt(0.5), rel=0, abs=1e-15)
 
 
 # ----------------------------------------------------------- OSOP theory
@@ -302,6 +309,10 @@ def test_schedule_bounds_are_strict():
     # one unit in the last place inside the band's edge, the rule acts
     assert oracle.next_n(N, I, 10 ** 6, L=np.nextafter(edge, 2 * edge), H=1e9) == 2 * N
     assert oracle.next_n(N, I, 10 ** 6, L=0.5, H=np.nextafter(edge, 0.0)) == N - math.ceil(nm)
+    # N never drops below one seed: with P = 0.001 and I = 2, N_min = 0.046, so
+    # N = 1 lies above H N_min and 1 - ceil(N_min) = 0 is clamped to 1
+    assert oracle.nmin(2, P=0.001) < 1.0 / 8.0
+    assert oracle.next_n(1, 2, 100, P=0.001) == 1
 
 
 # ------------------------------------------------------- whole method

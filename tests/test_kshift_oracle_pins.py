@@ -18,8 +18,10 @@ def test_euclid_flat_hand_worked_1d():
     P = np.array([[0.0], [0.5], [1.0], [3.0]])
     X, s, n = K.step(np.array([[0.4]]), P, K.EUCLID, K.FLAT, 1.2)
     assert X[0, 0] == pytest.approx(0.5, abs=1e-15) and s[0] == 3 and n[0] == 3
-    XT, _ = K.run(P, np.array([[0.4]]), K.EUCLID, K.FLAT, 1.2, 5)
+    XT, margin = K.run(P, np.array([[0.4]]), K.EUCLID, K.FLAT, 1.2, 5)
     assert XT[0, 0] == pytest.approx(0.5, abs=1e-15)
+    # the decision nearest the window's edge: d = 0.6 in the first step, t = 1/4
+    assert margin == pytest.approx(0.75, abs=1e-15)
 
 
 def test_epanechnikov_hand_worked_1d():

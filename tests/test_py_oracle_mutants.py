@@ -27,6 +27,7 @@ KSHIFT = {
     "empty_window_moves": ("ok = s > 0", "ok = s >= 0"),
     "count_includes_zero_weights": ("(W > 0).sum(axis=1)", "(W >= 0).sum(axis=1)"),
     "run_extra_step": ("    for _ in range(T):", "    for _ in range(T + 1):"),
+    "run_margin_ignored": ("            margin = min(margin, float(", "            margin = max(margin, float("),
     "run_seeds_not_normalised": ("        X = X / np.linalg.norm(X, axis=1, keepdims=True)\n", ""),
 }
 

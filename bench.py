@@ -879,6 +879,7 @@ def run_ours(args, rank, ws, local):
     step_ms, tot = timed(main, args.steps, args.warmup, ws, flush, stream)
     clk = clocks.stop()
     value, t_total = whole_job_rate(tot["frames"], sum(step_ms) / 1e3, ws)
+    launches = int(reduce_over_ranks(tot["launches"], ws, "sum"))   # every rank takes part
     roofline = roofline_of(args.form, tot, step_ms, clk, n_sm)
     forms = {args.form: {"value": value, "frames_per_step": args.frames, "steps": args.steps,
                          "ms_per_frame": sum(step_ms) / max(1, tot["frames"]),
@@ -902,18 +903,21 @@ def run_ours(args, rank, ws, local):
                         "clocks_sm_mhz": c_clk.get("sm_mhz")}
         r.close()
 
+    # The untimed legs below run on rank 0 of a one-GPU run only: no collective
+    # may sit inside them, and with N > 1 the other GPUs would wait idle.
+    extras = rank == 0 and ws == 1
     vmf = None
-    if rank == 0 and not args.no_vmf:
+    if extras and not args.no_vmf:
         vmf = vmf_leg(n_sm, clk)
     video = None
-    if rank == 0 and args.video_frames > 0:
+    if extras and args.video_frames > 0:
         video = video_leg(args.video_frames)
     kvar, d32 = None, None
-    if rank == 0 and not args.no_vmf:
+    if extras and not args.no_vmf:
         kvar = kernel_variants_leg(n_sm, clk)
         d32 = d32_leg(n_sm)
     cpu, parity = None, None
-    if rank == 0 and args.cpu != "none":
+    if extras and args.cpu != "none":
         import oracle
         if args.cpu == "full":
             f0 = frames[0]
@@ -985,7 +989,7 @@ def run_ours(args, rank, ws, local):
                 "video": video,
                 "parity_vs_oracle": parity,
                 "cpu_baseline": cpu,
-                "e2e": e2e, "gpu_launches": int(reduce_over_ranks(tot["launches"], ws, "sum")), "clocks": clk}
+                "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
 
 

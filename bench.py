@@ -298,6 +298,11 @@ def run_reference(args, rank):
     the gamma stop) and scales it to frames/s."""
     if rank != 0:
         return
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        # the other ranks do no work: the oracle gets every host core, as at
+        # N = 1 (torchrun's default of one thread per rank would otherwise
+        # hold; the OpenMP team is sized when the oracle library loads)
+        os.environ["OMP_NUM_THREADS"] = str(len(os.sched_getaffinity(0)))
     frame = c2_frames(0, 1)[0]
     per_frame = c2_seed_iters_per_frame()
     for _ in range(args.warmup):

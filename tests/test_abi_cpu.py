@@ -65,3 +65,37 @@ def test_kernels_compiled_for_sm103a(libpath):
     # the build passes exactly one -gencode for sm_103a
     from paper_2007_14283_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include "ms.h"
+int main(void) {
+    ms_config c;
+    int64_t bytes = 0;
+    ms_status s;
+    ms_config_default(&c);
+    if (c.dim != 16 || c.n_initial != 128) return 2;
+    c.dim = 0;
+    s = ms_workspace_bytes(&c, 100, &bytes);
+    printf("%s\n", ms_last_error());
+    return s == MS_ERR_INVALID_ARG ? 0 : 1;
+}
+"""
+
+
+def test_header_is_plain_c_and_links_from_c(libpath, tmp_path):
+    # the boundary is a C ABI: the header compiles as strict C99 and a C
+    # program links against the library and calls its host-side entry points
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    src = tmp_path / "main.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "main"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                    "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe), libpath,
+                    "-Wl,-rpath," + os.path.dirname(libpath)], check=True, capture_output=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert "dim" in r.stdout
